@@ -1,0 +1,244 @@
+/*
+ * shg.h - C ABI of the GB300 (sm_103a) solid-harmonic Gaussian integral library.
+ *
+ * The library evaluates, on the GPU, batched integrals over contracted real
+ * solid-harmonic Gaussian shells by the SHG scheme of Golze, Benedikter,
+ * Iannuzzi, Wilhelm and Hutter (arXiv:1701.06588):
+ *   - two-center integrals (a|O|b) for O = delta (overlap), 1/r, erfc(w r)/r,
+ *     erf(w r)/r and exp(-w r^2)  (Sec. II B, Eq. final_r12int_ab; Table S1),
+ *   - three-index overlaps (a b a~) with a and a~ on one center (Sec. II D),
+ *   - gradients of both with respect to the centers (Sec. II E, Eq. dev_ab).
+ *
+ * Conventions (all entry points):
+ *   * A shell is (l, K primitives with exponents alpha_i > 0 and contraction
+ *     coefficients c_i, a center).  Its functions are
+ *         phi_{l,m}(r) = N_l sum_i c_i S_{l,m}(r - R) exp(-alpha_i |r - R|^2),
+ *     S_{l,m} the unit-normalised real solid harmonics (S_{1,1} = x,
+ *     S_{1,-1} = y, S_{1,0} = z; S_{l,m} = A_{l,|m|} R^{c/s}_{l,|m|} of
+ *     Sec. II E), m = -l..l.  N_l is the closed form of Sec. II A (unit
+ *     self-overlap) when `normalize` != 0, else 1.
+ *   * A two-center block is stored row-major [m_a = -la..la][m_b = -lb..lb],
+ *     (2la+1)(2lb+1) doubles, at d_out + d_out_offsets[p].
+ *   * A three-index block is row-major [m_a][m_a~][m_b].
+ *   * Arguments named d_* are DEVICE pointers on the current CUDA device and
+ *     are owned by the caller (for example PyTorch tensors).  Arguments named
+ *     h_* or without prefix are host pointers, read during the call only.
+ *   * `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Evaluation calls are asynchronous with respect to the host
+ *     unless stated otherwise.
+ *   * Every int-returning call returns SHG_OK (0) or a negative SHG_E* code;
+ *     shg_last_error() then gives a message (thread-local).
+ */
+#ifndef SHG_H
+#define SHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHG_LMAX_2C 6      /* largest l of a shell in two-center calls            */
+#define SHG_LMAX_AAB_A 10  /* largest la + la~ in (aab) calls                     */
+#define SHG_KMAX 32        /* largest number of primitives of one shell           */
+
+enum shg_status {
+    SHG_OK = 0,
+    SHG_EINVAL = -1,   /* invalid argument (l, K, exponent, index, operator, ...) */
+    SHG_ENOMEM = -2,   /* host or device allocation failed                        */
+    SHG_ECUDA = -3,    /* a CUDA runtime call failed                              */
+    SHG_ETIMEOUT = -4, /* a bounded device-side wait gave up                      */
+    SHG_ERANGE = -5    /* size beyond a documented maximum                        */
+};
+
+enum shg_operator {
+    SHG_OP_OVERLAP = 0, /* delta(r12):       (a|b)                                */
+    SHG_OP_COULOMB = 1, /* 1/r12                                                  */
+    SHG_OP_ERFC = 2,    /* erfc(w r12)/r12, short range, w > 0                    */
+    SHG_OP_ERF = 3,     /* erf(w r12)/r12, long range, w > 0                      */
+    SHG_OP_GAUSS = 4    /* exp(-w r12^2), w > 0                                   */
+};
+
+enum shg_precision {
+    SHG_PREC_FP64 = 0,  /* every step in FP64                                     */
+    SHG_PREC_MIXED = 1  /* FP32-based compensated arithmetic, FP64 where needed   */
+};
+
+enum shg_schedule {
+    SHG_SCHED_PER_CLASS = 0,  /* one launch per (la, lb) class                    */
+    SHG_SCHED_PERSISTENT = 1  /* one launch, warps pull class-pure tiles          */
+};
+
+typedef struct shg_basis shg_basis_t;
+typedef struct shg_plan shg_plan_t;
+
+/*
+ * shg_basis_create - upload a shell set to the current device.
+ * Definition: contracted shells phi_{l,m} of Sec. II A, Eq. contracted_phi,
+ * with N_l of the equation after it (includes K_l = sqrt((2l+1)/4pi)).
+ *   n_shells          number of shells (>= 1)
+ *   l[n_shells]       angular momentum, 0 <= l <= SHG_LMAX_2C
+ *   nprim[n_shells]   primitives per shell, 1 <= K <= SHG_KMAX
+ *   exps, coefs       sum(nprim) values each, concatenated shell by shell
+ *   n_centers         number of centers
+ *   centers           n_centers x 3 doubles (bohr)
+ *   center_of_shell   center index of each shell, 0 <= c < n_centers
+ *   normalize         non-zero: multiply coefficients by N_l
+ * All input pointers are host pointers, copied; the caller keeps them.
+ * Returns SHG_EINVAL for l or K out of range, a non-positive or non-finite
+ * exponent, a non-finite coefficient or center, or a bad center index;
+ * SHG_ENOMEM / SHG_ECUDA on allocation or copy failure.  On success *out
+ * owns device memory until shg_basis_destroy.  Synchronous.
+ */
+int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const double *exps,
+                     const double *coefs, int n_centers, const double *centers,
+                     const int32_t *center_of_shell, int normalize, shg_basis_t **out);
+
+/*
+ * shg_basis_set_centers - replace all center coordinates (host array of
+ * n_centers x 3 doubles, same count as at creation).  Plans made on the basis
+ * stay valid: they depend only on l and K.  Synchronous.
+ */
+int shg_basis_set_centers(shg_basis_t *basis, const double *centers);
+
+/* shg_basis_destroy - free the device copy.  NULL is ignored. */
+void shg_basis_destroy(shg_basis_t *basis);
+
+/* Number of shells and primitives of a basis (0 for NULL). */
+int64_t shg_basis_nshells(const shg_basis_t *basis);
+int64_t shg_basis_nprims(const shg_basis_t *basis);
+
+/*
+ * shg_pair_offsets - host helper: offsets[p] = sum_{q<p} (2la_q+1)(2lb_q+1)
+ * for host pair lists; returns the total number of doubles, or a negative
+ * SHG_E* code for an out-of-range shell index.
+ */
+int64_t shg_pair_offsets(const shg_basis_t *basis, int64_t n_pairs, const int32_t *pair_a,
+                         const int32_t *pair_b, int64_t *offsets);
+
+/* As shg_pair_offsets for (aab) triples: blocks (2la+1)(2la~+1)(2lb+1). */
+int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n_triples,
+                           const int32_t *t_a, const int32_t *t_atilde, const int32_t *t_b, int64_t *offsets);
+
+/*
+ * shg_eval_2c - two-center integrals (a|O|b) of Sec. II B:
+ *   (a|O|b) = (-1)^lb A_{la,ma} A_{lb,mb} sum_j 2^{la+lb-j} O^{(la+lb-j)}(R^2)
+ *             (2j-1)!! sum_kappa B_{j,kappa} Q_{la,|ma|,lb,|mb|,j,kappa}
+ * with O^{(k)} the contracted R_ab^2-derivatives of Eq. O_rab2_deriv and the
+ * s-type integrals of Table S1.
+ *   basis          shells for both sides
+ *   n_pairs        number of pairs (0 is allowed and does nothing)
+ *   d_pair_a/b     device int32[n_pairs] shell indices
+ *   op, omega      operator (enum shg_operator); omega > 0 for ERF, ERFC, GAUSS
+ *   screen_thresh  0 disables screening; > 0: a pair whose bound on every
+ *                  element magnitude is below it writes zeros (overlap and
+ *                  Gaussian operator only; Coulomb-type pairs are never
+ *                  screened)
+ *   precision      enum shg_precision
+ *   d_out_offsets  device int64[n_pairs] start of each block in d_out
+ *   d_out          device doubles, large enough for every block
+ * One-shot convenience: builds a plan (device memory, one host sync to read
+ * class counts), executes it on `stream` and frees it.  Returns SHG_EINVAL
+ * for a bad operator, omega, precision or shell index.
+ */
+int shg_eval_2c(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,
+                int op, double omega, double screen_thresh, int precision, const int64_t *d_out_offsets,
+                double *d_out, void *stream);
+
+/*
+ * shg_plan_2c_create - bucket a pair list by (la, lb, Ka*Kb) class on the
+ * device and build the tile list of a schedule (enum shg_schedule).  The plan
+ * owns device memory (about 12 bytes per pair) and depends only on the pair
+ * list and the l and K of the shells, not on centers, exponents or operator.
+ * Validates the shell indices on the device and synchronises `stream` once.
+ * d_pair_a/b must stay valid and unchanged for the plan's lifetime.
+ */
+int shg_plan_2c_create(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a,
+                       const int32_t *d_pair_b, int schedule, void *stream, shg_plan_t **out);
+
+/*
+ * shg_plan_2c_exec - evaluate the integrals of a plan (see shg_eval_2c for the
+ * arguments).  Asynchronous; issues only kernel launches and a memset on
+ * `stream`, so it can be captured in a CUDA graph.
+ */
+int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thresh, int precision,
+                     const int64_t *d_out_offsets, double *d_out, void *stream);
+
+/* Number of kernel launches one shg_plan_2c_exec issues (for accounting). */
+int shg_plan_launches(const shg_plan_t *plan);
+
+/* shg_plan_destroy - free a plan (synchronises its stream first). NULL ok. */
+void shg_plan_destroy(shg_plan_t *plan);
+
+/*
+ * shg_eval_3c_aab - three-index overlaps (a b a~) = int phi_a phi_a~ phi_b of
+ * Sec. II D: the product phi_a phi_a~ is expanded with real Gaunt
+ * coefficients into shells L_a = |la-la~|..la+la~ (step 2) with exponent
+ * alpha + alpha~ (Eq. product_SHG_STGO), the radial part is P^{(k)} of
+ * Eq. Pa_aba built from (0_a'|r_a^{2m}|0_b)^{(k)} (Eqs. sra2ms, devsra2ms),
+ * and the angular part reuses Q of Sec. II E.
+ *   orb            basis of a and a~ (both on one center, checked)
+ *   aux            basis of b (may be the same handle as orb)
+ *   d_a, d_atilde  device int32[n_triples] indices into orb
+ *   d_b            device int32[n_triples] indices into aux
+ *   precision      enum shg_precision
+ *   screen_thresh  as in shg_eval_2c (overlap bound)
+ *   d_out_offsets  device int64[n_triples]; d_out device doubles
+ * Limits: la + la~ <= SHG_LMAX_AAB_A, lb <= SHG_LMAX_2C.  Returns SHG_EINVAL
+ * when a and a~ of a triple are not on the same center.
+ */
+int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n_triples, const int32_t *d_a,
+                    const int32_t *d_atilde, const int32_t *d_b, int precision, double screen_thresh,
+                    const int64_t *d_out_offsets, double *d_out, void *stream);
+
+/*
+ * shg_eval_2c_grad - vector-Jacobian product of the two-center integrals with
+ * respect to the centers (Sec. II E, Eq. dev_ab):
+ *   d_grad_a[p][i] = sum_{ma,mb} W_p[ma][mb] d(a|O|b)[ma][mb] / dR_{a,i}
+ *   d_grad_b[p][i] = -d_grad_a[p][i]   (translation invariance)
+ * using O^{(k+1)} with Q~ and O^{(k)} with dQ~/dR_a (Eqs. cartesian_dev_x/y/z);
+ * radial terms are recomputed, nothing is stored from a forward call.
+ *   d_w_offsets, d_upstream_w   device int64[n_pairs] / doubles: W_p blocks,
+ *                               same layout as shg_eval_2c output
+ *   d_grad_a, d_grad_b          device double[n_pairs][3]; d_grad_b may be NULL
+ * No atomics: per-atom sums are left to the caller.
+ */
+int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,
+                     int op, double omega, int precision, const int64_t *d_w_offsets, const double *d_upstream_w,
+                     double *d_grad_a, double *d_grad_b, void *stream);
+
+/*
+ * shg_eval_3c_aab_grad - as shg_eval_2c_grad for (a b a~):
+ *   d_grad_a[t][i] = sum W_t[ma][ma~][mb] d(a b a~)/dR_{a,i}, with R_a the
+ *   common center of a and a~; d_grad_b = -d_grad_a.
+ */
+int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n_triples, const int32_t *d_a,
+                         const int32_t *d_atilde, const int32_t *d_b, int precision, const int64_t *d_w_offsets,
+                         const double *d_upstream_w, double *d_grad_a, double *d_grad_b, void *stream);
+
+/*
+ * shg_debug_boys - device Boys function F_n(T) = int_0^1 exp(-T t^2) t^{2n} dt
+ * (SI Eq. 3) as used by the Coulomb-type radial terms: for every T in
+ * d_T[n_T] writes F_n for n = 0..nmax (nmax <= 24) to d_F[i*(nmax+1) + n].
+ */
+int shg_debug_boys(int64_t n_T, const double *d_T, int nmax, double *d_F, void *stream);
+
+/*
+ * shg_measure_alu_peak - ALU throughput probe: a grid of independent FMA
+ * chains in FP64 (kind 0) or FP32 (kind 1), `iters` FMAs per thread per
+ * chain, timed with CUDA events on `stream`.  Writes FLOP/s (2 per FMA) to
+ * *flops.  Synchronous.
+ */
+int shg_measure_alu_peak(int kind, int iters, double *flops, void *stream);
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char *shg_last_error(void);
+
+/* Library version string. */
+const char *shg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHG_H */

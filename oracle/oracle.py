@@ -55,8 +55,8 @@ def _lib(long_double=False):
             lib.oracle_sph_coef.argtypes = [i32, P]
             lib.oracle_cart_2c.argtypes = [i32, f64, i32, i32, f64, f64, P, P, P]
             lib.oracle_shell_norms.argtypes = [i32, P, P, P, P, P, P]
-            lib.oracle_eval_2c.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i32, f64, i32, P, P, i32]
-            lib.oracle_eval_3c_aab.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, P, i32, P, P, i32]
+            lib.oracle_eval_2c.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i32, f64, i32, i32, P, P, i32]
+            lib.oracle_eval_3c_aab.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, P, i32, i32, P, P, i32]
             _libs[long_double] = lib
         return _libs[long_double]
 
@@ -131,7 +131,7 @@ def _threads(nthreads):
     return int(nthreads) if nthreads else (os.cpu_count() or 1)
 
 
-def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double):
+def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double, normalize=True):
     s = _Shells(shells)
     pa = np.ascontiguousarray(pair_a, dtype=np.int32)
     pb = np.ascontiguousarray(pair_b, dtype=np.int32)
@@ -142,31 +142,33 @@ def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double):
     total = int(sizes.sum())
     out = np.zeros(total * (3 if deriv else 1))
     r = _lib(long_double).oracle_eval_2c(*s.args(), len(pa), _p(pa), _p(pb), int(op), float(omega), int(deriv),
-                                         _p(offsets), _p(out), _threads(nthreads))
+                                         int(bool(normalize)), _p(offsets), _p(out), _threads(nthreads))
     if r:
         raise ValueError("oracle_eval_2c failed: %d" % r)
     return out, offsets, sizes
 
 
-def eval_2c(shells, pair_a, pair_b, op, omega=0.0, nthreads=None, long_double=None):
+def eval_2c(shells, pair_a, pair_b, op, omega=0.0, nthreads=None, long_double=None, normalize=True):
     """Contracted normalised blocks (a|O|b) of all pairs, concatenated.
 
     Returns (values, offsets, sizes); block p is values[offsets[p]:offsets[p]+sizes[p]]
-    in row-major order [m_a = -la..la][m_b = -lb..lb].
+    in row-major order [m_a = -la..la][m_b = -lb..lb].  normalize=False uses
+    the coefficients as given.
     """
-    return _eval2c(shells, pair_a, pair_b, op, omega, 0, nthreads, long_double)
+    return _eval2c(shells, pair_a, pair_b, op, omega, 0, nthreads, long_double, normalize)
 
 
-def eval_2c_grad(shells, pair_a, pair_b, op, omega=0.0, center="A", nthreads=None, long_double=None):
+def eval_2c_grad(shells, pair_a, pair_b, op, omega=0.0, center="A", nthreads=None, long_double=None,
+                 normalize=True):
     """Jacobian of every block with respect to R_a (center='A') or R_b ('B').
 
     Returns (values, offsets, sizes): pair p owns values[3*offsets[p] : 3*(offsets[p]+sizes[p])]
     laid out [xyz][m_a][m_b].
     """
-    return _eval2c(shells, pair_a, pair_b, op, omega, 1 if center == "A" else 2, nthreads, long_double)
+    return _eval2c(shells, pair_a, pair_b, op, omega, 1 if center == "A" else 2, nthreads, long_double, normalize)
 
 
-def _eval3c(shells, ta, tt, tb, deriv, nthreads, long_double):
+def _eval3c(shells, ta, tt, tb, deriv, nthreads, long_double, normalize=True):
     s = _Shells(shells)
     ta = np.ascontiguousarray(ta, dtype=np.int32)
     tt = np.ascontiguousarray(tt, dtype=np.int32)
@@ -178,16 +180,16 @@ def _eval3c(shells, ta, tt, tb, deriv, nthreads, long_double):
         offsets[1:] = np.cumsum(sizes[:-1])
     out = np.zeros(int(sizes.sum()) * (3 if deriv else 1))
     r = _lib(long_double).oracle_eval_3c_aab(*s.args(), len(ta), _p(ta), _p(tt), _p(tb), int(deriv),
-                                             _p(offsets), _p(out), _threads(nthreads))
+                                             int(bool(normalize)), _p(offsets), _p(out), _threads(nthreads))
     if r:
         raise ValueError("oracle_eval_3c_aab failed: %d" % r)
     return out, offsets, sizes
 
 
-def eval_3c_aab(shells, t_a, t_atilde, t_b, nthreads=None, long_double=None):
+def eval_3c_aab(shells, t_a, t_atilde, t_b, nthreads=None, long_double=None, normalize=True):
     """Three-index overlaps (a b a~) with a, a~ on one center; blocks [m_a][m_a~][m_b]."""
-    return _eval3c(shells, t_a, t_atilde, t_b, 0, nthreads, long_double)
+    return _eval3c(shells, t_a, t_atilde, t_b, 0, nthreads, long_double, normalize)
 
 
-def eval_3c_aab_grad(shells, t_a, t_atilde, t_b, center="A", nthreads=None, long_double=None):
-    return _eval3c(shells, t_a, t_atilde, t_b, 1 if center == "A" else 2, nthreads, long_double)
+def eval_3c_aab_grad(shells, t_a, t_atilde, t_b, center="A", nthreads=None, long_double=None, normalize=True):
+    return _eval3c(shells, t_a, t_atilde, t_b, 1 if center == "A" else 2, nthreads, long_double, normalize)

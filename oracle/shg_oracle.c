@@ -429,7 +429,8 @@ static void get_center(const shells_t *S, int s, real *P)
  *            d/dA_x g_a = 2 alpha g_{a+1x} - a_x g_{a-1x}.
  * deriv = 2: d/dB_{x,y,z}, via the same identity on g_b.
  */
-static void pair_2c(work_t *w, const shells_t *S, int sa, int sb, int op, real omega, int deriv, double *out)
+static void pair_2c(work_t *w, const shells_t *S, int sa, int sb, int op, real omega, int deriv, int normalize,
+                    double *out)
 {
     int la = S->l[sa], lb = S->l[sb];
     int nca = ncart(la), ncb = ncart(lb);
@@ -437,8 +438,8 @@ static void pair_2c(work_t *w, const shells_t *S, int sa, int sb, int op, real o
     real A[3], B[3];
     get_center(S, sa, A);
     get_center(S, sb, B);
-    real Na = shell_norm(w->c, S, sa, w->tsph[la]);
-    real Nb = shell_norm(w->c, S, sb, w->tsph[lb]);
+    real Na = normalize ? shell_norm(w->c, S, sa, w->tsph[la]) : 1;
+    real Nb = normalize ? shell_norm(w->c, S, sb, w->tsph[lb]) : 1;
     int ncomp = deriv ? 3 : 1;
     real *C = (real *)calloc((size_t)ncomp * nca * ncb, sizeof(real));
     for (int i = 0; i < S->nprim[sa]; ++i)
@@ -500,7 +501,7 @@ static void pair_2c(work_t *w, const shells_t *S, int sa, int sb, int op, real o
  * deriv = 1: d/dA (both functions on A move), out[3][block], product rule.
  * deriv = 2: d/dB, out[3][block].
  */
-static void triple_aab(work_t *w, const shells_t *S, int sa, int st, int sb, int deriv, double *out)
+static void triple_aab(work_t *w, const shells_t *S, int sa, int st, int sb, int deriv, int normalize, double *out)
 {
     int la = S->l[sa], lt = S->l[st], lb = S->l[sb];
     int nca = ncart(la), nct = ncart(lt), ncb = ncart(lb);
@@ -508,9 +509,9 @@ static void triple_aab(work_t *w, const shells_t *S, int sa, int st, int sb, int
     real A[3], B[3];
     get_center(S, sa, A);
     get_center(S, sb, B);
-    real Na = shell_norm(w->c, S, sa, w->tsph[la]);
-    real Nt = shell_norm(w->c, S, st, w->tsph[lt]);
-    real Nb = shell_norm(w->c, S, sb, w->tsph[lb]);
+    real Na = normalize ? shell_norm(w->c, S, sa, w->tsph[la]) : 1;
+    real Nt = normalize ? shell_norm(w->c, S, st, w->tsph[lt]) : 1;
+    real Nb = normalize ? shell_norm(w->c, S, sb, w->tsph[lb]) : 1;
     int ncomp = deriv ? 3 : 1;
     size_t csz = (size_t)nca * nct * ncb;
     real *C = (real *)calloc((size_t)ncomp * csz, sizeof(real));
@@ -610,12 +611,13 @@ int oracle_shell_norms(int n_shells, const int32_t *l, const int32_t *nprim, con
 
 /*
  * Batched two-center blocks.  deriv as in pair_2c; for deriv > 0 each pair
- * writes 3 consecutive blocks starting at out + 3*offsets[p].
+ * writes 3 consecutive blocks starting at out + 3*offsets[p].  normalize = 0
+ * uses the coefficients as given (no unit-self-overlap factor).
  */
 int oracle_eval_2c(int n_shells, const int32_t *l, const int32_t *nprim, const int64_t *prim_off,
                    const double *exps, const double *coefs, const double *centers, const int32_t *center_of,
                    int64_t n_pairs, const int32_t *pa, const int32_t *pb, int op, double omega, int deriv,
-                   const int64_t *offsets, double *out, int nthreads)
+                   int normalize, const int64_t *offsets, double *out, int nthreads)
 {
     shells_t S = {n_shells, l, nprim, prim_off, exps, coefs, centers, center_of};
     if (check_shells(&S, 6)) return -1;
@@ -626,7 +628,7 @@ int oracle_eval_2c(int n_shells, const int32_t *l, const int32_t *nprim, const i
         work_init(&w);
 #pragma omp for schedule(dynamic, 4)
         for (int64_t p = 0; p < n_pairs; ++p)
-            pair_2c(&w, &S, pa[p], pb[p], op, (real)omega, deriv, out + (deriv ? 3 : 1) * offsets[p]);
+            pair_2c(&w, &S, pa[p], pb[p], op, (real)omega, deriv, normalize, out + (deriv ? 3 : 1) * offsets[p]);
         work_free(&w);
     }
     return 0;
@@ -635,7 +637,7 @@ int oracle_eval_2c(int n_shells, const int32_t *l, const int32_t *nprim, const i
 int oracle_eval_3c_aab(int n_shells, const int32_t *l, const int32_t *nprim, const int64_t *prim_off,
                        const double *exps, const double *coefs, const double *centers, const int32_t *center_of,
                        int64_t n_triples, const int32_t *ta, const int32_t *tt, const int32_t *tb, int deriv,
-                       const int64_t *offsets, double *out, int nthreads)
+                       int normalize, const int64_t *offsets, double *out, int nthreads)
 {
     shells_t S = {n_shells, l, nprim, prim_off, exps, coefs, centers, center_of};
     if (check_shells(&S, 6)) return -1;
@@ -647,7 +649,7 @@ int oracle_eval_3c_aab(int n_shells, const int32_t *l, const int32_t *nprim, con
         work_init(&w);
 #pragma omp for schedule(dynamic, 4)
         for (int64_t p = 0; p < n_triples; ++p)
-            triple_aab(&w, &S, ta[p], tt[p], tb[p], deriv, out + (deriv ? 3 : 1) * offsets[p]);
+            triple_aab(&w, &S, ta[p], tt[p], tb[p], deriv, normalize, out + (deriv ? 3 : 1) * offsets[p]);
         work_free(&w);
     }
     return 0;

@@ -1,0 +1,93 @@
+"""Work-count model.
+
+1. Contracted-element counts of Table II (Sec. IV A): for a family basis
+   whose shells share one set of K exponents,
+     SHG contracts the scalars (0_a|O|0_b)^{(k)}, k = 0..la_max+lb_max (plus
+     one more order for gradients), for each of the K_a K_b primitive pairs;
+     OS contracts every primitive spherical element: (sum over the distinct
+     l present of (2l+1) K)^2 per side pair, four times with gradients.
+
+2. Algorithmic FP64 operation counts of the two-center path as implemented
+   (add/mul = 1 flop, fma = 2 flops, counted from the formulas the kernels
+   evaluate; exp, rsqrt and the like counted separately as special ops).
+   Used for the roofline fraction: algorithmic FLOP/s over the measured FP64
+   FMA throughput.
+"""
+import numpy as np
+
+OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS = 0, 1, 2, 3, 4
+
+
+def shg_contracted_elements(l_a, l_b, k_a, k_b, gradients=False):
+    """Scalars contracted by the SHG scheme for one pair of exponent sets
+    (Table II convention: all orders 0..la_max+lb_max are contracted)."""
+    return (max(l_a) + max(l_b) + 1 + (1 if gradients else 0)) * k_a * k_b
+
+
+def os_contracted_elements(l_a, l_b, k_a, k_b, gradients=False):
+    """Primitive spherical elements contracted by the Obara-Saika route."""
+    na = sum(2 * l + 1 for l in sorted(set(l_a))) * k_a
+    nb = sum(2 * l + 1 for l in sorted(set(l_b))) * k_b
+    return na * nb * (4 if gradients else 1)
+
+
+# --------------------------------------------------------------------------- #
+# FP64 flop model of one shell pair                                           #
+# --------------------------------------------------------------------------- #
+_BOYS = 2 * 8 + 2 * 8 + 1          # Taylor of F_kmax (8 fma), exp Taylor (8 fma), scale by exp(-T_i)
+
+
+def _radial_flops(op, J, kmin):
+    """Per primitive pair: setup + operator part + contraction of J orders."""
+    setup = 1 + 1 + 2 + 1 + 1       # c, 1/c from rsqrt^2, rho, T, w_a w_b
+    powk = 2 * max(int(np.ceil(np.log2(kmin + 1))), 0)
+    if op == OP_OVERLAP:
+        return setup + 4 + powk + J * (1 + 1)
+    if op == OP_GAUSS:
+        return setup + 10 + powk + J * (1 + 1)
+    coul = 4 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
+    att = 6 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
+    if op == OP_COULOMB:
+        return setup + coul
+    if op == OP_ERF:
+        return setup + 4 + att
+    return setup + coul + att      # erfc
+
+
+def _radial_special(op):
+    """Special-function calls per primitive pair (rsqrt, exp)."""
+    return {OP_OVERLAP: 2, OP_GAUSS: 3, OP_COULOMB: 1, OP_ERF: 2, OP_ERFC: 2}[op]
+
+
+def pair_flops(la, lb, ka, kb, op):
+    """Algorithmic FP64 flops of one contracted shell pair (numpy-vectorised)."""
+    la = np.asarray(la, dtype=np.int64)
+    lb = np.asarray(lb, dtype=np.int64)
+    kk = np.asarray(ka, dtype=np.int64) * np.asarray(kb, dtype=np.int64)
+    J = np.minimum(la, lb) + 1
+    kmin = np.maximum(la, lb)
+    lmax = np.maximum(la, lb)
+    na, nb = 2 * la + 1, 2 * lb + 1
+    rad = np.zeros_like(kk, dtype=np.float64)
+    for j in range(1, 8):
+        for km in range(0, 7):
+            m = (J == j) & (kmin == km)
+            if m.any():
+                rad[m] = _radial_flops(op, j, km)
+    radial = kk * rad
+    harmonics = 8.0 * (lmax + 1) * (lmax + 2) / 2            # R^c, R^s recursions
+    w_rows = (na + nb) * J * J                              # one add per W entry
+    scale = na * J * J + 2 * J * J                          # g_e and U_a scaling
+    assembly = na * nb * (2 * J * J + 2)                    # J^2 fma + 2 mul per element
+    return radial + harmonics + w_rows + scale + assembly
+
+
+def workload_flops(shells, pair_a, pair_b, op):
+    l = np.asarray(shells["l"])
+    k = np.asarray(shells["nprim"])
+    return float(np.sum(pair_flops(l[pair_a], l[pair_b], k[pair_a], k[pair_b], op)))
+
+
+def workload_elements(shells, pair_a, pair_b):
+    l = np.asarray(shells["l"]).astype(np.int64)
+    return int(np.sum((2 * l[pair_a] + 1) * (2 * l[pair_b] + 1)))

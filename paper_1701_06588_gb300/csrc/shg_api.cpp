@@ -1,0 +1,600 @@
+// Host side of the SHG integral library: C ABI, input validation, shell
+// normalisation, device tables, planning and kernel dispatch.
+#include "../../include/shg.h"
+#include "shg_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+struct shg_basis {
+    shg::BasisDev d;
+};
+
+struct shg_plan {
+    shg::PlanDev d;
+    int launches = 0;
+};
+
+namespace shg {
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define SHG_CUDA(call)                                                                                    \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(SHG_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                                           __FILE__, __LINE__);                                          \
+    } while (0)
+
+// ------------------------------------------------------------------------- //
+// Constant tables                                                           //
+// ------------------------------------------------------------------------- //
+static long double lfact(int n)
+{
+    long double f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+void fill_consts(Consts &k)
+{
+    std::memset(&k, 0, sizeof k);
+    // A_{l,mu} = (-1)^mu sqrt((2 - delta_{mu,0}) (l+mu)! (l-mu)!)      Eq. (A)
+    for (int l = 0; l <= kLmaxR; ++l)
+        for (int mu = 0; mu <= l; ++mu) {
+            long double v = std::sqrt((long double)(mu == 0 ? 1 : 2) * lfact(l + mu) * lfact(l - mu));
+            k.A[l][mu] = (double)((mu & 1) ? -v : v);
+        }
+    // (2j-1)!! B_{j,kappa},  B_{j,kappa} = 1 / ((2 - delta_{kappa,0}) (j+kappa)! (j-kappa)!)   Eq. (B)
+    for (int j = 0; j < kJmax; ++j) {
+        long double df = 1;
+        for (int i = 2 * j - 1; i > 1; i -= 2) df *= i;
+        for (int kp = 0; kp <= j; ++kp)
+            k.jB[j][kp] = (double)(df / ((kp == 0 ? 1 : 2) * lfact(j + kp) * lfact(j - kp)));
+    }
+    for (int i = 0; i < 32; ++i) k.pow2[i] = std::ldexp(1.0, i);
+    for (int i = 0; i < 64; ++i) k.dint[i] = (double)i;
+    for (int i = 1; i < 192; ++i) k.inv_int[i] = (double)(1.0L / (long double)i);
+}
+
+// Boys table, computed in long double: F_N(T) from its power series
+//   F_N(T) = exp(-T) sum_k (2T)^k / ((2N+1)(2N+3)...(2N+2k+1))
+// at N = 40, then the stable downward recursion
+//   F_{n-1}(T) = (2T F_n(T) + exp(-T)) / (2n-1).
+void make_boys_table(double *tab, double *etab)
+{
+    const int ntop = 40;
+    for (int i = 0; i < kBoysGrid; ++i) {
+        const long double T = (long double)i / 16.0L;
+        const long double e = std::exp(-T);
+        long double term = 1.0L / (2 * ntop + 1), sum = term;
+        for (int k = 1; k < 4000; ++k) {
+            term *= 2 * T / (long double)(2 * ntop + 2 * k + 1);
+            sum += term;
+            if (term < sum * 1e-24L) break;
+        }
+        long double F[ntop + 1];
+        F[ntop] = e * sum;
+        for (int n = ntop; n > 0; --n) F[n - 1] = (2 * T * F[n] + e) / (long double)(2 * n - 1);
+        for (int n = 0; n < kBoysN; ++n) {
+            long double tf = 1;
+            for (int t = 0; t < kBoysTerms; ++t) {
+                if (t > 0) tf *= t;
+                tab[((size_t)i * kBoysN + n) * kBoysTerms + t] = (double)(F[n + t] / tf);
+            }
+        }
+        etab[i] = (double)e;
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// Per-device tables                                                          //
+// ------------------------------------------------------------------------- //
+constexpr int kNBins = kNClass * kKmax * kKmax;
+
+struct DevState {
+    DeviceTables t{};
+    int *bin_rank[2] = {nullptr, nullptr};   // [2 * kNBins]: rank of bin, then bin of rank
+    bool ready = false;
+};
+
+static std::mutex g_mu;
+static DevState g_dev[64];
+
+static double class_cost(int la, int lb, int kk)
+{
+    const int J = std::min(la, lb) + 1;
+    const double radial = kk * (40.0 + 4.0 * J);
+    const double na = 2 * la + 1, nb = 2 * lb + 1;
+    const double angular = na * nb * (J * J + 2) + (2 * na + nb) * J * J + 10.0 * (std::max(la, lb) + 1) * (std::max(la, lb) + 1);
+    return radial + angular;
+}
+
+static void make_ranks(int schedule, std::vector<int> &rank, std::vector<int> &inv)
+{
+    rank.assign(kNBins, 0);
+    inv.assign(kNBins, 0);
+    std::vector<int> order(kNBins);
+    for (int b = 0; b < kNBins; ++b) order[b] = b;
+    if (schedule == SHG_SCHED_PER_CLASS) {
+        // class-major, Ka*Kb descending inside a class
+        std::sort(order.begin(), order.end(), [](int x, int y) {
+            const int cx = x / (kKmax * kKmax), cy = y / (kKmax * kKmax);
+            if (cx != cy) return cx < cy;
+            return (x % (kKmax * kKmax)) > (y % (kKmax * kKmax));
+        });
+    } else {
+        // estimated cost descending (longest tiles first)
+        std::vector<double> cost(kNBins);
+        for (int b = 0; b < kNBins; ++b) {
+            const int cls = b / (kKmax * kKmax), kk = b % (kKmax * kKmax) + 1;
+            cost[b] = class_cost(cls / (kLmax2c + 1), cls % (kLmax2c + 1), kk);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    }
+    for (int r = 0; r < kNBins; ++r) {
+        rank[order[r]] = r;
+        inv[r] = order[r];
+    }
+}
+
+const DeviceTables *device_tables_impl(int **ranks)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        fail(SHG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &st = g_dev[dev];
+    if (!st.ready) {
+        std::vector<double> tab((size_t)kBoysGrid * kBoysN * kBoysTerms), etab(kBoysGrid);
+        make_boys_table(tab.data(), etab.data());
+        double *d_tab = nullptr, *d_e = nullptr;
+        int *d_r[2] = {nullptr, nullptr};
+        if (cudaMalloc(&d_tab, tab.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&d_e, etab.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&d_r[0], 2 * kNBins * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&d_r[1], 2 * kNBins * sizeof(int)) != cudaSuccess) {
+            cudaFree(d_tab); cudaFree(d_e); cudaFree(d_r[0]); cudaFree(d_r[1]);
+            fail(SHG_ENOMEM, "device tables: cudaMalloc failed");
+            return nullptr;
+        }
+        bool ok = cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(d_e, etab.data(), etab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        for (int s = 0; s < 2 && ok; ++s) {
+            std::vector<int> rank, inv;
+            make_ranks(s, rank, inv);
+            rank.insert(rank.end(), inv.begin(), inv.end());
+            ok = cudaMemcpy(d_r[s], rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        if (!ok) {
+            fail(SHG_ECUDA, "device tables: upload failed");
+            return nullptr;
+        }
+        st.t.boys = d_tab;
+        st.t.boys_e = d_e;
+        st.bin_rank[0] = d_r[0];
+        st.bin_rank[1] = d_r[1];
+        st.ready = true;
+    }
+    if (ranks) {
+        ranks[0] = st.bin_rank[0];
+        ranks[1] = st.bin_rank[1];
+    }
+    return &st.t;
+}
+
+const DeviceTables *device_tables() { return device_tables_impl(nullptr); }
+
+static const Consts &consts()
+{
+    static Consts k;
+    static std::once_flag once;
+    std::call_once(once, [] { fill_consts(k); });
+    return k;
+}
+
+static bool is_finite_d(double x) { return std::isfinite(x); }
+
+static int current_device_matches(int dev)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(SHG_ECUDA, "cudaGetDevice failed");
+    if (cur != dev) return fail(SHG_EINVAL, "current device %d differs from the basis device %d", cur, dev);
+    return SHG_OK;
+}
+
+}  // namespace shg
+
+using namespace shg;
+
+// ------------------------------------------------------------------------- //
+// C ABI                                                                      //
+// ------------------------------------------------------------------------- //
+extern "C" {
+
+const char *shg_last_error(void) { return g_err.c_str(); }
+
+const char *shg_version(void) { return "shg-gb300 0.1 (sm_103a)"; }
+
+int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const double *exps, const double *coefs,
+                     int n_centers, const double *centers, const int32_t *center_of_shell, int normalize,
+                     shg_basis_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(SHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_shells < 1 || n_centers < 1) return fail(SHG_EINVAL, "n_shells and n_centers must be >= 1");
+    if (!l || !nprim || !exps || !coefs || !centers || !center_of_shell) return fail(SHG_EINVAL, "NULL input array");
+    int64_t n_prims = 0;
+    for (int s = 0; s < n_shells; ++s) {
+        if (l[s] < 0 || l[s] > kLmax2c) return fail(SHG_EINVAL, "shell %d: l = %d outside 0..%d", s, l[s], kLmax2c);
+        if (nprim[s] < 1 || nprim[s] > kKmax) return fail(SHG_EINVAL, "shell %d: K = %d outside 1..%d", s, nprim[s], kKmax);
+        if (center_of_shell[s] < 0 || center_of_shell[s] >= n_centers)
+            return fail(SHG_EINVAL, "shell %d: center index %d out of range", s, center_of_shell[s]);
+        n_prims += nprim[s];
+    }
+    if (n_prims > (int64_t)INT32_MAX) return fail(SHG_ERANGE, "too many primitives");
+    for (int64_t i = 0; i < n_prims; ++i) {
+        if (!is_finite_d(exps[i]) || exps[i] <= 0) return fail(SHG_EINVAL, "primitive %lld: exponent %g not > 0", (long long)i, exps[i]);
+        if (!is_finite_d(coefs[i])) return fail(SHG_EINVAL, "primitive %lld: coefficient not finite", (long long)i);
+    }
+    for (int64_t i = 0; i < 3 * (int64_t)n_centers; ++i)
+        if (!is_finite_d(centers[i])) return fail(SHG_EINVAL, "center coordinate %lld not finite", (long long)i);
+
+    std::vector<ShellRec> sh(n_shells);
+    std::vector<PrimRec> pr(n_prims);
+    int64_t off = 0;
+    for (int s = 0; s < n_shells; ++s) {
+        const int L = l[s], K = nprim[s];
+        long double N = 1.0L;
+        if (normalize) {
+            // N_l = K_l [sum_ij sqrt(pi) (2l+2)! c_i c_j / (2^{2l+3} (l+1)! (a_i+a_j)^{l+3/2})]^{-1/2}
+            long double sum = 0;
+            const long double pref = std::sqrt(3.14159265358979323846264338327950288L) * lfact(2 * L + 2) /
+                                     (std::ldexp(1.0L, 2 * L + 3) * lfact(L + 1));
+            for (int i = 0; i < K; ++i)
+                for (int j = 0; j < K; ++j)
+                    sum += pref * (long double)coefs[off + i] * coefs[off + j] /
+                           std::pow((long double)exps[off + i] + exps[off + j], (long double)L + 1.5L);
+            if (!(sum > 0)) return fail(SHG_EINVAL, "shell %d: contracted function has zero norm", s);
+            N = std::sqrt((2 * L + 1) / (4 * 3.14159265358979323846264338327950288L)) / std::sqrt(sum);
+        }
+        for (int i = 0; i < K; ++i) {
+            const long double a = exps[off + i];
+            const long double c = N * (long double)coefs[off + i];
+            PrimRec p;
+            p.alpha = (double)a;
+            p.inv_alpha = (double)(1.0L / a);
+            p.w2c = (double)(c / std::pow(2 * a, (long double)L));
+            p.wN = (double)c;
+            pr[off + i] = p;
+        }
+        sh[s] = ShellRec{L, K, (int)off, center_of_shell[s]};
+        off += K;
+    }
+    std::vector<Vec4> ctr(n_centers);
+    for (int c = 0; c < n_centers; ++c) ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+
+    shg_basis_t *b = new (std::nothrow) shg_basis_t;
+    if (!b) return fail(SHG_ENOMEM, "host allocation failed");
+    BasisDev &d = b->d;
+    d.n_shells = n_shells;
+    d.n_centers = n_centers;
+    d.n_prims = n_prims;
+    cudaGetDevice(&d.device);
+    d.h_l = new int32_t[n_shells];
+    d.h_nprim = new int32_t[n_shells];
+    d.h_center = new int32_t[n_shells];
+    std::memcpy(d.h_l, l, sizeof(int32_t) * n_shells);
+    std::memcpy(d.h_nprim, nprim, sizeof(int32_t) * n_shells);
+    std::memcpy(d.h_center, center_of_shell, sizeof(int32_t) * n_shells);
+    if (cudaMalloc(&d.shells, sizeof(ShellRec) * n_shells) != cudaSuccess ||
+        cudaMalloc(&d.prims, sizeof(PrimRec) * n_prims) != cudaSuccess ||
+        cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess) {
+        shg_basis_destroy(b);
+        return fail(SHG_ENOMEM, "basis: cudaMalloc failed");
+    }
+    if (cudaMemcpy(d.shells, sh.data(), sizeof(ShellRec) * n_shells, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.prims, pr.data(), sizeof(PrimRec) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.centers, ctr.data(), sizeof(Vec4) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess) {
+        shg_basis_destroy(b);
+        return fail(SHG_ECUDA, "basis: upload failed");
+    }
+    if (!device_tables()) {
+        shg_basis_destroy(b);
+        return SHG_ECUDA;
+    }
+    *out = b;
+    return SHG_OK;
+}
+
+int shg_basis_set_centers(shg_basis_t *b, const double *centers)
+{
+    g_err.clear();
+    if (!b || !centers) return fail(SHG_EINVAL, "NULL argument");
+    for (int64_t i = 0; i < 3 * (int64_t)b->d.n_centers; ++i)
+        if (!is_finite_d(centers[i])) return fail(SHG_EINVAL, "center coordinate %lld not finite", (long long)i);
+    std::vector<Vec4> ctr(b->d.n_centers);
+    for (int c = 0; c < b->d.n_centers; ++c) ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+    SHG_CUDA(cudaMemcpy(b->d.centers, ctr.data(), sizeof(Vec4) * b->d.n_centers, cudaMemcpyHostToDevice));
+    return SHG_OK;
+}
+
+void shg_basis_destroy(shg_basis_t *b)
+{
+    if (!b) return;
+    cudaFree(b->d.shells);
+    cudaFree(b->d.prims);
+    cudaFree(b->d.centers);
+    delete[] b->d.h_l;
+    delete[] b->d.h_nprim;
+    delete[] b->d.h_center;
+    delete b;
+}
+
+int64_t shg_basis_nshells(const shg_basis_t *b) { return b ? b->d.n_shells : 0; }
+int64_t shg_basis_nprims(const shg_basis_t *b) { return b ? b->d.n_prims : 0; }
+
+int64_t shg_pair_offsets(const shg_basis_t *b, int64_t n, const int32_t *pa, const int32_t *pb, int64_t *offsets)
+{
+    g_err.clear();
+    if (!b || n < 0 || (n > 0 && (!pa || !pb || !offsets))) return fail(SHG_EINVAL, "bad argument");
+    int64_t tot = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        if (pa[p] < 0 || pa[p] >= b->d.n_shells || pb[p] < 0 || pb[p] >= b->d.n_shells)
+            return fail(SHG_EINVAL, "pair %lld: shell index out of range", (long long)p);
+        offsets[p] = tot;
+        tot += (int64_t)(2 * b->d.h_l[pa[p]] + 1) * (2 * b->d.h_l[pb[p]] + 1);
+    }
+    return tot;
+}
+
+int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta,
+                           const int32_t *tt, const int32_t *tb, int64_t *offsets)
+{
+    g_err.clear();
+    if (!orb || !aux || n < 0 || (n > 0 && (!ta || !tt || !tb || !offsets))) return fail(SHG_EINVAL, "bad argument");
+    int64_t tot = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        if (ta[p] < 0 || ta[p] >= orb->d.n_shells || tt[p] < 0 || tt[p] >= orb->d.n_shells || tb[p] < 0 ||
+            tb[p] >= aux->d.n_shells)
+            return fail(SHG_EINVAL, "triple %lld: shell index out of range", (long long)p);
+        offsets[p] = tot;
+        tot += (int64_t)(2 * orb->d.h_l[ta[p]] + 1) * (2 * orb->d.h_l[tt[p]] + 1) * (2 * aux->d.h_l[tb[p]] + 1);
+    }
+    return tot;
+}
+
+int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int schedule,
+                       void *stream, shg_plan_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(SHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!basis) return fail(SHG_EINVAL, "basis is NULL");
+    if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_pairs %lld out of range", (long long)n);
+    if (n > 0 && (!pa || !pb)) return fail(SHG_EINVAL, "NULL pair list");
+    if (schedule != SHG_SCHED_PER_CLASS && schedule != SHG_SCHED_PERSISTENT)
+        return fail(SHG_EINVAL, "bad schedule %d", schedule);
+    int r = current_device_matches(basis->d.device);
+    if (r) return r;
+    int *ranks[2];
+    if (!device_tables_impl(ranks)) return SHG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const int64_t max_tiles = n / kTile + std::min<int64_t>(n, kNBins) + 1;
+    const size_t bytes_perm = sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1);
+    const size_t bytes_tiles = sizeof(Tile) * (size_t)max_tiles;
+    const size_t bytes_ws = sizeof(int) * ((size_t)n + 4 * (size_t)kNBins + 1);
+    const size_t bytes = bytes_perm + bytes_tiles + 2 * sizeof(int) + bytes_ws + 256;
+    void *blk = nullptr;
+    SHG_CUDA(cudaMallocAsync(&blk, bytes, s));
+
+    shg_plan_t *p = new (std::nothrow) shg_plan_t;
+    if (!p) {
+        cudaFreeAsync(blk, s);
+        return fail(SHG_ENOMEM, "host allocation failed");
+    }
+    PlanDev &d = p->d;
+    d.basis = &basis->d;
+    d.n_pairs = n;
+    d.schedule = schedule;
+    d.pair_a = pa;
+    d.pair_b = pb;
+    d.owner_block = blk;
+    d.stream = s;
+    char *c = (char *)blk;
+    d.tiles = (Tile *)c;                 c += (bytes_tiles + 15) / 16 * 16;
+    d.perm = (int32_t *)c;               c += (bytes_perm + 15) / 16 * 16;
+    d.counter = (int *)c;                c += 16;
+    int *d_err = (int *)c;               c += 16;
+    int *ws = (int *)c;
+
+    auto cleanup = [&](int code) {
+        cudaFreeAsync(blk, s);
+        delete p;
+        return code;
+    };
+    if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) return cleanup(fail(SHG_ECUDA, "memset failed"));
+    cudaError_t e = launch_plan_build(d, ws, kNBins, ranks[schedule], d_err, s);
+    if (e != cudaSuccess) return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(e)));
+    std::vector<int> tile_start(kNBins + 1);
+    int h_err = 0;
+    int *d_tile_start = ws + n + 3 * kNBins;
+    if (cudaMemcpyAsync(tile_start.data(), d_tile_start, sizeof(int) * (kNBins + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(cudaGetLastError())));
+    if (h_err) return cleanup(fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", basis->d.n_shells - 1));
+    d.n_tiles = tile_start[kNBins];
+    for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = tile_start[cls * kKmax * kKmax];
+    if (schedule == SHG_SCHED_PERSISTENT) {
+        p->launches = d.n_tiles > 0 ? 1 : 0;
+    } else {
+        p->launches = 0;
+        for (int cls = 0; cls < kNClass; ++cls) p->launches += d.class_tile_begin[cls + 1] > d.class_tile_begin[cls];
+    }
+    *out = p;
+    return SHG_OK;
+}
+
+int shg_plan_launches(const shg_plan_t *p) { return p ? p->launches : 0; }
+
+void shg_plan_destroy(shg_plan_t *p)
+{
+    if (!p) return;
+    cudaFreeAsync(p->d.owner_block, p->d.stream);
+    delete p;
+}
+
+static int check_op(int op, double omega, int precision)
+{
+    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS) return fail(SHG_EINVAL, "bad operator %d", op);
+    if ((op == SHG_OP_ERF || op == SHG_OP_ERFC || op == SHG_OP_GAUSS) && !(omega > 0 && std::isfinite(omega)))
+        return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
+    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available", precision);
+    return SHG_OK;
+}
+
+int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int precision, const int64_t *off,
+                     double *out, void *stream)
+{
+    g_err.clear();
+    if (!p) return fail(SHG_EINVAL, "plan is NULL");
+    int r = check_op(op, omega, precision);
+    if (r) return r;
+    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
+    if (p->d.n_pairs == 0 || p->d.n_tiles == 0) return SHG_OK;
+    if (!off || !out) return fail(SHG_EINVAL, "NULL output");
+    r = current_device_matches(p->d.basis->device);
+    if (r) return r;
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    Args2c a;
+    a.shells = p->d.basis->shells;
+    a.prims = p->d.basis->prims;
+    a.centers = p->d.basis->centers;
+    a.pair_a = p->d.pair_a;
+    a.pair_b = p->d.pair_b;
+    a.perm = p->d.perm;
+    a.tiles = p->d.tiles;
+    a.out_off = reinterpret_cast<const long long *>(off);
+    a.out = out;
+    a.omega = omega;
+    a.boys = t->boys;
+    a.boys_e = t->boys_e;
+    a.k = consts();
+    if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+        a.tile_begin = 0;
+        a.tile_end = p->d.n_tiles;
+        a.counter = p->d.counter;
+        SHG_CUDA(launch_2c(a, op, precision, persistent_grid_2c(op, precision), true, s));
+    } else {
+        a.counter = nullptr;
+        for (int cls = 0; cls < kNClass; ++cls) {
+            a.tile_begin = p->d.class_tile_begin[cls];
+            a.tile_end = p->d.class_tile_begin[cls + 1];
+            if (a.tile_end <= a.tile_begin) continue;
+            SHG_CUDA(launch_2c(a, op, precision, 0, false, s));
+        }
+    }
+    return SHG_OK;
+}
+
+int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,
+                double screen, int precision, const int64_t *off, double *out, void *stream)
+{
+    g_err.clear();
+    int r = check_op(op, omega, precision);
+    if (r) return r;
+    if (n == 0) return SHG_OK;
+    shg_plan_t *p = nullptr;
+    r = shg_plan_2c_create(basis, n, pa, pb, SHG_SCHED_PERSISTENT, stream, &p);
+    if (r) return r;
+    r = shg_plan_2c_exec(p, op, omega, screen, precision, off, out, stream);
+    shg_plan_destroy(p);
+    return r;
+}
+
+int shg_eval_3c_aab(const shg_basis_t *, const shg_basis_t *, int64_t, const int32_t *, const int32_t *,
+                    const int32_t *, int, double, const int64_t *, double *, void *)
+{
+    return fail(SHG_EINVAL, "shg_eval_3c_aab: not available in this build");
+}
+
+int shg_eval_2c_grad(const shg_basis_t *, int64_t, const int32_t *, const int32_t *, int, double, int,
+                     const int64_t *, const double *, double *, double *, void *)
+{
+    return fail(SHG_EINVAL, "shg_eval_2c_grad: not available in this build");
+}
+
+int shg_eval_3c_aab_grad(const shg_basis_t *, const shg_basis_t *, int64_t, const int32_t *, const int32_t *,
+                         const int32_t *, int, const int64_t *, const double *, double *, double *, void *)
+{
+    return fail(SHG_EINVAL, "shg_eval_3c_aab_grad: not available in this build");
+}
+
+int shg_debug_boys(int64_t n, const double *T, int nmax, double *F, void *stream)
+{
+    g_err.clear();
+    if (n < 0 || nmax < 0 || nmax >= kBoysN) return fail(SHG_EINVAL, "bad n or nmax (nmax <= %d)", kBoysN - 1);
+    if (n == 0) return SHG_OK;
+    if (!T || !F) return fail(SHG_EINVAL, "NULL pointer");
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    SHG_CUDA(launch_debug_boys(n, T, nmax, F, *t, (cudaStream_t)stream));
+    return SHG_OK;
+}
+
+int shg_measure_alu_peak(int kind, int iters, double *flops, void *stream)
+{
+    g_err.clear();
+    if ((kind != 0 && kind != 1) || iters < 1 || !flops) return fail(SHG_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    SHG_CUDA(cudaGetDevice(&dev));
+    SHG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = sms * 8;
+    double *sink = nullptr;
+    SHG_CUDA(cudaMalloc(&sink, 16));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch_alu_probe(kind, iters, blocks, threads, sink, s);   // warm-up
+    cudaEventRecord(e0, s);
+    cudaError_t le = launch_alu_probe(kind, iters, blocks, threads, sink, s);
+    cudaEventRecord(e1, s);
+    cudaError_t se = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (le != cudaSuccess || se != cudaSuccess) return fail(SHG_ECUDA, "probe failed");
+    *flops = 2.0 * 8.0 * (double)iters * threads * (double)blocks / (ms * 1e-3);
+    return SHG_OK;
+}
+
+}  // extern "C"

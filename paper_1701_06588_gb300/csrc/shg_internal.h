@@ -1,0 +1,123 @@
+// Internal declarations shared by the host API (shg_api.cpp) and the CUDA
+// kernels (shg_*.cu).  Plain C++: no device code, no torch types.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace shg {
+
+constexpr int kLmax2c = 6;        // largest l of a two-center shell
+constexpr int kLmaxAabA = 10;     // largest la + la~ of an (aab) triple
+constexpr int kLmaxR = 10;        // largest l of the scaled solid harmonics table
+constexpr int kKmax = 32;         // largest contraction length
+constexpr int kJmax = 7;          // min(la, lb) + 1 <= 7
+constexpr int kNClass = (kLmax2c + 1) * (kLmax2c + 1);
+constexpr int kTile = 32;         // pairs per warp tile
+
+// Boys table: F_{n+t}(T_i)/t!, T_i = i/16, i = 0..kBoysGrid-1, n < kBoysN,
+// t = 0..7; Taylor expansion about the nearest grid point (|delta| <= 1/32).
+constexpr int kBoysGrid = 577;    // covers T < 36
+constexpr double kBoysTmax = 36.0;
+constexpr int kBoysN = 16;        // orders n = 0..15 from the table
+constexpr int kBoysTerms = 8;
+
+// Per-shell record on the device (16 bytes): l, K, first primitive, center.
+struct ShellRec {
+    int l, nprim, prim_off, center;
+};
+
+// Center coordinates on the device (x, y, z, padding), 32-byte aligned.
+struct alignas(32) Vec4 {
+    double x, y, z, w;
+};
+
+// Per-primitive record on the device (32 bytes).
+//   alpha, 1/alpha, w2c = N_l c / (2 alpha)^l (the two-center weight of
+//   Eq. O_rab2_deriv), wN = N_l c (normalised coefficient, used by (aab)).
+struct alignas(32) PrimRec {
+    double alpha, inv_alpha, w2c, wN;
+};
+
+// Small constant tables, passed by value in kernel parameters.
+struct Consts {
+    double A[kLmaxR + 1][kLmaxR + 1];      // A_{l,mu} of Eq. (A)
+    double jB[kJmax][kJmax];               // (2j-1)!! B_{j,kappa}, Eq. (B)
+    double pow2[32];                       // 2^k
+    double dint[64];                       // (double) n
+    double inv_int[192];                   // 1/n (0 for n = 0)
+};
+
+void fill_consts(Consts &k);
+
+// Device-resident tables owned by the library, one set per device.
+struct DeviceTables {
+    const double *boys;   // [kBoysGrid][kBoysN][kBoysTerms]
+    const double *boys_e; // [kBoysGrid] exp(-T_i)
+};
+
+// Returns the tables of the current device (created on first use), or null
+// and sets the error message.
+const DeviceTables *device_tables();
+
+// Host generation of the Boys table (long double arithmetic).
+void make_boys_table(double *tab, double *etab);
+
+struct BasisDev {
+    int n_shells = 0, n_centers = 0;
+    int64_t n_prims = 0;
+    int device = 0;
+    ShellRec *shells = nullptr;   // device
+    PrimRec *prims = nullptr;     // device
+    Vec4 *centers = nullptr;      // device
+    // host copies used for validation and offsets
+    int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
+};
+
+struct Tile {
+    int start, count, la, lb;
+};
+
+struct PlanDev {
+    const BasisDev *basis = nullptr;
+    int64_t n_pairs = 0;
+    int schedule = 0;
+    const int32_t *pair_a = nullptr, *pair_b = nullptr;   // device, caller-owned
+    int32_t *perm = nullptr;       // device [n_pairs], pairs sorted by bin
+    Tile *tiles = nullptr;         // device [n_tiles]
+    int *counter = nullptr;        // device, persistent work counter
+    int n_tiles = 0;
+    int class_tile_begin[kNClass + 1] = {};   // host, per-class tile ranges (class-major)
+    void *owner_block = nullptr;   // device allocation holding all of the above
+    cudaStream_t stream = nullptr;
+};
+
+// Arguments of the two-center kernels (by value).
+struct Args2c {
+    const ShellRec *shells;
+    const PrimRec *prims;
+    const Vec4 *centers;
+    const int32_t *pair_a, *pair_b;
+    const int32_t *perm;
+    const Tile *tiles;
+    int tile_begin, tile_end;
+    int *counter;                 // persistent schedule (null: static)
+    const long long *out_off;
+    double *out;
+    double omega;
+    const double *boys, *boys_e;
+    Consts k;
+};
+
+// Kernel launchers (shg_kernels.cu).
+cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, const int *d_bin_rank,
+                              int *d_err, cudaStream_t s);
+cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
+                      cudaStream_t s);
+int persistent_grid_2c(int op, int precision);
+cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t,
+                              cudaStream_t s);
+cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s);
+
+}  // namespace shg

@@ -1,0 +1,586 @@
+// CUDA kernels of the SHG integral library (sm_103a), FP64 two-center path,
+// planning kernels, Boys debug kernel and the ALU throughput probe.
+//
+// Two-center integrals follow Sec. II B of Golze et al. (arXiv:1701.06588):
+//   (a|O|b) = (-1)^lb A_{la,ma} A_{lb,mb} sum_j 2^{la+lb-j} O^{(la+lb-j)}
+//             (2j-1)!! sum_kappa B_{j,kappa} Q^{c/s,c/s}_{la,|ma|,lb,|mb|,j,kappa}
+// with Q = W_a W_b^T (Eq. Q_matrix), W built from the regular scaled solid
+// harmonics R^{c/s}_{l,m} of the vector R_a - R_b (Sec. II E), and
+// O^{(k)} = sum_{alpha,beta} w_alpha w_beta (d/dR^2)^k (0_a|O|0_b)  (Eq. O_rab2_deriv,
+// Table S1).
+//
+// Work mapping: one thread evaluates one shell pair (radial terms of every
+// primitive pair in registers, then the (2la+1)(2lb+1) block); a warp owns a
+// tile of up to 32 pairs of one (la, lb) class with similar Ka*Kb, so the
+// lanes run the same loop trip counts.
+
+#include "shg_internal.h"
+
+#include <cstdio>
+
+namespace shg {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kPi32 = 5.568327996831707845284817982118835702;      // pi^{3/2}
+constexpr double kTwoPi52 = 34.98683665524972497843742820021;         // 2 pi^{5/2}
+constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
+constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
+
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
+
+// ------------------------------------------------------------------------- //
+// Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
+// T < 36: Taylor expansion of F_kmax about the nearest grid point          //
+//   F_n(T_i + d) = sum_t F_{n+t}(T_i) (-d)^t / t!  (dF_n/dT = -F_{n+1}, SI  //
+//   Eq. 4), exp(-T) = exp(-T_i) exp(-d), then the downward recursion       //
+//   F_{k-1} = (2T F_k + exp(-T)) / (2k-1).                                 //
+// T >= 36: F_0 = sqrt(pi/(4T)) (erf(sqrt T) = 1 to 2e-17) and the upward    //
+//   recursion F_{k+1} = ((2k+1) F_k - exp(-T)) / (2T), stable for T > k.   //
+// ------------------------------------------------------------------------- //
+template <int J>
+__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
+                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+{
+    if (T < kBoysTmax) {
+        const int i = __double2int_rn(T * 16.0);
+        const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
+        const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
+        const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
+        double f = fma(c67.y, y, c67.x);
+        f = fma(f, y, c45.y);
+        f = fma(f, y, c45.x);
+        f = fma(f, y, c23.y);
+        f = fma(f, y, c23.x);
+        f = fma(f, y, c01.y);
+        f = fma(f, y, c01.x);
+        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
+        double e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
+        e = fma(e, y, 1.0 / 120.0);
+        e = fma(e, y, 1.0 / 24.0);
+        e = fma(e, y, 1.0 / 6.0);
+        e = fma(e, y, 0.5);
+        e = fma(e, y, 1.0);
+        e = fma(e, y, 1.0);
+        e *= __ldg(etab + i);
+        F[0] = f;
+        const double twoT = T + T;
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            const int kk = kmax - j + 1;                       // F_{kk-1} from F_kk
+            F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
+        }
+    } else {
+        const double rT = rsqrt(T);
+        const double e = exp(-T);
+        const double h = 0.5 * rT * rT;                        // 1/(2T)
+        double f = kSqrtPiHalf * rT;                           // F_0
+        const int kmin = kmax - J + 1;
+        for (int kk = 0; kk < kmin; ++kk) f = fma(k.dint[2 * kk + 1], f, -e) * h;
+        F[J - 1] = f;
+#pragma unroll
+        for (int t = 1; t < J; ++t) {
+            const int kk = kmin + t - 1;
+            f = fma(k.dint[2 * kk + 1], f, -e) * h;
+            F[J - 1 - t] = f;
+        }
+    }
+}
+
+__device__ __forceinline__ double powi(double x, int n)
+{
+    double p = 1.0;
+    while (n) {
+        if (n & 1) p *= x;
+        x *= x;
+        n >>= 1;
+    }
+    return p;
+}
+
+// ------------------------------------------------------------------------- //
+// Radial terms of one primitive pair, accumulated into the contracted        //
+// O[j] = O^{(kmax-j)}, j = 0..J-1 (Table S1 and Eq. O_rab2_deriv).          //
+//   w = w_alpha w_beta = N_a N_b c_alpha c_beta / ((2alpha)^la (2beta)^lb)  //
+// ------------------------------------------------------------------------- //
+template <int OP, int J>
+__device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec &pb, double R2, int kmax,
+                                                const Args2c &g, double (&O)[J])
+{
+    const int kmin = kmax - J + 1;
+    const double w = pa.w2c * pb.w2c;
+    const double c = pa.alpha + pb.alpha;
+    const double rc = rsqrt(c);
+    const double ic = rc * rc;
+    const double rho = pa.alpha * pb.alpha * ic;
+    const double T = rho * R2;
+    if (OP == OP_OVERLAP) {
+        // (pi/c)^{3/2} exp(-T) (-rho)^k
+        double q = w * kPi32 * ic * rc * exp(-T) * powi(-rho, kmin);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            O[j] += q;
+            q *= -rho;
+        }
+    } else if (OP == OP_GAUSS) {
+        // (pi^2/(c (rho+w)))^{3/2} exp(-w T/(rho+w)) (-w rho/(rho+w))^k
+        const double rd = rsqrt(rho + g.omega);
+        const double id = rd * rd;
+        const double f = -g.omega * rho * id;
+        double q = w * kPi3 * ic * rc * id * rd * exp(-g.omega * T * id) * powi(f, kmin);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            O[j] += q;
+            q *= f;
+        }
+    } else {
+        // Coulomb-type: 2 pi^{5/2} / (alpha beta sqrt(c)) * ...
+        const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
+        if (OP == OP_COULOMB || OP == OP_ERFC) {
+            double F[J];
+            boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, F);
+            double q = pre * powi(-rho, kmin);
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                O[j] += q * F[j];
+                q *= -rho;
+            }
+        }
+        if (OP == OP_ERF || OP == OP_ERFC) {
+            // omega/sqrt(omega^2+rho) (-omega^2 rho/(omega^2+rho))^k F_k(omega^2 T/(omega^2+rho))
+            const double w2 = g.omega * g.omega;
+            const double rw = rsqrt(w2 + rho);
+            const double s = w2 * rw * rw;
+            const double f = -rho * s;
+            double F[J];
+            boys_top<J>(s * T, kmax, g.boys, g.boys_e, g.k, F);
+            double q = pre * g.omega * rw * powi(f, kmin);
+            if (OP == OP_ERFC) q = -q;
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                O[j] += q * F[j];
+                q *= f;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// Regular scaled solid harmonics R^{c/s}_{l,m}(v), 0 <= m <= l <= lmax      //
+// (recursions of Sec. II E), stored at l(l+1)/2 + m.                       //
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ void scaled_harmonics(double x, double y, double z, int lmax, const Consts &k,
+                                                 double *Rc, double *Rs)
+{
+    const double r2 = x * x + y * y + z * z;
+    Rc[0] = 1.0;
+    Rs[0] = 0.0;
+    for (int l = 0; l < lmax; ++l) {
+        const int d0 = l * (l + 1) / 2, d1 = (l + 1) * (l + 2) / 2, dm = (l - 1) * l / 2;
+        const double cll = Rc[d0 + l], sll = Rs[d0 + l];
+        const double inv = k.inv_int[2 * l + 2];
+        Rc[d1 + l + 1] = -(x * cll - y * sll) * inv;
+        Rs[d1 + l + 1] = -(y * cll + x * sll) * inv;
+        const double zl = k.dint[2 * l + 1] * z;
+        for (int m = 0; m <= l; ++m) {
+            const double im = k.inv_int[(l + m + 1) * (l - m + 1)];
+            const double pc = (m <= l - 1) ? Rc[dm + m] : 0.0;
+            const double ps = (m <= l - 1) ? Rs[dm + m] : 0.0;
+            Rc[d1 + m] = (zl * Rc[d0 + m] - r2 * pc) * im;
+            Rs[d1 + m] = (m == 0) ? 0.0 : (zl * Rs[d0 + m] - r2 * ps) * im;
+        }
+    }
+}
+
+// R^c_{L,m} and R^s_{L,m} for any integer m, with R_{L,-m} from the symmetry
+// relations R^c_{l,-m} = (-1)^m R^c_{l,m}, R^s_{l,-m} = -(-1)^m R^s_{l,m}
+// and zero for |m| > L.
+__device__ __forceinline__ double rc_get(const double *Rc, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return 0.0;
+    const double v = Rc[L * (L + 1) / 2 + am];
+    return (m < 0 && (am & 1)) ? -v : v;
+}
+__device__ __forceinline__ double rs_get(const double *Rs, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return 0.0;
+    const double v = Rs[L * (L + 1) / 2 + am];
+    return (m < 0 && !(am & 1)) ? -v : v;
+}
+
+// One row of the translation matrix W_{l,mu,j,kappa} (Sec. II E) for the
+// real function m (cosine part for m >= 0, sine part for m < 0), flattened
+// over e = (j, kappa, z): j^2 + (kappa == 0 ? 0 : 2 kappa - 1 + z).
+// kappa = 0 keeps only the z = c column (the z = s column is exactly zero);
+// the factor (1/2)^{delta_kappa0} cancels the doubled m +- 0 term.
+template <int J>
+__device__ __forceinline__ void w_row(const double *Rc, const double *Rs, int l, int m, double (&w)[J * J])
+{
+    const int mu = m < 0 ? -m : m;
+    const bool sine = m < 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int L = l - j;
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            if (kp == 0) {
+                w[e0] = sine ? rs_get(Rs, L, mu) : rc_get(Rc, L, mu);
+            } else {
+                const double cm = rc_get(Rc, L, mu - kp), cp = rc_get(Rc, L, mu + kp);
+                const double sm = rs_get(Rs, L, mu - kp), sp = rs_get(Rs, L, mu + kp);
+                if (!sine) {
+                    w[e0] = (kp & 1) ? cm - cp : cm + cp;       // W^{cc}
+                    w[e0 + 1] = (kp & 1) ? -sm - sp : sp - sm;   // W^{cs}
+                } else {
+                    w[e0] = (kp & 1) ? sm - sp : sm + sp;        // W^{sc}
+                    w[e0 + 1] = (kp & 1) ? cm + cp : cm - cp;    // W^{ss}
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// One shell pair, FP64.                                                     //
+// ------------------------------------------------------------------------- //
+template <int OP, int J>
+__device__ void pair_2c_fp64(const Args2c &g, int p)
+{
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l;
+    const Vec4 A = g.centers[sa.center];
+    const Vec4 B = g.centers[sb.center];
+    const double vx = A.x - B.x, vy = A.y - B.y, vz = A.z - B.z;
+    const double R2 = vx * vx + vy * vy + vz * vz;
+    const int kmax = la + lb;
+
+    double O[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) O[j] = 0.0;
+    for (int ia = 0; ia < sa.nprim; ++ia) {
+        const PrimRec pa = g.prims[sa.prim_off + ia];
+        for (int ib = 0; ib < sb.nprim; ++ib) {
+            const PrimRec pb = g.prims[sb.prim_off + ib];
+            radial_acc_fp64<OP, J>(pa, pb, R2, kmax, g, O);
+        }
+    }
+
+    // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}, shared by z = c, s
+    double ge[J * J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const double oj = O[j] * g.k.pow2[kmax - j];
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const double v = oj * g.k.jB[j][kp];
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            ge[e0] = v;
+            if (kp) ge[e0 + 1] = v;
+        }
+    }
+
+    double Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics(vx, vy, vz, la > lb ? la : lb, g.k, Rc, Rs);
+
+    const int nb = 2 * lb + 1;
+    double Ub[2 * kLmax2c + 1][J * J];
+    for (int mb = -lb; mb <= lb; ++mb) {
+        double w[J * J];
+        w_row<J>(Rc, Rs, lb, mb, w);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) Ub[mb + lb][e] = w[e];
+    }
+    const double sgn_b = (lb & 1) ? -1.0 : 1.0;
+    double *out = g.out + g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        double ua[J * J];
+        w_row<J>(Rc, Rs, la, ma, ua);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) ua[e] *= ge[e];
+        const double Aa = g.k.A[la][ma < 0 ? -ma : ma] * sgn_b;
+        for (int mb = -lb; mb <= lb; ++mb) {
+            double s = 0.0;
+#pragma unroll
+            for (int e = 0; e < J * J; ++e) s = fma(ua[e], Ub[mb + lb][e], s);
+            out[(ma + la) * nb + (mb + lb)] = Aa * (g.k.A[lb][mb < 0 ? -mb : mb] * s);
+        }
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void pair_2c_fp64_dispatch(const Args2c &g, int p, int J)
+{
+    switch (J) {
+    case 1: pair_2c_fp64<OP, 1>(g, p); break;
+    case 2: pair_2c_fp64<OP, 2>(g, p); break;
+    case 3: pair_2c_fp64<OP, 3>(g, p); break;
+    case 4: pair_2c_fp64<OP, 4>(g, p); break;
+    case 5: pair_2c_fp64<OP, 5>(g, p); break;
+    case 6: pair_2c_fp64<OP, 6>(g, p); break;
+    default: pair_2c_fp64<OP, 7>(g, p); break;
+    }
+}
+
+__device__ __forceinline__ void run_tile_fp64(const Args2c &g, int op, const Tile &t, int lane)
+{
+    if (lane >= t.count) return;
+    const int p = g.perm[t.start + lane];
+    const int J = (t.la < t.lb ? t.la : t.lb) + 1;
+    switch (op) {
+    case OP_OVERLAP: pair_2c_fp64_dispatch<OP_OVERLAP>(g, p, J); break;
+    case OP_COULOMB: pair_2c_fp64_dispatch<OP_COULOMB>(g, p, J); break;
+    case OP_ERFC: pair_2c_fp64_dispatch<OP_ERFC>(g, p, J); break;
+    case OP_ERF: pair_2c_fp64_dispatch<OP_ERF>(g, p, J); break;
+    default: pair_2c_fp64_dispatch<OP_GAUSS>(g, p, J); break;
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_2c_fp64_static(const Args2c g)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = g.tile_begin + warp;
+    if (t >= g.tile_end) return;
+    run_tile_fp64(g, OP, g.tiles[t], lane);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_2c_fp64_persistent(const Args2c g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        run_tile_fp64(g, OP, g.tiles[t], lane);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// Planning: counting sort of pairs into (class, Ka*Kb) bins, bins visited in //
+// a schedule-specific rank order, then class-pure tiles of <= 32 pairs.     //
+// ------------------------------------------------------------------------- //
+__global__ void k_classify(int64_t n, const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
+                           const ShellRec *__restrict__ shells, int n_shells, const int *__restrict__ bin_rank,
+                           int *__restrict__ key, int *__restrict__ hist, int *__restrict__ err)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int a = pa[p], b = pb[p];
+        int r = 0;
+        if (a < 0 || a >= n_shells || b < 0 || b >= n_shells) {
+            atomicOr(err, 1);
+        } else {
+            const ShellRec sa = shells[a], sb = shells[b];
+            const int cls = sa.l * (kLmax2c + 1) + sb.l;
+            const int kk = sa.nprim * sb.nprim;
+            r = bin_rank[cls * kKmax * kKmax + (kk - 1)];
+        }
+        key[p] = r;
+        atomicAdd(hist + r, 1);
+    }
+}
+
+// single block: exclusive scans of hist and of ceil(hist/32); tile_start[n_bins] = total
+__global__ void k_scan_bins(int n_bins, const int *__restrict__ hist, int *__restrict__ bin_start,
+                            int *__restrict__ cursor, int *__restrict__ tile_start)
+{
+    __shared__ long long s_cnt[1024], s_til[1024];
+    const int per = (n_bins + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    long long c = 0, t = 0;
+    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
+        c += hist[i];
+        t += (hist[i] + kTile - 1) / kTile;
+    }
+    s_cnt[threadIdx.x] = c;
+    s_til[threadIdx.x] = t;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        long long vc = 0, vt = 0;
+        if (threadIdx.x >= off) {
+            vc = s_cnt[threadIdx.x - off];
+            vt = s_til[threadIdx.x - off];
+        }
+        __syncthreads();
+        s_cnt[threadIdx.x] += vc;
+        s_til[threadIdx.x] += vt;
+        __syncthreads();
+    }
+    long long rc = s_cnt[threadIdx.x] - c, rt = s_til[threadIdx.x] - t;
+    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
+        bin_start[i] = (int)rc;
+        cursor[i] = (int)rc;
+        tile_start[i] = (int)rt;
+        rc += hist[i];
+        rt += (hist[i] + kTile - 1) / kTile;
+    }
+    if (threadIdx.x == blockDim.x - 1) tile_start[n_bins] = (int)s_til[blockDim.x - 1];
+}
+
+__global__ void k_scatter(int64_t n, const int *__restrict__ key, int *__restrict__ cursor, int32_t *__restrict__ perm)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(cursor + key[p], 1);
+        perm[pos] = (int32_t)p;
+    }
+}
+
+__global__ void k_make_tiles(int n_bins, const int *__restrict__ hist, const int *__restrict__ bin_start,
+                             const int *__restrict__ tile_start, const int *__restrict__ rank_to_bin,
+                             Tile *__restrict__ tiles)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_bins; r += gridDim.x * blockDim.x) {
+        const int c = hist[r];
+        if (!c) continue;
+        const int bin = rank_to_bin[r];
+        const int cls = bin / (kKmax * kKmax);
+        const int la = cls / (kLmax2c + 1), lb = cls % (kLmax2c + 1);
+        const int nt = (c + kTile - 1) / kTile;
+        for (int t = 0; t < nt; ++t) {
+            Tile tl;
+            tl.start = bin_start[r] + t * kTile;
+            tl.count = (c - t * kTile) < kTile ? (c - t * kTile) : kTile;
+            tl.la = la;
+            tl.lb = lb;
+            tiles[tile_start[r] + t] = tl;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// Debug: Boys values through the device code path.                          //
+// ------------------------------------------------------------------------- //
+__global__ void k_debug_boys(int64_t n, const double *__restrict__ T, int nmax, double *__restrict__ F,
+                             const double *tab, const double *etab, const Consts k)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double f[kBoysN];
+        boys_top<kBoysN>(T[i], kBoysN - 1, tab, etab, k, f);
+        for (int m = 0; m <= nmax; ++m) F[i * (nmax + 1) + m] = f[kBoysN - 1 - m];
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// ALU throughput probe: 8 independent FMA chains per thread.                //
+// ------------------------------------------------------------------------- //
+template <typename T>
+__global__ void __launch_bounds__(256) k_alu_probe(int iters, T *sink)
+{
+    T a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (T)(threadIdx.x + i) * (T)1e-3;
+    const T b = (T)0.999999, c = (T)1e-6;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == (T)-12345.0) sink[0] = s;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- //
+// Launchers                                                                 //
+// ------------------------------------------------------------------------- //
+cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d_bin_rank, int *d_err,
+                              cudaStream_t s)
+{
+    // d_ws layout: key[n] | hist[n_bins] | bin_start[n_bins] | cursor[n_bins] | tile_start[n_bins+1]
+    // d_bin_rank: bin_rank[n_bins] followed by rank_to_bin[n_bins]
+    const int64_t n = plan.n_pairs;
+    int *key = d_ws;
+    int *hist = key + n;
+    int *bin_start = hist + n_bins;
+    int *cursor = bin_start + n_bins;
+    int *tile_start = cursor + n_bins;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * n_bins, s);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const int blocks = (int)((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
+    if (n > 0) {
+        k_classify<<<blocks, threads, 0, s>>>(n, plan.pair_a, plan.pair_b, plan.basis->shells, plan.basis->n_shells,
+                                              d_bin_rank, key, hist, d_err);
+    }
+    k_scan_bins<<<1, 1024, 0, s>>>(n_bins, hist, bin_start, cursor, tile_start);
+    if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, key, cursor, plan.perm);
+    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, hist, bin_start, tile_start, d_bin_rank + n_bins,
+                                                       plan.tiles);
+    return cudaGetLastError();
+}
+
+template <int OP>
+static cudaError_t launch_2c_op(const Args2c &a, int n, bool persistent, cudaStream_t s)
+{
+    if (persistent) {
+        k_2c_fp64_persistent<OP><<<n, 128, 0, s>>>(a);
+    } else {
+        const int tiles = a.tile_end - a.tile_begin;
+        if (tiles <= 0) return cudaSuccess;
+        k_2c_fp64_static<OP><<<(tiles + 3) / 4, 128, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persistent, cudaStream_t s)
+{
+    (void)precision;
+    switch (op) {
+    case OP_OVERLAP: return launch_2c_op<OP_OVERLAP>(a, n, persistent, s);
+    case OP_COULOMB: return launch_2c_op<OP_COULOMB>(a, n, persistent, s);
+    case OP_ERFC: return launch_2c_op<OP_ERFC>(a, n, persistent, s);
+    case OP_ERF: return launch_2c_op<OP_ERF>(a, n, persistent, s);
+    case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, persistent, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int persistent_grid_2c(int op, int precision)
+{
+    (void)precision;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    switch (op) {
+    case OP_OVERLAP: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_OVERLAP>, 128, 0); break;
+    case OP_COULOMB: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_COULOMB>, 128, 0); break;
+    case OP_ERFC: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERFC>, 128, 0); break;
+    case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, 128, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, 128, 0); break;
+    }
+    if (e != cudaSuccess || per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    return sms * per;
+}
+
+cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t, cudaStream_t s)
+{
+    Consts k;
+    fill_consts(k);
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096);
+    k_debug_boys<<<blocks, 128, 0, s>>>(n, T, nmax, F, t.boys, t.boys_e, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s)
+{
+    if (kind == 0)
+        k_alu_probe<double><<<blocks, threads, 0, s>>>(iters, sink);
+    else
+        k_alu_probe<float><<<blocks, threads, 0, s>>>(iters, reinterpret_cast<float *>(sink));
+    return cudaGetLastError();
+}
+
+}  // namespace shg

@@ -1,0 +1,31 @@
+"""Count model against the paper's printed Table II, and sanity of the flop model."""
+import json
+import os
+
+import numpy as np
+
+from paper_1701_06588_gb300 import counts
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_table2_contracted_element_counts():
+    g = json.load(open(os.path.join(HERE, "golden", "table2_contracted_elements.json")))
+    for name, spec in g["bases"].items():
+        for col, grad in (("Int.", False), ("Int.+Dev.", True)):
+            shg = counts.shg_contracted_elements(spec["l"], spec["l"], spec["K"], spec["K"], grad)
+            os_ = counts.os_contracted_elements(spec["l"], spec["l"], spec["K"], spec["K"], grad)
+            assert shg == g["values"]["SHG"][name][col], (name, col, shg)
+            assert os_ == g["values"]["OS"][name][col], (name, col, os_)
+
+
+def test_flop_model_monotone_and_positive():
+    for op in range(5):
+        f = counts.pair_flops(np.array([0, 1, 2, 4, 6]), np.array([0, 1, 2, 4, 6]), np.ones(5), np.ones(5), op)
+        assert np.all(f > 0) and np.all(np.diff(f) > 0)
+        g = counts.pair_flops(np.full(4, 2), np.full(4, 3), np.array([1, 2, 4, 8]), np.array([1, 2, 4, 8]), op)
+        assert np.all(np.diff(g) > 0)
+    # erfc costs the Coulomb and the erf radial parts together
+    a = counts.pair_flops(3, 2, 5, 5, counts.OP_ERFC)
+    assert a > counts.pair_flops(3, 2, 5, 5, counts.OP_COULOMB)
+    assert a > counts.pair_flops(3, 2, 5, 5, counts.OP_ERF)

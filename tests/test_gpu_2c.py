@@ -1,0 +1,169 @@
+"""GPU parity of the two-center SHG path (C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_06588_gb300 import workloads as W
+from tests.parity import TOL_FP64, assert_parity, reference_2c
+
+pytestmark = pytest.mark.gpu
+
+OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+_REF = {}
+
+
+def _oracle(name, n, op, omega):
+    """Oracle blocks of a named workload, computed once per module."""
+    key = (name, n, op, omega)
+    if key not in _REF:
+        sh, pa, pb = W.make(name, n=n)
+        _REF[key] = reference_2c(sh, pa, pb, op, omega)
+    return _REF[key]
+
+
+@pytest.fixture(scope="module")
+def shg():
+    import torch
+    from paper_1701_06588_gb300 import api, build
+    build.build()
+    torch.cuda.init()
+    return api
+
+
+def _run(api, shells, pa, pb, opname, omega, schedule="persistent", precision="fp64"):
+    import torch
+    b = api.Basis(shells)
+    off, total = b.pair_offsets(pa, pb)
+    plan = api.Plan2c(b, pa, pb, schedule=schedule)
+    out = torch.full((max(total, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    plan.exec(opname, torch.from_numpy(off).cuda(), out, omega=omega, precision=precision)
+    torch.cuda.synchronize()
+    res = out[:total].cpu().numpy()
+    plan.close()
+    b.close()
+    return res
+
+
+@pytest.mark.parametrize("opname,op,omega", OPS)
+@pytest.mark.parametrize("schedule", ["per_class", "persistent"])
+def test_c1_full(shg, opname, op, omega, schedule):
+    """2,000 pairs, l <= 3, K = 4 (the small configuration), every element."""
+    sh, pa, pb = W.make("c1_2k_l3_k4")
+    got = _run(shg, sh, pa, pb, opname, omega, schedule)
+    ref, scale = _oracle("c1_2k_l3_k4", None, op, omega)
+    assert_parity(got, ref, TOL_FP64, "c1 %s %s" % (opname, schedule), scale)
+
+
+@pytest.mark.parametrize("opname,op,omega", OPS)
+def test_c2_subset(shg, opname, op, omega):
+    """First 3,000 pairs of the 200k workload recipe (l <= 4, K 1..8): spans
+    every class, many tiles and ragged tile tails."""
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=3000)
+    got = _run(shg, sh, pa, pb, opname, omega)
+    ref, scale = reference_2c(sh, pa, pb, op, omega)
+    assert_parity(got, ref, TOL_FP64, "c2 %s" % opname, scale)
+
+
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+def test_c3_subset_high_l_long_contractions(shg, opname, op, omega):
+    """l up to 6, K up to 20, exponents to 5000."""
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=1500)
+    got = _run(shg, sh, pa, pb, opname, omega)
+    ref, scale = reference_2c(sh, pa, pb, op, omega)
+    assert_parity(got, ref, TOL_FP64, "c3 %s" % opname, scale)
+
+
+def test_full_size_c2_sampled(shg):
+    """The full 200k-pair workload in the benchmark's launch configuration;
+    400 sampled pairs checked element by element against the oracle."""
+    import torch
+    sh, pa, pb = W.make("c2_200k_l4_k8")
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    plan = shg.Plan2c(b, pa, pb, schedule="persistent")
+    d_off = torch.from_numpy(off).cuda()
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(len(pa), 400, replace=False))
+    sub, spa, spb = W.subset_pairs(sh, pa, pb, idx)
+    for opname, op, omega in OPS:
+        out = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+        plan.exec(opname, d_off, out, omega=omega)
+        torch.cuda.synchronize()
+        res = out.cpu().numpy()
+        assert np.all(np.isfinite(res)), opname
+        got = np.concatenate([res[off[p]:off[p] + (2 * sh["l"][pa[p]] + 1) * (2 * sh["l"][pb[p]] + 1)] for p in idx])
+        ref, scale = reference_2c(sub, spa, spb, op, omega)
+        assert_parity(got, ref, TOL_FP64, "c2 full-size sampled %s" % opname, scale)
+    plan.close()
+    b.close()
+
+
+def test_edge_cases(shg):
+    import torch
+    # empty pair list
+    sh, pa, pb = W.make("c1_2k_l3_k4", n=5)
+    b = shg.Basis(sh)
+    out, off = shg.eval_2c(b, pa[:0], pb[:0], "coulomb")
+    assert out.numel() == 0
+    # one pair, both shells on one center (R = 0), every l combination up to 6, K = 1 and K = 20
+    rng = np.random.default_rng(5)
+    ls, ks = [], []
+    for la in range(7):
+        for lb in range(7):
+            ls += [la, lb]
+    n = len(ls) // 2
+    for K in (1, 20):
+        nprim = np.full(2 * n, K, np.int32)
+        shells = dict(l=np.array(ls, np.int32), nprim=nprim, exps=np.exp(rng.uniform(np.log(0.05), np.log(500), 2 * n * K)),
+                      coefs=rng.uniform(-1, 1, 2 * n * K), centers=np.zeros((1, 3)),
+                      center_of=np.zeros(2 * n, np.int32))
+        pa = np.arange(0, 2 * n, 2, dtype=np.int32)
+        pb = pa + 1
+        for opname, op, omega in OPS:
+            got = _run(shg, shells, pa, pb, opname, omega)
+            ref, scale = reference_2c(shells, pa, pb, op, omega)
+            assert_parity(got, ref, TOL_FP64, "R=0 K=%d %s" % (K, opname), scale)
+    # a pair of one shell with itself, and a pair list with repeated pairs
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=40)
+    pa2 = np.r_[pa, pa[:7], pb[:3]].astype(np.int32)
+    pb2 = np.r_[pb, pb[:7], pb[:3]].astype(np.int32)
+    got = _run(shg, sh, pa2, pb2, "overlap", 0.0)
+    ref, scale = reference_2c(sh, pa2, pb2, 0, 0.0)
+    assert_parity(got, ref, TOL_FP64, "repeated pairs", scale)
+    b.close()
+
+
+def test_errors_are_reported(shg):
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    sh, pa, pb = W.make("c1_2k_l3_k4", n=4)
+    b = shg.Basis(sh)
+    bad = torch.tensor([0, 1, 2, 10_000], dtype=torch.int32, device="cuda")
+    good = torch.tensor([0, 1, 2, 3], dtype=torch.int32, device="cuda")
+    with pytest.raises(L.ShgError) as e:
+        shg.Plan2c(b, bad, good)
+    assert e.value.code == L.SHG_EINVAL
+    plan = shg.Plan2c(b, good, good)
+    out = torch.zeros(100, dtype=torch.float64, device="cuda")
+    off = torch.zeros(4, dtype=torch.int64, device="cuda")
+    for op, om in [("erf", 0.0), ("gauss", -1.0), (7, 1.0)]:
+        with pytest.raises(L.ShgError):
+            plan.exec(op, off, out, omega=om)
+    plan.close()
+    b.close()
+
+
+def test_device_boys_against_oracle(shg):
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    T = np.concatenate([[0.0, 1e-12, 1e-3], np.linspace(0, 40, 3001), np.exp(np.linspace(np.log(30), np.log(800), 300)),
+                        np.array([35.999999, 36.0, 36.000001])])
+    dT = torch.from_numpy(T).cuda()
+    nmax = 15
+    dF = torch.empty(len(T) * (nmax + 1), dtype=torch.float64, device="cuda")
+    L.shg_debug_boys(len(T), dT, nmax, dF, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    F = dF.cpu().numpy().reshape(len(T), nmax + 1)
+    ref = np.stack([oracle.boys(nmax, t) for t in T])
+    rel = np.abs(F - ref) / ref
+    assert rel.max() < 4e-15, rel.max()
