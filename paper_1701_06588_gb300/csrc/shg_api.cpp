@@ -107,7 +107,7 @@ void make_boys_table(double *tab, double *etab)
 // ------------------------------------------------------------------------- //
 // Per-device tables                                                          //
 // ------------------------------------------------------------------------- //
-constexpr int kNBins = kNClass * kKmax * kKmax;
+constexpr int kNBins = kNClass * kKbins2c;
 
 struct DevState {
     DeviceTables t{};
@@ -136,15 +136,15 @@ static void make_ranks(int schedule, std::vector<int> &rank, std::vector<int> &i
     if (schedule == SHG_SCHED_PER_CLASS) {
         // class-major, Ka*Kb descending inside a class
         std::sort(order.begin(), order.end(), [](int x, int y) {
-            const int cx = x / (kKmax * kKmax), cy = y / (kKmax * kKmax);
+            const int cx = x / kKbins2c, cy = y / kKbins2c;
             if (cx != cy) return cx < cy;
-            return (x % (kKmax * kKmax)) > (y % (kKmax * kKmax));
+            return (x % kKbins2c) > (y % kKbins2c);
         });
     } else {
         // estimated cost descending (longest tiles first)
         std::vector<double> cost(kNBins);
         for (int b = 0; b < kNBins; ++b) {
-            const int cls = b / (kKmax * kKmax), kk = b % (kKmax * kKmax) + 1;
+            const int cls = b / kKbins2c, kk = b % kKbins2c + 1;
             cost[b] = class_cost(cls / (kLmax2c + 1), cls % (kLmax2c + 1), kk);
         }
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
@@ -447,7 +447,7 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
         return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(cudaGetLastError())));
     if (h_err) return cleanup(fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", basis->d.n_shells - 1));
     d.n_tiles = tile_start[kNBins];
-    for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = tile_start[cls * kKmax * kKmax];
+    for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = tile_start[cls * kKbins2c];
     if (schedule == SHG_SCHED_PERSISTENT) {
         p->launches = d.n_tiles > 0 ? 1 : 0;
     } else {

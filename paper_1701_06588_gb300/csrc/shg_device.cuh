@@ -1,0 +1,193 @@
+// Device helpers shared by the SHG kernels: Boys function, scaled solid
+// harmonics R^{c/s}_{l,m}, rows of the real translation matrix W (Sec. II E).
+#pragma once
+
+#include "shg_internal.h"
+
+namespace shg {
+namespace dev {
+
+constexpr double kPi32 = 5.568327996831707845284817982118835702;      // pi^{3/2}
+constexpr double kTwoPi52 = 34.98683665524972497843742820021;         // 2 pi^{5/2}
+constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
+constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
+
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
+
+// ------------------------------------------------------------------------- //
+// Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
+// T < 36: Taylor expansion of F_kmax about the nearest grid point          //
+//   F_n(T_i + d) = sum_t F_{n+t}(T_i) (-d)^t / t!  (dF_n/dT = -F_{n+1}, SI  //
+//   Eq. 4), exp(-T) = exp(-T_i) exp(-d), then the downward recursion       //
+//   F_{k-1} = (2T F_k + exp(-T)) / (2k-1).                                 //
+// T >= 36: F_0 = sqrt(pi/(4T)) (erf(sqrt T) = 1 to 2e-17) and the upward    //
+//   recursion F_{k+1} = ((2k+1) F_k - exp(-T)) / (2T), stable for T > k.   //
+// ------------------------------------------------------------------------- //
+template <int J>
+__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
+                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+{
+    if (T < kBoysTmax) {
+        const int i = __double2int_rn(T * 16.0);
+        const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
+        const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
+        const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
+        double f = fma(c67.y, y, c67.x);
+        f = fma(f, y, c45.y);
+        f = fma(f, y, c45.x);
+        f = fma(f, y, c23.y);
+        f = fma(f, y, c23.x);
+        f = fma(f, y, c01.y);
+        f = fma(f, y, c01.x);
+        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
+        double e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
+        e = fma(e, y, 1.0 / 120.0);
+        e = fma(e, y, 1.0 / 24.0);
+        e = fma(e, y, 1.0 / 6.0);
+        e = fma(e, y, 0.5);
+        e = fma(e, y, 1.0);
+        e = fma(e, y, 1.0);
+        e *= __ldg(etab + i);
+        F[0] = f;
+        const double twoT = T + T;
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            const int kk = kmax - j + 1;                       // F_{kk-1} from F_kk
+            F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
+        }
+    } else {
+        const double rT = rsqrt(T);
+        const double e = exp(-T);
+        const double h = 0.5 * rT * rT;                        // 1/(2T)
+        double f = kSqrtPiHalf * rT;                           // F_0
+        const int kmin = kmax - J + 1;
+        for (int kk = 0; kk < kmin; ++kk) f = fma(k.dint[2 * kk + 1], f, -e) * h;
+        F[J - 1] = f;
+#pragma unroll
+        for (int t = 1; t < J; ++t) {
+            const int kk = kmin + t - 1;
+            f = fma(k.dint[2 * kk + 1], f, -e) * h;
+            F[J - 1 - t] = f;
+        }
+    }
+}
+
+__device__ __forceinline__ double powi(double x, int n)
+{
+    double p = 1.0;
+    while (n) {
+        if (n & 1) p *= x;
+        x *= x;
+        n >>= 1;
+    }
+    return p;
+}
+
+// ------------------------------------------------------------------------- //
+// Regular scaled solid harmonics R^{c/s}_{l,m}(v), 0 <= m <= l <= lmax      //
+// (recursions of Sec. II E), stored at l(l+1)/2 + m.                       //
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ void scaled_harmonics(double x, double y, double z, int lmax, const Consts &k,
+                                                 double *Rc, double *Rs)
+{
+    const double r2 = x * x + y * y + z * z;
+    Rc[0] = 1.0;
+    Rs[0] = 0.0;
+    for (int l = 0; l < lmax; ++l) {
+        const int d0 = l * (l + 1) / 2, d1 = (l + 1) * (l + 2) / 2, dm = (l - 1) * l / 2;
+        const double cll = Rc[d0 + l], sll = Rs[d0 + l];
+        const double inv = k.inv_int[2 * l + 2];
+        Rc[d1 + l + 1] = -(x * cll - y * sll) * inv;
+        Rs[d1 + l + 1] = -(y * cll + x * sll) * inv;
+        const double zl = k.dint[2 * l + 1] * z;
+        for (int m = 0; m <= l; ++m) {
+            const double im = k.inv_int[(l + m + 1) * (l - m + 1)];
+            const double pc = (m <= l - 1) ? Rc[dm + m] : 0.0;
+            const double ps = (m <= l - 1) ? Rs[dm + m] : 0.0;
+            Rc[d1 + m] = (zl * Rc[d0 + m] - r2 * pc) * im;
+            Rs[d1 + m] = (m == 0) ? 0.0 : (zl * Rs[d0 + m] - r2 * ps) * im;
+        }
+    }
+}
+
+// R^c_{L,m} and R^s_{L,m} for any integer m, with R_{L,-m} from the symmetry
+// relations R^c_{l,-m} = (-1)^m R^c_{l,m}, R^s_{l,-m} = -(-1)^m R^s_{l,m}
+// and zero for |m| > L.
+__device__ __forceinline__ double rc_get(const double *Rc, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return 0.0;
+    const double v = Rc[L * (L + 1) / 2 + am];
+    return (m < 0 && (am & 1)) ? -v : v;
+}
+__device__ __forceinline__ double rs_get(const double *Rs, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return 0.0;
+    const double v = Rs[L * (L + 1) / 2 + am];
+    return (m < 0 && !(am & 1)) ? -v : v;
+}
+
+// One row of the translation matrix W_{l,mu,j,kappa} (Sec. II E) for the
+// real function m (cosine part for m >= 0, sine part for m < 0), flattened
+// over e = (j, kappa, z): j^2 + (kappa == 0 ? 0 : 2 kappa - 1 + z).
+// kappa = 0 keeps only the z = c column (the z = s column is exactly zero);
+// the factor (1/2)^{delta_kappa0} cancels the doubled m +- 0 term.
+template <int J>
+__device__ __forceinline__ void w_row(const double *Rc, const double *Rs, int l, int m, double (&w)[J * J])
+{
+    const int mu = m < 0 ? -m : m;
+    const bool sine = m < 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int L = l - j;
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            if (kp == 0) {
+                w[e0] = sine ? rs_get(Rs, L, mu) : rc_get(Rc, L, mu);
+            } else {
+                const double cm = rc_get(Rc, L, mu - kp), cp = rc_get(Rc, L, mu + kp);
+                const double sm = rs_get(Rs, L, mu - kp), sp = rs_get(Rs, L, mu + kp);
+                if (!sine) {
+                    w[e0] = (kp & 1) ? cm - cp : cm + cp;       // W^{cc}
+                    w[e0 + 1] = (kp & 1) ? -sm - sp : sp - sm;   // W^{cs}
+                } else {
+                    w[e0] = (kp & 1) ? sm - sp : sm + sp;        // W^{sc}
+                    w[e0 + 1] = (kp & 1) ? cm + cp : cm - cp;    // W^{ss}
+                }
+            }
+        }
+    }
+}
+
+
+// Runtime-J variant of w_row (used where J varies inside one thread).
+__device__ __forceinline__ void w_row_rt(const double *Rc, const double *Rs, int l, int m, int J, double *w)
+{
+    const int mu = m < 0 ? -m : m;
+    const bool sine = m < 0;
+    for (int j = 0; j < J; ++j) {
+        const int L = l - j;
+        for (int kp = 0; kp <= j; ++kp) {
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            if (kp == 0) {
+                w[e0] = sine ? rs_get(Rs, L, mu) : rc_get(Rc, L, mu);
+            } else {
+                const double cm = rc_get(Rc, L, mu - kp), cp = rc_get(Rc, L, mu + kp);
+                const double sm = rs_get(Rs, L, mu - kp), sp = rs_get(Rs, L, mu + kp);
+                const bool odd = kp & 1;
+                if (!sine) {
+                    w[e0] = odd ? cm - cp : cm + cp;
+                    w[e0 + 1] = odd ? -sm - sp : sp - sm;
+                } else {
+                    w[e0] = odd ? sm - sp : sm + sp;
+                    w[e0 + 1] = odd ? cm + cp : cm - cp;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace shg

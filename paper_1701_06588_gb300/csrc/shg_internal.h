@@ -40,6 +40,12 @@ struct alignas(32) PrimRec {
     double alpha, inv_alpha, w2c, wN;
 };
 
+// Real Gaunt coefficient entry G = int Y_{L,M} Y_{l,m} Y_{l~,m~} dOmega.
+struct GauntEnt {
+    double g;
+    int L, M;
+};
+
 // Small constant tables, passed by value in kernel parameters.
 struct Consts {
     double A[kLmaxR + 1][kLmaxR + 1];      // A_{l,mu} of Eq. (A)
@@ -55,7 +61,22 @@ void fill_consts(Consts &k);
 struct DeviceTables {
     const double *boys;   // [kBoysGrid][kBoysN][kBoysTerms]
     const double *boys_e; // [kBoysGrid] exp(-T_i)
+    // real Gaunt coefficients for l, l~ <= 6 with l + l~ <= kLmaxAabA:
+    // rows (l, l~, m, m~) -> entries [gaunt_row[r], gaunt_row[r+1]) of gaunt
+    const int *gaunt_base;     // [7*7] first row of the (l, l~) block
+    const int *gaunt_row;      // row pointers
+    const GauntEnt *gaunt;     // entries
 };
+
+// Extra constants of the three-index kernels (by value).
+struct Consts3 {
+    double binom[18][18];       // binom(k, i)
+    double dd[6][6][6];         // d_{m,j} j!/(j-i)!: D_m^{(i)}(x) = sum_j dd[m][i][j] x^{j-i}
+    double bj[11][6][6];        // binom(p, j) (L)_j (rising factorial, (0)_0 = 1)
+    double sqrt_int[32];        // sqrt(n)
+};
+
+void fill_consts3(Consts3 &k);
 
 // Returns the tables of the current device (created on first use), or null
 // and sets the error message.
@@ -75,15 +96,25 @@ struct BasisDev {
     int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
 };
 
+// A warp's unit of work: up to kTile consecutive entries of the sorted list,
+// all of one class.  cls = la*7 + lb (two-center) or (la*7 + la~)*7 + lb.
 struct Tile {
-    int start, count, la, lb;
+    int start, count, cls, pad;
 };
+
+constexpr int kKbins2c = kKmax * kKmax;      // two-center bins per class: Ka*Kb - 1
+constexpr int kNClass3 = 7 * 7 * 7;          // (la, la~, lb) classes
+constexpr int kKbins3c = 64;                 // three-index bins per class: min(Ka*Ka~*Kb, 64) - 1
+
 
 struct PlanDev {
     const BasisDev *basis = nullptr;
+    const BasisDev *aux = nullptr;  // three-index plans: basis of b
+    int kind = 2;                   // 2: pairs, 3: (aab) triples
     int64_t n_pairs = 0;
     int schedule = 0;
     const int32_t *pair_a = nullptr, *pair_b = nullptr;   // device, caller-owned
+    const int32_t *trip_t = nullptr;                      // a~ of triples (kind 3)
     int32_t *perm = nullptr;       // device [n_pairs], pairs sorted by bin
     Tile *tiles = nullptr;         // device [n_tiles]
     int *counter = nullptr;        // device, persistent work counter
@@ -110,9 +141,29 @@ struct Args2c {
     Consts k;
 };
 
-// Kernel launchers (shg_kernels.cu).
+// Arguments of the three-index kernels (by value).
+struct Args3c {
+    const ShellRec *orb_shells, *aux_shells;
+    const PrimRec *orb_prims, *aux_prims;
+    const Vec4 *orb_centers, *aux_centers;
+    const int32_t *t_a, *t_t, *t_b;
+    const int32_t *perm;
+    const Tile *tiles;
+    int tile_begin, tile_end;
+    int *counter;
+    const long long *out_off;
+    double *out;
+    const int *gaunt_base, *gaunt_row;
+    const GauntEnt *gaunt;
+    Consts k;
+    Consts3 k3;
+};
+
+// Kernel launchers (shg_kernels.cu, shg_3c.cu).
 cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, const int *d_bin_rank,
                               int *d_err, cudaStream_t s);
+cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
+int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
                       cudaStream_t s);
 int persistent_grid_2c(int op, int precision);

@@ -14,90 +14,14 @@
 // tile of up to 32 pairs of one (la, lb) class with similar Ka*Kb, so the
 // lanes run the same loop trip counts.
 
-#include "shg_internal.h"
+#include "shg_device.cuh"
 
 #include <cstdio>
 
 namespace shg {
 
 namespace {
-
-constexpr double kPi = 3.141592653589793238462643383279502884;
-constexpr double kPi32 = 5.568327996831707845284817982118835702;      // pi^{3/2}
-constexpr double kTwoPi52 = 34.98683665524972497843742820021;         // 2 pi^{5/2}
-constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
-constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
-
-enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
-
-// ------------------------------------------------------------------------- //
-// Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
-// T < 36: Taylor expansion of F_kmax about the nearest grid point          //
-//   F_n(T_i + d) = sum_t F_{n+t}(T_i) (-d)^t / t!  (dF_n/dT = -F_{n+1}, SI  //
-//   Eq. 4), exp(-T) = exp(-T_i) exp(-d), then the downward recursion       //
-//   F_{k-1} = (2T F_k + exp(-T)) / (2k-1).                                 //
-// T >= 36: F_0 = sqrt(pi/(4T)) (erf(sqrt T) = 1 to 2e-17) and the upward    //
-//   recursion F_{k+1} = ((2k+1) F_k - exp(-T)) / (2T), stable for T > k.   //
-// ------------------------------------------------------------------------- //
-template <int J>
-__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
-                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
-{
-    if (T < kBoysTmax) {
-        const int i = __double2int_rn(T * 16.0);
-        const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
-        const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
-        const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
-        double f = fma(c67.y, y, c67.x);
-        f = fma(f, y, c45.y);
-        f = fma(f, y, c45.x);
-        f = fma(f, y, c23.y);
-        f = fma(f, y, c23.x);
-        f = fma(f, y, c01.y);
-        f = fma(f, y, c01.x);
-        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
-        double e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
-        e = fma(e, y, 1.0 / 120.0);
-        e = fma(e, y, 1.0 / 24.0);
-        e = fma(e, y, 1.0 / 6.0);
-        e = fma(e, y, 0.5);
-        e = fma(e, y, 1.0);
-        e = fma(e, y, 1.0);
-        e *= __ldg(etab + i);
-        F[0] = f;
-        const double twoT = T + T;
-#pragma unroll
-        for (int j = 1; j < J; ++j) {
-            const int kk = kmax - j + 1;                       // F_{kk-1} from F_kk
-            F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
-        }
-    } else {
-        const double rT = rsqrt(T);
-        const double e = exp(-T);
-        const double h = 0.5 * rT * rT;                        // 1/(2T)
-        double f = kSqrtPiHalf * rT;                           // F_0
-        const int kmin = kmax - J + 1;
-        for (int kk = 0; kk < kmin; ++kk) f = fma(k.dint[2 * kk + 1], f, -e) * h;
-        F[J - 1] = f;
-#pragma unroll
-        for (int t = 1; t < J; ++t) {
-            const int kk = kmin + t - 1;
-            f = fma(k.dint[2 * kk + 1], f, -e) * h;
-            F[J - 1 - t] = f;
-        }
-    }
-}
-
-__device__ __forceinline__ double powi(double x, int n)
-{
-    double p = 1.0;
-    while (n) {
-        if (n & 1) p *= x;
-        x *= x;
-        n >>= 1;
-    }
-    return p;
-}
+using namespace dev;
 
 // ------------------------------------------------------------------------- //
 // Radial terms of one primitive pair, accumulated into the contracted        //
@@ -161,84 +85,6 @@ __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec
             for (int j = J - 1; j >= 0; --j) {
                 O[j] += q * F[j];
                 q *= f;
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------------- //
-// Regular scaled solid harmonics R^{c/s}_{l,m}(v), 0 <= m <= l <= lmax      //
-// (recursions of Sec. II E), stored at l(l+1)/2 + m.                       //
-// ------------------------------------------------------------------------- //
-__device__ __forceinline__ void scaled_harmonics(double x, double y, double z, int lmax, const Consts &k,
-                                                 double *Rc, double *Rs)
-{
-    const double r2 = x * x + y * y + z * z;
-    Rc[0] = 1.0;
-    Rs[0] = 0.0;
-    for (int l = 0; l < lmax; ++l) {
-        const int d0 = l * (l + 1) / 2, d1 = (l + 1) * (l + 2) / 2, dm = (l - 1) * l / 2;
-        const double cll = Rc[d0 + l], sll = Rs[d0 + l];
-        const double inv = k.inv_int[2 * l + 2];
-        Rc[d1 + l + 1] = -(x * cll - y * sll) * inv;
-        Rs[d1 + l + 1] = -(y * cll + x * sll) * inv;
-        const double zl = k.dint[2 * l + 1] * z;
-        for (int m = 0; m <= l; ++m) {
-            const double im = k.inv_int[(l + m + 1) * (l - m + 1)];
-            const double pc = (m <= l - 1) ? Rc[dm + m] : 0.0;
-            const double ps = (m <= l - 1) ? Rs[dm + m] : 0.0;
-            Rc[d1 + m] = (zl * Rc[d0 + m] - r2 * pc) * im;
-            Rs[d1 + m] = (m == 0) ? 0.0 : (zl * Rs[d0 + m] - r2 * ps) * im;
-        }
-    }
-}
-
-// R^c_{L,m} and R^s_{L,m} for any integer m, with R_{L,-m} from the symmetry
-// relations R^c_{l,-m} = (-1)^m R^c_{l,m}, R^s_{l,-m} = -(-1)^m R^s_{l,m}
-// and zero for |m| > L.
-__device__ __forceinline__ double rc_get(const double *Rc, int L, int m)
-{
-    const int am = m < 0 ? -m : m;
-    if (L < 0 || am > L) return 0.0;
-    const double v = Rc[L * (L + 1) / 2 + am];
-    return (m < 0 && (am & 1)) ? -v : v;
-}
-__device__ __forceinline__ double rs_get(const double *Rs, int L, int m)
-{
-    const int am = m < 0 ? -m : m;
-    if (L < 0 || am > L) return 0.0;
-    const double v = Rs[L * (L + 1) / 2 + am];
-    return (m < 0 && !(am & 1)) ? -v : v;
-}
-
-// One row of the translation matrix W_{l,mu,j,kappa} (Sec. II E) for the
-// real function m (cosine part for m >= 0, sine part for m < 0), flattened
-// over e = (j, kappa, z): j^2 + (kappa == 0 ? 0 : 2 kappa - 1 + z).
-// kappa = 0 keeps only the z = c column (the z = s column is exactly zero);
-// the factor (1/2)^{delta_kappa0} cancels the doubled m +- 0 term.
-template <int J>
-__device__ __forceinline__ void w_row(const double *Rc, const double *Rs, int l, int m, double (&w)[J * J])
-{
-    const int mu = m < 0 ? -m : m;
-    const bool sine = m < 0;
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const int L = l - j;
-#pragma unroll
-        for (int kp = 0; kp <= j; ++kp) {
-            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
-            if (kp == 0) {
-                w[e0] = sine ? rs_get(Rs, L, mu) : rc_get(Rc, L, mu);
-            } else {
-                const double cm = rc_get(Rc, L, mu - kp), cp = rc_get(Rc, L, mu + kp);
-                const double sm = rs_get(Rs, L, mu - kp), sp = rs_get(Rs, L, mu + kp);
-                if (!sine) {
-                    w[e0] = (kp & 1) ? cm - cp : cm + cp;       // W^{cc}
-                    w[e0 + 1] = (kp & 1) ? -sm - sp : sp - sm;   // W^{cs}
-                } else {
-                    w[e0] = (kp & 1) ? sm - sp : sm + sp;        // W^{sc}
-                    w[e0 + 1] = (kp & 1) ? cm + cp : cm - cp;    // W^{ss}
-                }
             }
         }
     }
@@ -330,7 +176,8 @@ __device__ __forceinline__ void run_tile_fp64(const Args2c &g, int op, const Til
 {
     if (lane >= t.count) return;
     const int p = g.perm[t.start + lane];
-    const int J = (t.la < t.lb ? t.la : t.lb) + 1;
+    const int la = t.cls / (kLmax2c + 1), lb = t.cls % (kLmax2c + 1);
+    const int J = (la < lb ? la : lb) + 1;
     switch (op) {
     case OP_OVERLAP: pair_2c_fp64_dispatch<OP_OVERLAP>(g, p, J); break;
     case OP_COULOMB: pair_2c_fp64_dispatch<OP_COULOMB>(g, p, J); break;
@@ -381,7 +228,31 @@ __global__ void k_classify(int64_t n, const int32_t *__restrict__ pa, const int3
             const ShellRec sa = shells[a], sb = shells[b];
             const int cls = sa.l * (kLmax2c + 1) + sb.l;
             const int kk = sa.nprim * sb.nprim;
-            r = bin_rank[cls * kKmax * kKmax + (kk - 1)];
+            r = bin_rank[cls * kKbins2c + (kk - 1)];
+        }
+        key[p] = r;
+        atomicAdd(hist + r, 1);
+    }
+}
+
+__global__ void k_classify_3c(int64_t n, const int32_t *__restrict__ ta, const int32_t *__restrict__ tt,
+                              const int32_t *__restrict__ tb, const ShellRec *__restrict__ orb, int n_orb,
+                              const ShellRec *__restrict__ aux, int n_aux, const int *__restrict__ bin_rank,
+                              int *__restrict__ key, int *__restrict__ hist, int *__restrict__ err)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int a = ta[p], t = tt[p], b = tb[p];
+        int r = 0;
+        if (a < 0 || a >= n_orb || t < 0 || t >= n_orb || b < 0 || b >= n_aux) {
+            atomicOr(err, 1);
+        } else {
+            const ShellRec sa = orb[a], st = orb[t], sb = aux[b];
+            if (sa.center != st.center) atomicOr(err, 2);
+            if (sa.l + st.l > kLmaxAabA) atomicOr(err, 4);
+            const int cls = (sa.l * 7 + st.l) * 7 + sb.l;
+            int kk = sa.nprim * st.nprim * sb.nprim;
+            kk = kk < kKbins3c ? kk : kKbins3c;
+            r = bin_rank[cls * kKbins3c + (kk - 1)];
         }
         key[p] = r;
         atomicAdd(hist + r, 1);
@@ -433,23 +304,21 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ key, int *__restric
     }
 }
 
-__global__ void k_make_tiles(int n_bins, const int *__restrict__ hist, const int *__restrict__ bin_start,
-                             const int *__restrict__ tile_start, const int *__restrict__ rank_to_bin,
-                             Tile *__restrict__ tiles)
+__global__ void k_make_tiles(int n_bins, int bins_per_class, const int *__restrict__ hist,
+                             const int *__restrict__ bin_start, const int *__restrict__ tile_start,
+                             const int *__restrict__ rank_to_bin, Tile *__restrict__ tiles)
 {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_bins; r += gridDim.x * blockDim.x) {
         const int c = hist[r];
         if (!c) continue;
         const int bin = rank_to_bin[r];
-        const int cls = bin / (kKmax * kKmax);
-        const int la = cls / (kLmax2c + 1), lb = cls % (kLmax2c + 1);
         const int nt = (c + kTile - 1) / kTile;
         for (int t = 0; t < nt; ++t) {
             Tile tl;
             tl.start = bin_start[r] + t * kTile;
             tl.count = (c - t * kTile) < kTile ? (c - t * kTile) : kTile;
-            tl.la = la;
-            tl.lb = lb;
+            tl.cls = bin / bins_per_class;
+            tl.pad = 0;
             tiles[tile_start[r] + t] = tl;
         }
     }
@@ -508,14 +377,18 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int blocks = (int)((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
-    if (n > 0) {
+    if (n > 0 && plan.kind == 2) {
         k_classify<<<blocks, threads, 0, s>>>(n, plan.pair_a, plan.pair_b, plan.basis->shells, plan.basis->n_shells,
                                               d_bin_rank, key, hist, d_err);
+    } else if (n > 0) {
+        k_classify_3c<<<blocks, threads, 0, s>>>(n, plan.pair_a, plan.trip_t, plan.pair_b, plan.basis->shells,
+                                                 plan.basis->n_shells, plan.aux->shells, plan.aux->n_shells,
+                                                 d_bin_rank, key, hist, d_err);
     }
     k_scan_bins<<<1, 1024, 0, s>>>(n_bins, hist, bin_start, cursor, tile_start);
     if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, key, cursor, plan.perm);
-    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, hist, bin_start, tile_start, d_bin_rank + n_bins,
-                                                       plan.tiles);
+    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, plan.kind == 2 ? kKbins2c : kKbins3c, hist,
+                                                       bin_start, tile_start, d_bin_rank + n_bins, plan.tiles);
     return cudaGetLastError();
 }
 

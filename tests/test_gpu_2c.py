@@ -166,4 +166,5 @@ def test_device_boys_against_oracle(shg):
     F = dF.cpu().numpy().reshape(len(T), nmax + 1)
     ref = np.stack([oracle.boys(nmax, t) for t in T])
     rel = np.abs(F - ref) / ref
-    assert rel.max() < 4e-15, rel.max()
+    # 15 downward recursion steps from F_15: about 20 ulp at F_0
+    assert rel.max() < 1e-14, rel.max()
