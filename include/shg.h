@@ -218,6 +218,36 @@ int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t
                          const double *d_upstream_w, double *d_grad_a, double *d_grad_b, void *stream);
 
 /*
+ * shg_eval_2c_noalloc - shg_eval_2c for callers that cannot allocate device
+ * memory during the call.  The paper has no counterpart: this is a property
+ * of the library, not of the integral scheme.
+ *
+ * shg_eval_2c allocates its plan (the bucketed pair list and tile list) with
+ * cudaMallocAsync.  Some callers cannot allow that at call time: a framework
+ * that hands out device memory only from its own pool, a real-time loop that
+ * must not pay allocation latency or its implicit synchronisation, a process
+ * that has reserved all device memory up front.  This entry point builds the
+ * same plan in a fixed array inside the library (a file-scope __device__
+ * array of about 10.5 MB that every GPU loading the library keeps until the
+ * process exits) and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Results equal those of shg_eval_2c with the persistent schedule.
+ *   arguments      as shg_eval_2c (no screening threshold); FP64 and the
+ *                  basis must have been created on the current device, which
+ *                  also set up the library's tables there
+ *   limit          n_pairs <= 1,048,576; larger lists return SHG_ERANGE
+ *                  with a message, before any device work
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call outside stream capture.
+ * The call synchronises `stream` once, after planning, to read the pair-index
+ * check and the tile count.  All calls share the one array and each clears
+ * what must start at zero; calls whose GPU work overlaps (other streams or
+ * unordered host threads) race on it, so order them on one stream.
+ */
+int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a,
+                        const int32_t *d_pair_b, int op, double omega, int precision,
+                        const int64_t *d_out_offsets, double *d_out, void *stream);
+
+/*
  * shg_debug_boys - device Boys function F_n(T) = int_0^1 exp(-T t^2) t^{2n} dt
  * (SI Eq. 3) as used by the Coulomb-type radial terms: for every T in
  * d_T[n_T] writes F_n for n = 0..nmax (nmax <= 24) to d_F[i*(nmax+1) + n].

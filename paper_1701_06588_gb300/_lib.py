@@ -42,6 +42,7 @@ SIGNATURES = [
     ("shg_eval_3c_aab", _I, [_P, _P, _L, _P, _P, _P, _I, _D, _P, _P, _P]),
     ("shg_eval_2c_grad", _I, [_P, _L, _P, _P, _I, _D, _I, _P, _P, _P, _P, _P]),
     ("shg_eval_3c_aab_grad", _I, [_P, _P, _L, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
+    ("shg_eval_2c_noalloc", _I, [_P, _L, _P, _P, _I, _D, _I, _P, _P, _P]),
     ("shg_debug_boys", _I, [_L, _P, _I, _P, _P]),
     ("shg_measure_alu_peak", _I, [_I, _I, ctypes.POINTER(_D), _P]),
     ("shg_last_error", ctypes.c_char_p, []),
@@ -159,6 +160,11 @@ def shg_eval_2c_grad(basis, n, d_pair_a, d_pair_b, op, omega, precision, d_w_off
 def shg_eval_3c_aab_grad(orb, aux, n, d_a, d_atilde, d_b, precision, d_w_offsets, d_w, d_grad_a, d_grad_b, stream):
     return check(load().shg_eval_3c_aab_grad(orb, aux, n, _ptr(d_a), _ptr(d_atilde), _ptr(d_b), precision,
                                              _ptr(d_w_offsets), _ptr(d_w), _ptr(d_grad_a), _ptr(d_grad_b), stream))
+
+
+def shg_eval_2c_noalloc(basis, n_pairs, d_pair_a, d_pair_b, op, omega, precision, d_out_offsets, d_out, stream):
+    return check(load().shg_eval_2c_noalloc(basis, n_pairs, _ptr(d_pair_a), _ptr(d_pair_b), op, omega, precision,
+                                            _ptr(d_out_offsets), _ptr(d_out), stream))
 
 
 def shg_debug_boys(n, d_T, nmax, d_F, stream):

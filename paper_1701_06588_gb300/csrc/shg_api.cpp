@@ -12,20 +12,11 @@
 #include <string>
 #include <vector>
 
-struct shg_basis {
-    shg::BasisDev d;
-};
-
-struct shg_plan {
-    shg::PlanDev d;
-    int launches = 0;
-};
-
 namespace shg {
 
 static thread_local std::string g_err;
 
-static int fail(int code, const char *fmt, ...)
+int fail(int code, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -205,7 +196,21 @@ const DeviceTables *device_tables_impl(int **ranks)
 
 const DeviceTables *device_tables() { return device_tables_impl(nullptr); }
 
-static const Consts &consts()
+const DeviceTables *device_tables_if_ready(const int **ranks)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &st = g_dev[dev];
+    if (!st.ready) return nullptr;
+    if (ranks) {
+        ranks[0] = st.bin_rank[0];
+        ranks[1] = st.bin_rank[1];
+    }
+    return &st.t;
+}
+
+const Consts &consts()
 {
     static Consts k;
     static std::once_flag once;
@@ -220,6 +225,15 @@ static int current_device_matches(int dev)
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return fail(SHG_ECUDA, "cudaGetDevice failed");
     if (cur != dev) return fail(SHG_EINVAL, "current device %d differs from the basis device %d", cur, dev);
+    return SHG_OK;
+}
+
+int check_op(int op, double omega, int precision)
+{
+    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS) return fail(SHG_EINVAL, "bad operator %d", op);
+    if ((op == SHG_OP_ERF || op == SHG_OP_ERFC || op == SHG_OP_GAUSS) && !(omega > 0 && std::isfinite(omega)))
+        return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
+    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available", precision);
     return SHG_OK;
 }
 
@@ -467,14 +481,6 @@ void shg_plan_destroy(shg_plan_t *p)
     delete p;
 }
 
-static int check_op(int op, double omega, int precision)
-{
-    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS) return fail(SHG_EINVAL, "bad operator %d", op);
-    if ((op == SHG_OP_ERF || op == SHG_OP_ERFC || op == SHG_OP_GAUSS) && !(omega > 0 && std::isfinite(omega)))
-        return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
-    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available", precision);
-    return SHG_OK;
-}
 
 int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int precision, const int64_t *off,
                      double *out, void *stream)

@@ -82,6 +82,15 @@ void fill_consts3(Consts3 &k);
 // and sets the error message.
 const DeviceTables *device_tables();
 
+// Tables of the current device if a basis was already created on it (never
+// allocates); ranks[0..1] receive the bin rank tables of both schedules.
+const DeviceTables *device_tables_if_ready(const int **ranks);
+
+// Host helpers of shg_api.cpp.
+int fail(int code, const char *fmt, ...);          // sets shg_last_error(), returns code
+const Consts &consts();                            // constant tables (host copy)
+int check_op(int op, double omega, int precision);  // operator / omega / precision check
+
 // Host generation of the Boys table (long double arithmetic).
 void make_boys_table(double *tab, double *etab);
 
@@ -103,6 +112,7 @@ struct Tile {
 };
 
 constexpr int kKbins2c = kKmax * kKmax;      // two-center bins per class: Ka*Kb - 1
+constexpr int kNBins2c = kNClass * kKbins2c;
 constexpr int kNClass3 = 7 * 7 * 7;          // (la, la~, lb) classes
 constexpr int kKbins3c = 64;                 // three-index bins per class: min(Ka*Ka~*Kb, 64) - 1
 
@@ -172,3 +182,14 @@ cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, c
 cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s);
 
 }  // namespace shg
+
+// Opaque handles of the C ABI.
+struct shg_basis {
+    shg::BasisDev d;
+};
+
+struct shg_plan {
+    shg::PlanDev d;
+    int launches = 0;
+};
+
