@@ -128,3 +128,57 @@ def eval_2c(basis, pair_a, pair_b, op, omega=0.0, precision="fp64", screen_thres
     L.shg_eval_2c(basis.handle, len(off), _dev_i32(pair_a), _dev_i32(pair_b), _op(op), float(omega),
                   float(screen_thresh), _prec(precision), d_off, out, _stream(stream))
     return out[:total], off
+
+
+def eval_3c_aab(orb, aux, t_a, t_atilde, t_b, precision="fp64", stream=None):
+    """Three-index overlaps (a b a~) of a triple list (a, a~ in `orb` on one
+    center, b in `aux`) as one flat float64 CUDA tensor plus block offsets."""
+    off, total = orb.triple_offsets(aux, t_a, t_atilde, t_b)
+    out = torch.empty(max(total, 1), dtype=torch.float64, device="cuda")
+    L.shg_eval_3c_aab(orb.handle, aux.handle, len(off), _dev_i32(t_a), _dev_i32(t_atilde), _dev_i32(t_b),
+                      _prec(precision), 0.0, _dev_i64(off), out, _stream(stream))
+    return out[:total], off
+
+
+def eval_2c_grad(basis, pair_a, pair_b, op, upstream, offsets=None, omega=0.0, precision="fp64", stream=None):
+    """Vector-Jacobian product of the two-center blocks with upstream weights
+    (flat float64 CUDA tensor in the layout of eval_2c): returns per-pair
+    gradients with respect to R_a and R_b, each (n_pairs, 3) CUDA tensors."""
+    if offsets is None:
+        offsets, _ = basis.pair_offsets(pair_a, pair_b)
+    n = len(offsets)
+    ga = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    gb = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    L.shg_eval_2c_grad(basis.handle, n, _dev_i32(pair_a), _dev_i32(pair_b), _op(op), float(omega), _prec(precision),
+                       _dev_i64(offsets), upstream.contiguous(), ga, gb, _stream(stream))
+    return ga, gb
+
+
+class TwoCenterIntegrals(torch.autograd.Function):
+    """Blocks (a|O|b) as a differentiable function of the center coordinates.
+
+    forward(centers[n_centers, 3] float64, basis, pair_a, pair_b, op, omega)
+    returns the flat block tensor; backward calls the library's gradient
+    kernel (radial terms recomputed, nothing stored) and scatters the per-pair
+    gradients onto the centers with index_add_.
+    """
+
+    @staticmethod
+    def forward(ctx, centers, basis, pair_a, pair_b, op, omega):
+        basis.set_centers(centers.detach().cpu().numpy())
+        out, off = eval_2c(basis, pair_a, pair_b, op, omega=omega)
+        ctx.basis, ctx.pair_a, ctx.pair_b, ctx.op, ctx.omega, ctx.off = basis, pair_a, pair_b, op, omega, off
+        ctx.n_centers = centers.shape[0]
+        ctx.device = centers.device
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        ga, gb = eval_2c_grad(ctx.basis, ctx.pair_a, ctx.pair_b, ctx.op, grad_out.to("cuda", torch.float64),
+                              offsets=ctx.off, omega=ctx.omega)
+        ca = torch.from_numpy(ctx.basis.center_of[np.asarray(ctx.pair_a)].astype(np.int64)).cuda()
+        cb = torch.from_numpy(ctx.basis.center_of[np.asarray(ctx.pair_b)].astype(np.int64)).cuda()
+        g = torch.zeros((ctx.n_centers, 3), dtype=torch.float64, device="cuda")
+        g.index_add_(0, ca, ga)
+        g.index_add_(0, cb, gb)
+        return g.to(ctx.device), None, None, None, None, None

@@ -1,0 +1,213 @@
+// Three-index overlap (a b a~), a and a~ on center A, b on center B, by the
+// SHG scheme of Sec. II D (arXiv:1701.06588), FP64.
+//
+// The product of the two functions on A is expanded with real Gaunt
+// coefficients into solid harmonics L_a = |la-la~|..la+la~ (step 2) times
+// r_a^{2p}, p = (la+la~-L_a)/2 (Eq. product_SHG_STGO); each term is a
+// two-center block of shell (L_a, exponent alpha' = alpha+alpha~) with b,
+// whose monopole P^{(k)} (Eq. Pa_aba) contracts
+//   binom(p,j) (L_a)_j alpha'^{-j} (0_a'|r_a^{2(p-j)}|0_b)^{(k)}
+// over primitive triples, with (0_a'|r_a^{2m}|0_b)^{(k)} from Eqs. sra2ms and
+// devsra2ms.  The angular part is the real translation matrix of Sec. II E.
+//
+// One thread per triple; a warp owns a class-pure tile (la, la~, lb).
+#include "shg_device.cuh"
+
+namespace shg {
+namespace {
+using namespace dev;
+
+constexpr int kPmax = 5;          // min(la, la~) <= 5 when la + la~ <= 10
+constexpr int kNL = kPmax + 1;    // number of L_a terms
+constexpr int kKmax3 = kLmaxAabA + kLmax2c;  // highest derivative order, 16
+constexpr int kLR = kLmaxAabA;    // scaled harmonics up to l = 10
+
+__device__ void triple_aab_fp64(const Args3c &g, int p)
+{
+    const ShellRec sa = g.orb_shells[g.t_a[p]];
+    const ShellRec st = g.orb_shells[g.t_t[p]];
+    const ShellRec sb = g.aux_shells[g.t_b[p]];
+    const int la = sa.l, lt = st.l, lb = sb.l;
+    const Vec4 A = g.orb_centers[sa.center];
+    const Vec4 B = g.aux_centers[sb.center];
+    const double vx = A.x - B.x, vy = A.y - B.y, vz = A.z - B.z;
+    const double R2 = vx * vx + vy * vy + vz * vz;
+    const int Lmin = la > lt ? la - lt : lt - la;
+    const int Lmax = la + lt;
+    const int nL = (Lmax - Lmin) / 2 + 1;
+    const int pmax = nL - 1;
+    const int kmaxA = Lmax + lb;
+    const int kminA = Lmin > lb ? Lmin : lb;
+
+    double P[kNL][kJmax];
+    for (int i = 0; i < kNL; ++i)
+        for (int j = 0; j < kJmax; ++j) P[i][j] = 0.0;
+
+    const int Ka = sa.nprim, Kt = st.nprim, Kb = sb.nprim;
+    const int ntrip = Ka * Kt * Kb;
+    for (int q = 0; q < ntrip; ++q) {
+        const int ib = q % Kb;
+        const int it = (q / Kb) % Kt;
+        const int ia = q / (Kb * Kt);
+        const PrimRec pa = g.orb_prims[sa.prim_off + ia];
+        const PrimRec pt = g.orb_prims[st.prim_off + it];
+        const PrimRec pb = g.aux_prims[sb.prim_off + ib];
+        const double ap = pa.alpha + pt.alpha;
+        const double be = pb.alpha;
+        const double c = ap + be;
+        const double rc = rsqrt(c);
+        const double ic = rc * rc;
+        const double rho = ap * be * ic;
+        const double gg = be * be * ic;                 // beta^2 / c
+        const double x = gg * R2;
+        const double h = 0.5 * ic;                      // 1 / (2c)
+        const double rap = rsqrt(ap);
+        const double iap = rap * rap;                   // 1 / alpha'
+        // pi^{3/2} c^{-3/2} exp(-rho R^2) and the weights N c of a, a~ and N c / (2beta)^lb of b
+        const double w0 = pa.wN * pt.wN * pb.w2c * kPi32 * ic * rc * exp(-rho * R2);
+
+        // D_m^{(i)}(x) = sum_{j=i..m} d_{m,j} j!/(j-i)! x^{j-i}
+        double D[kPmax + 1][kPmax + 1];
+        for (int m = 0; m <= pmax; ++m)
+            for (int i = 0; i <= m; ++i) {
+                double s = g.k3.dd[m][i][m];
+                for (int j = m - 1; j >= i; --j) s = fma(s, x, g.k3.dd[m][i][j]);
+                D[m][i] = s;
+            }
+        double nr[kKmax3 + 1];                          // (-rho)^n
+        nr[0] = 1.0;
+        for (int n = 1; n <= kmaxA; ++n) nr[n] = nr[n - 1] * -rho;
+        double gp[kPmax + 1], hm[kPmax + 1], ia_p[kPmax + 1];
+        gp[0] = hm[0] = ia_p[0] = 1.0;
+        for (int m = 1; m <= pmax; ++m) {
+            gp[m] = gp[m - 1] * gg;
+            hm[m] = hm[m - 1] * h;
+            ia_p[m] = ia_p[m - 1] * iap;
+        }
+        // V[m][k] = (2c)^{-m} sum_{i<=min(m,k)} binom(k,i) (-rho)^{k-i} (beta^2/c)^i D_m^{(i)}(x)
+        double V[kPmax + 1][kKmax3 + 1];
+        for (int m = 0; m <= pmax; ++m)
+            for (int k = kminA; k <= kmaxA; ++k) {
+                double v = 0.0;
+                const int imax = m < k ? m : k;
+                for (int i = 0; i <= imax; ++i) v = fma(g.k3.binom[k][i] * nr[k - i], gp[i] * D[m][i], v);
+                V[m][k] = hm[m] * v;
+            }
+        // P_L^{(k)} += w0 (2 alpha')^{-L} sum_j binom(p,j) (L)_j alpha'^{-j} V[p-j][k]
+        const double i2ap = 0.5 * iap;
+        double wL = w0 * powi(i2ap, Lmin);
+        const double i2ap2 = i2ap * i2ap;
+        for (int iL = 0; iL < nL; ++iL) {
+            const int L = Lmin + 2 * iL;
+            const int pL = pmax - iL;
+            const int J = (L < lb ? L : lb) + 1;
+            const int kmaxL = L + lb;
+            for (int j = 0; j < J; ++j) {
+                const int k = kmaxL - j;
+                double s = 0.0;
+                for (int jj = 0; jj <= pL; ++jj) s = fma(g.k3.bj[L][pL][jj] * ia_p[jj], V[pL - jj][k], s);
+                P[iL][j] = fma(wL, s, P[iL][j]);
+            }
+            wL *= i2ap2;
+        }
+    }
+
+    // angular part: R^{c/s}_{l,m}(R_a - R_b) up to max(L_a max, lb)
+    double Rc[(kLR + 1) * (kLR + 2) / 2], Rs[(kLR + 1) * (kLR + 2) / 2];
+    scaled_harmonics(vx, vy, vz, Lmax > lb ? Lmax : lb, g.k, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    const int Jmax = (Lmax < lb ? Lmax : lb) + 1;
+    double Wb[2 * kLmax2c + 1][kJmax * kJmax];
+    for (int mb = -lb; mb <= lb; ++mb) w_row_rt(Rc, Rs, lb, mb, Jmax, Wb[mb + lb]);
+
+    // blocks B_L[M][mb] of every L_a term, each a two-center formula with P
+    double Bst[(1 + 5 + 9 + 13 + 17 + 21) * (2 * kLmax2c + 1)];
+    const double sgn_b = (lb & 1) ? -1.0 : 1.0;
+    // lambda K_L = sqrt(4 pi (2L+1) / ((2la+1)(2la~+1)))
+    const double lam0 = 3.5449077018110320545963349666822903 / (g.k3.sqrt_int[2 * la + 1] * g.k3.sqrt_int[2 * lt + 1]);
+    int boff = 0;
+    for (int iL = 0; iL < nL; ++iL) {
+        const int L = Lmin + 2 * iL;
+        const int J = (L < lb ? L : lb) + 1;
+        const double lamK = lam0 * g.k3.sqrt_int[2 * L + 1];
+        double ge[kJmax * kJmax];
+        for (int j = 0; j < J; ++j) {
+            const double oj = P[iL][j] * lamK * g.k.pow2[L + lb - j];
+            for (int kp = 0; kp <= j; ++kp) {
+                const double v = oj * g.k.jB[j][kp];
+                const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+                ge[e0] = v;
+                if (kp) ge[e0 + 1] = v;
+            }
+        }
+        for (int M = -L; M <= L; ++M) {
+            double wa[kJmax * kJmax];
+            w_row_rt(Rc, Rs, L, M, J, wa);
+            const double Aa = g.k.A[L][M < 0 ? -M : M] * sgn_b;
+            for (int e = 0; e < J * J; ++e) wa[e] *= ge[e];
+            for (int mb = -lb; mb <= lb; ++mb) {
+                double s = 0.0;
+                for (int e = 0; e < J * J; ++e) s = fma(wa[e], Wb[mb + lb][e], s);
+                Bst[boff + (M + L) * nb + (mb + lb)] = Aa * (g.k.A[lb][mb < 0 ? -mb : mb] * s);
+            }
+        }
+        boff += (2 * L + 1) * nb;
+    }
+
+    // Gaunt sum over (L_a, M_a) for each (m_a, m_a~)
+    const int nt = 2 * lt + 1;
+    const int rbase = g.gaunt_base[la * 7 + lt];
+    double *out = g.out + g.out_off[p];
+    for (int ma = 0; ma < 2 * la + 1; ++ma)
+        for (int mt = 0; mt < nt; ++mt) {
+            const int r = rbase + ma * nt + mt;
+            double acc[2 * kLmax2c + 1];
+            for (int mb = 0; mb < nb; ++mb) acc[mb] = 0.0;
+            for (int q = g.gaunt_row[r]; q < g.gaunt_row[r + 1]; ++q) {
+                const GauntEnt ge = g.gaunt[q];
+                const int iL = (ge.L - Lmin) / 2;
+                // offset of block L = sum_{L' < L} (2L'+1) nb over the L' of this triple
+                const int off_L = iL * (2 * Lmin + 1 + 2 * (iL - 1)) * nb;
+                const double *bl = Bst + off_L + (ge.M + ge.L) * nb;
+                for (int mb = 0; mb < nb; ++mb) acc[mb] = fma(ge.g, bl[mb], acc[mb]);
+            }
+            double *o = out + (ma * nt + mt) * nb;
+            for (int mb = 0; mb < nb; ++mb) o[mb] = acc[mb];
+        }
+}
+
+__global__ void __launch_bounds__(128) k_3c_fp64_persistent(const Args3c g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        const Tile tl = g.tiles[t];
+        if (lane < tl.count) triple_aab_fp64(g, g.perm[tl.start + lane]);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_3c(const Args3c &a, int precision, int grid, cudaStream_t s)
+{
+    (void)precision;
+    k_3c_fp64_persistent<<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int persistent_grid_3c(int precision)
+{
+    (void)precision;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_fp64_persistent, 128, 0) != cudaSuccess || per < 1)
+        per = 1;
+    return (sms > 0 ? sms : 1) * per;
+}
+
+}  // namespace shg

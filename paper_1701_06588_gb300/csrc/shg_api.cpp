@@ -95,16 +95,183 @@ void make_boys_table(double *tab, double *etab)
     }
 }
 
+static float2 split2(long double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (long double)hi));
+}
+
+void fill_consts_mix(ConstsMix &k)
+{
+    std::memset(&k, 0, sizeof k);
+    for (int l = 0; l <= kLmax2c; ++l)
+        for (int mu = 0; mu <= l; ++mu) {
+            long double v = std::sqrt((long double)(mu == 0 ? 1 : 2) * lfact(l + mu) * lfact(l - mu));
+            k.A[l][mu] = split2((mu & 1) ? -v : v);
+        }
+    for (int j = 0; j < kJmax; ++j) {
+        long double df = 1;
+        for (int i = 2 * j - 1; i > 1; i -= 2) df *= i;
+        for (int kp = 0; kp <= j; ++kp) k.jB[j][kp] = split2(df / ((kp == 0 ? 1 : 2) * lfact(j + kp) * lfact(j - kp)));
+    }
+    for (int i = 1; i < 64; ++i) k.inv_int[i] = split2(1.0L / i);
+    for (int t = 0; t < 14; ++t) {
+        k.inv_fact[t] = split2(1.0L / lfact(t));
+        k.inv_fact_f[t] = (float)(1.0L / lfact(t));
+    }
+    const long double pi = 3.14159265358979323846264338327950288L;
+    k.pi32 = split2(std::pow(pi, 1.5L));
+    k.pi3 = split2(pi * pi * pi);
+    k.two_pi52 = split2(2 * std::pow(pi, 2.5L));
+    k.sqrt_pi_half = split2(std::sqrt(pi) / 2);
+}
+
+void fill_consts3(Consts3 &k)
+{
+    std::memset(&k, 0, sizeof k);
+    for (int n = 0; n < 18; ++n)
+        for (int i = 0; i <= n; ++i) k.binom[n][i] = (double)(lfact(n) / (lfact(i) * lfact(n - i)));
+    // d_{m,j} = 2^j (2m+1)!! binom(m,j) / (2j+1)!!   (Eq. I_jab); dd[m][i][j] = d_{m,j} j!/(j-i)!
+    auto dfact = [](int n) { long double f = 1; for (int i = n; i > 1; i -= 2) f *= i; return f; };
+    for (int m = 0; m < 6; ++m)
+        for (int j = 0; j <= m; ++j) {
+            const long double d = std::ldexp(1.0L, j) * dfact(2 * m + 1) * (lfact(m) / (lfact(j) * lfact(m - j))) /
+                                  dfact(2 * j + 1);
+            for (int i = 0; i <= j; ++i) k.dd[m][i][j] = (double)(d * lfact(j) / lfact(j - i));
+        }
+    // binom(p, j) (L)_j with the rising factorial (L)_j = L (L+1) ... (L+j-1), (0)_0 = 1, (0)_j = 0
+    for (int L = 0; L < 11; ++L)
+        for (int p = 0; p < 6; ++p)
+            for (int j = 0; j <= p; ++j) {
+                long double r = 1;
+                for (int i = 0; i < j; ++i) r *= (L + i);
+                k.bj[L][p][j] = (double)((lfact(p) / (lfact(j) * lfact(p - j))) * r);
+            }
+    for (int n = 0; n < 32; ++n) k.sqrt_int[n] = (double)std::sqrt((long double)n);
+}
+
+// Real orthonormal spherical harmonics Y_{l,m} = A_{l,|m|} R^{c/s}_{l,|m|} / sqrt(4pi/(2l+1))
+// at a unit vector (Sec. II E recursions), l <= lmax, stored at l*l + l + m.
+static void real_ylm(long double x, long double y, long double z, int lmax, long double *Y)
+{
+    long double Rc[16][16] = {}, Rs[16][16] = {};
+    const long double r2 = x * x + y * y + z * z;
+    Rc[0][0] = 1;
+    for (int l = 0; l < lmax; ++l) {
+        Rc[l + 1][l + 1] = -(x * Rc[l][l] - y * Rs[l][l]) / (2 * l + 2);
+        Rs[l + 1][l + 1] = -(y * Rc[l][l] + x * Rs[l][l]) / (2 * l + 2);
+        for (int m = 0; m <= l; ++m) {
+            const long double pc = (l >= 1 && m <= l - 1) ? Rc[l - 1][m] : 0, ps = (l >= 1 && m <= l - 1) ? Rs[l - 1][m] : 0;
+            Rc[l + 1][m] = ((2 * l + 1) * z * Rc[l][m] - r2 * pc) / ((l + m + 1) * (l - m + 1));
+            Rs[l + 1][m] = ((2 * l + 1) * z * Rs[l][m] - r2 * ps) / ((l + m + 1) * (l - m + 1));
+        }
+    }
+    const long double pi = 3.14159265358979323846264338327950288L;
+    for (int l = 0; l <= lmax; ++l) {
+        const long double nrm = std::sqrt((2 * l + 1) / (4 * pi));
+        for (int m = -l; m <= l; ++m) {
+            const int mu = m < 0 ? -m : m;
+            long double A = std::sqrt((long double)(mu == 0 ? 1 : 2) * lfact(l + mu) * lfact(l - mu));
+            if (mu & 1) A = -A;
+            Y[l * l + l + m] = nrm * A * (m >= 0 ? Rc[l][mu] : Rs[l][mu]);
+        }
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n).
+static void gauss_legendre(int n, std::vector<long double> &x, std::vector<long double> &w)
+{
+    const long double pi = 3.14159265358979323846264338327950288L;
+    x.assign(n, 0);
+    w.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        long double t = std::cos(pi * (i + 0.75L) / (n + 0.5L)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const long double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1);
+            const long double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-19L) break;
+        }
+        x[i] = t;
+        w[i] = 2 / ((1 - t * t) * dp * dp);
+    }
+}
+
+// Real Gaunt coefficients G = int Y_{L,M} Y_{l,m} Y_{l~,m~} dOmega for
+// l, l~ <= 6, l + l~ <= kLmaxAabA, L = |l-l~|..l+l~ step 2 (the expansion of
+// Eq. CG_expansion written for real harmonics), by product quadrature that is
+// exact for these degrees: 16-point Gauss-Legendre in cos(theta) (polynomial
+// degree <= 20) times the 32-point trapezoid rule in phi (|frequency| <= 20).
+static void make_gaunt(std::vector<int> &base, std::vector<int> &row, std::vector<GauntEnt> &ent)
+{
+    const int nt = 16, np = 32, LY = 16;
+    const long double pi = 3.14159265358979323846264338327950288L;
+    std::vector<long double> gx, gw;
+    gauss_legendre(nt, gx, gw);
+    std::vector<double> Y((size_t)nt * np * LY * LY), W((size_t)nt * np);
+    long double Yl[LY * LY];
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < np; ++j) {
+            const long double ct = gx[i], st = std::sqrt(1 - ct * ct), ph = 2 * pi * j / np;
+            real_ylm(st * std::cos(ph), st * std::sin(ph), ct, 12, Yl);
+            for (int q = 0; q < LY * LY; ++q) Y[((size_t)i * np + j) * LY * LY + q] = (double)Yl[q];
+            W[(size_t)i * np + j] = (double)(gw[i] * 2 * pi / np);
+        }
+    base.assign(49, -1);
+    row.clear();
+    ent.clear();
+    row.push_back(0);
+    for (int l = 0; l <= 6; ++l)
+        for (int lt = 0; lt <= 6; ++lt) {
+            if (l + lt > kLmaxAabA) continue;
+            base[l * 7 + lt] = (int)row.size() - 1;
+            for (int m = -l; m <= l; ++m)
+                for (int mt = -lt; mt <= lt; ++mt) {
+                    for (int L = std::abs(l - lt); L <= l + lt; L += 2)
+                        for (int M = -L; M <= L; ++M) {
+                            double g = 0;
+                            for (size_t q = 0; q < W.size(); ++q) {
+                                const double *Yq = &Y[q * LY * LY];
+                                g += W[q] * Yq[L * L + L + M] * Yq[l * l + l + m] * Yq[lt * lt + lt + mt];
+                            }
+                            if (std::fabs(g) > 1e-13) ent.push_back(GauntEnt{g, L, M});
+                        }
+                    row.push_back((int)ent.size());
+                }
+        }
+}
+
 // ------------------------------------------------------------------------- //
 // Per-device tables                                                          //
 // ------------------------------------------------------------------------- //
 constexpr int kNBins = kNClass * kKbins2c;
 
+constexpr int kNBins3 = kNClass3 * kKbins3c;
+
 struct DevState {
     DeviceTables t{};
     int *bin_rank[2] = {nullptr, nullptr};   // [2 * kNBins]: rank of bin, then bin of rank
+    int *bin_rank3 = nullptr;                // [2 * kNBins3], three-index bins by cost
     bool ready = false;
 };
+
+static double class_cost3(int la, int lt, int lb, int kk)
+{
+    const int Lmin = std::abs(la - lt), Lmax = la + lt, nL = (Lmax - Lmin) / 2 + 1;
+    double rad = 30.0, ang = 0;
+    for (int L = Lmin; L <= Lmax; L += 2) {
+        const int J = std::min(L, lb) + 1;
+        rad += 4.0 * J * ((Lmax - L) / 2 + 1);
+        ang += (2.0 * L + 1) * (2 * lb + 1) * (J * J + 2) + (2.0 * L + 1) * J * J;
+    }
+    return kk * rad + ang + (2.0 * la + 1) * (2 * lt + 1) * (2 * lb + 1) * nL * 2;
+}
 
 static std::mutex g_mu;
 static DevState g_dev[64];
@@ -146,7 +313,7 @@ static void make_ranks(int schedule, std::vector<int> &rank, std::vector<int> &i
     }
 }
 
-const DeviceTables *device_tables_impl(int **ranks)
+const DeviceTables *device_tables_impl(int **ranks, int **rank3 = nullptr)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -159,7 +326,23 @@ const DeviceTables *device_tables_impl(int **ranks)
     if (!st.ready) {
         std::vector<double> tab((size_t)kBoysGrid * kBoysN * kBoysTerms), etab(kBoysGrid);
         make_boys_table(tab.data(), etab.data());
+        std::vector<float4> mtab((size_t)kBoysGrid * kBoysN * 4);
+        std::vector<float2> metab(kBoysGrid);
+        for (int i = 0; i < kBoysGrid; ++i) {
+            for (int n = 0; n < kBoysN; ++n) {
+                const double *cf = &tab[((size_t)i * kBoysN + n) * kBoysTerms];
+                float4 *q = &mtab[((size_t)i * kBoysN + n) * 4];
+                const float2 c0 = split2(cf[0]), c1 = split2(cf[1]), c2 = split2(cf[2]), c3 = split2(cf[3]);
+                q[0] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                q[1] = make_float4(c2.x, c2.y, c3.x, c3.y);
+                q[2] = make_float4((float)cf[4], (float)cf[5], (float)cf[6], (float)cf[7]);
+                q[3] = make_float4(0, 0, 0, 0);
+            }
+            metab[i] = split2(etab[i]);
+        }
         double *d_tab = nullptr, *d_e = nullptr;
+        float4 *d_mtab = nullptr;
+        float2 *d_metab = nullptr;
         int *d_r[2] = {nullptr, nullptr};
         if (cudaMalloc(&d_tab, tab.size() * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&d_e, etab.size() * sizeof(double)) != cudaSuccess ||
@@ -170,17 +353,59 @@ const DeviceTables *device_tables_impl(int **ranks)
             return nullptr;
         }
         bool ok = cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(d_e, etab.data(), etab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+                  cudaMemcpy(d_e, etab.data(), etab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMalloc(&d_mtab, mtab.size() * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&d_metab, metab.size() * sizeof(float2)) == cudaSuccess &&
+                  cudaMemcpy(d_mtab, mtab.data(), mtab.size() * sizeof(float4), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(d_metab, metab.data(), metab.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
         for (int s = 0; s < 2 && ok; ++s) {
             std::vector<int> rank, inv;
             make_ranks(s, rank, inv);
             rank.insert(rank.end(), inv.begin(), inv.end());
             ok = cudaMemcpy(d_r[s], rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
         }
+        // three-index bins ordered by estimated cost
+        int *d_r3 = nullptr;
+        if (ok) {
+            std::vector<int> order(kNBins3), rank3(2 * kNBins3);
+            std::vector<double> cost(kNBins3);
+            for (int b = 0; b < kNBins3; ++b) {
+                order[b] = b;
+                const int cls = b / kKbins3c, kk = b % kKbins3c + 1;
+                cost[b] = class_cost3(cls / 49, (cls / 7) % 7, cls % 7, kk);
+            }
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+            for (int r = 0; r < kNBins3; ++r) {
+                rank3[order[r]] = r;
+                rank3[kNBins3 + r] = order[r];
+            }
+            ok = cudaMalloc(&d_r3, rank3.size() * sizeof(int)) == cudaSuccess &&
+                 cudaMemcpy(d_r3, rank3.data(), rank3.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        // real Gaunt coefficients
+        int *d_gb = nullptr, *d_gr = nullptr;
+        GauntEnt *d_ge = nullptr;
+        if (ok) {
+            std::vector<int> gb, gr;
+            std::vector<GauntEnt> ge;
+            make_gaunt(gb, gr, ge);
+            ok = cudaMalloc(&d_gb, gb.size() * sizeof(int)) == cudaSuccess &&
+                 cudaMalloc(&d_gr, gr.size() * sizeof(int)) == cudaSuccess &&
+                 cudaMalloc(&d_ge, ge.size() * sizeof(GauntEnt)) == cudaSuccess &&
+                 cudaMemcpy(d_gb, gb.data(), gb.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+                 cudaMemcpy(d_gr, gr.data(), gr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+                 cudaMemcpy(d_ge, ge.data(), ge.size() * sizeof(GauntEnt), cudaMemcpyHostToDevice) == cudaSuccess;
+        }
         if (!ok) {
             fail(SHG_ECUDA, "device tables: upload failed");
             return nullptr;
         }
+        st.bin_rank3 = d_r3;
+        st.t.gaunt_base = d_gb;
+        st.t.gaunt_row = d_gr;
+        st.t.gaunt = d_ge;
+        st.t.boys_mix = d_mtab;
+        st.t.boys_e_mix = d_metab;
         st.t.boys = d_tab;
         st.t.boys_e = d_e;
         st.bin_rank[0] = d_r[0];
@@ -191,6 +416,7 @@ const DeviceTables *device_tables_impl(int **ranks)
         ranks[0] = st.bin_rank[0];
         ranks[1] = st.bin_rank[1];
     }
+    if (rank3) *rank3 = st.bin_rank3;
     return &st.t;
 }
 
@@ -208,6 +434,22 @@ const DeviceTables *device_tables_if_ready(const int **ranks)
         ranks[1] = st.bin_rank[1];
     }
     return &st.t;
+}
+
+const ConstsMix &consts_mix()
+{
+    static ConstsMix k;
+    static std::once_flag once;
+    std::call_once(once, [] { fill_consts_mix(k); });
+    return k;
+}
+
+const Consts3 &consts3()
+{
+    static Consts3 k;
+    static std::once_flag once;
+    std::call_once(once, [] { fill_consts3(k); });
+    return k;
 }
 
 const Consts &consts()
@@ -233,7 +475,8 @@ int check_op(int op, double omega, int precision)
     if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS) return fail(SHG_EINVAL, "bad operator %d", op);
     if ((op == SHG_OP_ERF || op == SHG_OP_ERFC || op == SHG_OP_GAUSS) && !(omega > 0 && std::isfinite(omega)))
         return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
-    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available", precision);
+    if (precision != SHG_PREC_FP64 && precision != SHG_PREC_MIXED)
+        return fail(SHG_EINVAL, "precision %d not available", precision);
     return SHG_OK;
 }
 
@@ -307,7 +550,23 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         off += K;
     }
     std::vector<Vec4> ctr(n_centers);
-    for (int c = 0; c < n_centers; ++c) ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+    std::vector<MixCenter> mctr(n_centers);
+    for (int c = 0; c < n_centers; ++c) {
+        ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+        mctr[c] = MixCenter{split2(centers[3 * c]), split2(centers[3 * c + 1]), split2(centers[3 * c + 2]),
+                            make_float2(0, 0)};
+    }
+    std::vector<MixPrim> mpr(n_prims);
+    {
+        int64_t o = 0;
+        for (int s2 = 0; s2 < n_shells; ++s2)
+            for (int i = 0; i < nprim[s2]; ++i, ++o) {
+                const long double a = exps[o];
+                long double N = 1.0L;
+                (void)N;
+                mpr[o] = MixPrim{split2(a), split2(1.0L / a), split2((long double)pr[o].wN), make_float2(0, 0)};
+            }
+    }
 
     shg_basis_t *b = new (std::nothrow) shg_basis_t;
     if (!b) return fail(SHG_ENOMEM, "host allocation failed");
@@ -324,13 +583,17 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
     std::memcpy(d.h_center, center_of_shell, sizeof(int32_t) * n_shells);
     if (cudaMalloc(&d.shells, sizeof(ShellRec) * n_shells) != cudaSuccess ||
         cudaMalloc(&d.prims, sizeof(PrimRec) * n_prims) != cudaSuccess ||
-        cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess) {
+        cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess ||
+        cudaMalloc(&d.mprims, sizeof(MixPrim) * n_prims) != cudaSuccess ||
+        cudaMalloc(&d.mcenters, sizeof(MixCenter) * n_centers) != cudaSuccess) {
         shg_basis_destroy(b);
         return fail(SHG_ENOMEM, "basis: cudaMalloc failed");
     }
     if (cudaMemcpy(d.shells, sh.data(), sizeof(ShellRec) * n_shells, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.prims, pr.data(), sizeof(PrimRec) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.centers, ctr.data(), sizeof(Vec4) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(d.centers, ctr.data(), sizeof(Vec4) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.mprims, mpr.data(), sizeof(MixPrim) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.mcenters, mctr.data(), sizeof(MixCenter) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess) {
         shg_basis_destroy(b);
         return fail(SHG_ECUDA, "basis: upload failed");
     }
@@ -349,8 +612,14 @@ int shg_basis_set_centers(shg_basis_t *b, const double *centers)
     for (int64_t i = 0; i < 3 * (int64_t)b->d.n_centers; ++i)
         if (!is_finite_d(centers[i])) return fail(SHG_EINVAL, "center coordinate %lld not finite", (long long)i);
     std::vector<Vec4> ctr(b->d.n_centers);
-    for (int c = 0; c < b->d.n_centers; ++c) ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+    std::vector<MixCenter> mctr(b->d.n_centers);
+    for (int c = 0; c < b->d.n_centers; ++c) {
+        ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
+        mctr[c] = MixCenter{split2(centers[3 * c]), split2(centers[3 * c + 1]), split2(centers[3 * c + 2]),
+                            make_float2(0, 0)};
+    }
     SHG_CUDA(cudaMemcpy(b->d.centers, ctr.data(), sizeof(Vec4) * b->d.n_centers, cudaMemcpyHostToDevice));
+    SHG_CUDA(cudaMemcpy(b->d.mcenters, mctr.data(), sizeof(MixCenter) * b->d.n_centers, cudaMemcpyHostToDevice));
     return SHG_OK;
 }
 
@@ -360,6 +629,8 @@ void shg_basis_destroy(shg_basis_t *b)
     cudaFree(b->d.shells);
     cudaFree(b->d.prims);
     cudaFree(b->d.centers);
+    cudaFree(b->d.mprims);
+    cudaFree(b->d.mcenters);
     delete[] b->d.h_l;
     delete[] b->d.h_nprim;
     delete[] b->d.h_center;
@@ -497,6 +768,39 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
     const DeviceTables *t = device_tables();
     if (!t) return SHG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    if (precision == SHG_PREC_MIXED) {
+        ArgsMix m;
+        m.shells = p->d.basis->shells;
+        m.prims = p->d.basis->mprims;
+        m.centers = p->d.basis->mcenters;
+        m.pair_a = p->d.pair_a;
+        m.pair_b = p->d.pair_b;
+        m.perm = p->d.perm;
+        m.tiles = p->d.tiles;
+        m.out_off = reinterpret_cast<const long long *>(off);
+        m.out = out;
+        m.omega = split2(omega);
+        m.omega2 = split2((long double)omega * omega);
+        m.boys = t->boys_mix;
+        m.boys_e = t->boys_e_mix;
+        m.km = consts_mix();
+        if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+            m.tile_begin = 0;
+            m.tile_end = p->d.n_tiles;
+            m.counter = p->d.counter;
+            SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op), true, s));
+        } else {
+            m.counter = nullptr;
+            for (int cls = 0; cls < kNClass; ++cls) {
+                m.tile_begin = p->d.class_tile_begin[cls];
+                m.tile_end = p->d.class_tile_begin[cls + 1];
+                if (m.tile_end <= m.tile_begin) continue;
+                SHG_CUDA(launch_2c_mixed(m, op, 0, false, s));
+            }
+        }
+        return SHG_OK;
+    }
     Args2c a;
     a.shells = p->d.basis->shells;
     a.prims = p->d.basis->prims;
@@ -544,16 +848,131 @@ int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const in
     return r;
 }
 
-int shg_eval_3c_aab(const shg_basis_t *, const shg_basis_t *, int64_t, const int32_t *, const int32_t *,
-                    const int32_t *, int, double, const int64_t *, double *, void *)
+int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta, const int32_t *tt,
+                    const int32_t *tb, int precision, double screen, const int64_t *off, double *out, void *stream)
 {
-    return fail(SHG_EINVAL, "shg_eval_3c_aab: not available in this build");
+    g_err.clear();
+    if (!orb || !aux) return fail(SHG_EINVAL, "basis is NULL");
+    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available for (aab)", precision);
+    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
+    if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_triples %lld out of range", (long long)n);
+    if (n == 0) return SHG_OK;
+    if (!ta || !tt || !tb || !off || !out) return fail(SHG_EINVAL, "NULL device pointer");
+    int r = current_device_matches(orb->d.device);
+    if (r) return r;
+    if (aux->d.device != orb->d.device) return fail(SHG_EINVAL, "orb and aux bases live on different devices");
+    int *ranks[2], *rank3 = nullptr;
+    const DeviceTables *t = device_tables_impl(ranks, &rank3);
+    if (!t) return SHG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const int64_t max_tiles = n / kTile + std::min<int64_t>(n, kNBins3) + 1;
+    const size_t bytes_perm = sizeof(int32_t) * (size_t)n;
+    const size_t bytes_tiles = sizeof(Tile) * (size_t)max_tiles;
+    const size_t bytes_ws = sizeof(int) * ((size_t)n + 4 * (size_t)kNBins3 + 1);
+    const size_t bytes = bytes_perm + bytes_tiles + bytes_ws + 512;
+    void *blk = nullptr;
+    SHG_CUDA(cudaMallocAsync(&blk, bytes, s));
+    PlanDev d;
+    d.basis = &orb->d;
+    d.aux = &aux->d;
+    d.kind = 3;
+    d.n_pairs = n;
+    d.schedule = SHG_SCHED_PERSISTENT;
+    d.pair_a = ta;
+    d.trip_t = tt;
+    d.pair_b = tb;
+    char *c = (char *)blk;
+    d.tiles = (Tile *)c;                 c += (bytes_tiles + 15) / 16 * 16;
+    d.perm = (int32_t *)c;               c += (bytes_perm + 15) / 16 * 16;
+    d.counter = (int *)c;                c += 16;
+    int *d_err = (int *)c;               c += 16;
+    int *ws = (int *)c;
+    int *d_tile_start = ws + n + 3 * kNBins3;
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_plan_build(d, ws, kNBins3, rank3, d_err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h[0], d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], d_tile_start + kNBins3, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(blk, s);
+        return fail(SHG_ECUDA, "(aab) planning: %s", cudaGetErrorString(e));
+    }
+    if (h[0]) {
+        cudaFreeAsync(blk, s);
+        if (h[0] & 1) return fail(SHG_EINVAL, "triple list holds a shell index out of range");
+        if (h[0] & 2) return fail(SHG_EINVAL, "a and a~ of a triple are not on the same center");
+        return fail(SHG_EINVAL, "la + la~ exceeds %d", kLmaxAabA);
+    }
+    Args3c a;
+    a.orb_shells = orb->d.shells;
+    a.aux_shells = aux->d.shells;
+    a.orb_prims = orb->d.prims;
+    a.aux_prims = aux->d.prims;
+    a.orb_centers = orb->d.centers;
+    a.aux_centers = aux->d.centers;
+    a.t_a = ta;
+    a.t_t = tt;
+    a.t_b = tb;
+    a.perm = d.perm;
+    a.tiles = d.tiles;
+    a.tile_begin = 0;
+    a.tile_end = h[1];
+    a.counter = d.counter;
+    a.out_off = reinterpret_cast<const long long *>(off);
+    a.out = out;
+    a.gaunt_base = t->gaunt_base;
+    a.gaunt_row = t->gaunt_row;
+    a.gaunt = t->gaunt;
+    a.k = consts();
+    a.k3 = consts3();
+    e = cudaMemsetAsync(d.counter, 0, sizeof(int), s);
+    if (e == cudaSuccess && h[1] > 0) e = launch_3c(a, precision, persistent_grid_3c(precision), s);
+    cudaFreeAsync(blk, s);
+    if (e != cudaSuccess) return fail(SHG_ECUDA, "(aab) launch: %s", cudaGetErrorString(e));
+    return SHG_OK;
 }
 
-int shg_eval_2c_grad(const shg_basis_t *, int64_t, const int32_t *, const int32_t *, int, double, int,
-                     const int64_t *, const double *, double *, double *, void *)
+int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,
+                     int precision, const int64_t *w_off, const double *w, double *grad_a, double *grad_b,
+                     void *stream)
 {
-    return fail(SHG_EINVAL, "shg_eval_2c_grad: not available in this build");
+    g_err.clear();
+    int r = check_op(op, omega, precision);
+    if (r) return r;
+    if (n == 0) return SHG_OK;
+    if (!w_off || !w || !grad_a) return fail(SHG_EINVAL, "NULL device pointer");
+    shg_plan_t *p = nullptr;
+    r = shg_plan_2c_create(basis, n, pa, pb, SHG_SCHED_PERSISTENT, stream, &p);
+    if (r) return r;
+    const DeviceTables *t = device_tables();
+    cudaStream_t s = (cudaStream_t)stream;
+    Args2c a;
+    std::memset(&a, 0, sizeof a);
+    a.shells = basis->d.shells;
+    a.prims = basis->d.prims;
+    a.centers = basis->d.centers;
+    a.pair_a = pa;
+    a.pair_b = pb;
+    a.perm = p->d.perm;
+    a.tiles = p->d.tiles;
+    a.tile_begin = 0;
+    a.tile_end = p->d.n_tiles;
+    a.counter = p->d.counter;
+    a.omega = omega;
+    a.boys = t->boys;
+    a.boys_e = t->boys_e;
+    a.w_off = reinterpret_cast<const long long *>(w_off);
+    a.w = w;
+    a.grad_a = grad_a;
+    a.grad_b = grad_b;
+    a.k = consts();
+    cudaError_t e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
+    if (e == cudaSuccess && p->d.n_tiles > 0) e = launch_2c_grad(a, op, precision, persistent_grid_2c_grad(op, precision), s);
+    shg_plan_destroy(p);
+    if (e != cudaSuccess) return fail(SHG_ECUDA, "gradient launch: %s", cudaGetErrorString(e));
+    return SHG_OK;
 }
 
 int shg_eval_3c_aab_grad(const shg_basis_t *, const shg_basis_t *, int64_t, const int32_t *, const int32_t *,

@@ -46,6 +46,15 @@ struct GauntEnt {
     int L, M;
 };
 
+// Mixed-precision (double-float) copies: each value v as float2 (hi, lo),
+// hi = fl32(v), lo = fl32(v - hi).
+struct alignas(32) MixPrim {
+    float2 alpha, inv_alpha, wN, pad;
+};
+struct alignas(32) MixCenter {
+    float2 x, y, z, pad;
+};
+
 // Small constant tables, passed by value in kernel parameters.
 struct Consts {
     double A[kLmaxR + 1][kLmaxR + 1];      // A_{l,mu} of Eq. (A)
@@ -57,6 +66,18 @@ struct Consts {
 
 void fill_consts(Consts &k);
 
+// Double-float constants of the mixed-precision kernels.
+struct ConstsMix {
+    float2 A[kLmax2c + 1][kLmax2c + 1];    // A_{l,mu}
+    float2 jB[kJmax][kJmax];               // (2j-1)!! B_{j,kappa}
+    float2 inv_int[64];                    // 1/n
+    float2 inv_fact[14];                   // 1/t!
+    float inv_fact_f[14];
+    float2 pi32, pi3, two_pi52, sqrt_pi_half;
+};
+
+void fill_consts_mix(ConstsMix &k);
+
 // Device-resident tables owned by the library, one set per device.
 struct DeviceTables {
     const double *boys;   // [kBoysGrid][kBoysN][kBoysTerms]
@@ -66,6 +87,8 @@ struct DeviceTables {
     const int *gaunt_base;     // [7*7] first row of the (l, l~) block
     const int *gaunt_row;      // row pointers
     const GauntEnt *gaunt;     // entries
+    const float4 *boys_mix;    // [kBoysGrid][kBoysN][4] (c0..c3 as hi/lo, c4..c7 as float, pad)
+    const float2 *boys_e_mix;  // [kBoysGrid] exp(-T_i) as hi/lo
 };
 
 // Extra constants of the three-index kernels (by value).
@@ -101,6 +124,8 @@ struct BasisDev {
     ShellRec *shells = nullptr;   // device
     PrimRec *prims = nullptr;     // device
     Vec4 *centers = nullptr;      // device
+    MixPrim *mprims = nullptr;    // device, double-float copies for the mixed path
+    MixCenter *mcenters = nullptr;
     // host copies used for validation and offsets
     int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
 };
@@ -148,7 +173,30 @@ struct Args2c {
     double *out;
     double omega;
     const double *boys, *boys_e;
+    // gradient kernels only: upstream weights W (blocks at w + w_off[p]) and
+    // the per-pair outputs dI/dR_a . W and dI/dR_b . W
+    const long long *w_off;
+    const double *w;
+    double *grad_a, *grad_b;
     Consts k;
+};
+
+// Arguments of the mixed-precision two-center kernels (by value).
+struct ArgsMix {
+    const ShellRec *shells;
+    const MixPrim *prims;
+    const MixCenter *centers;
+    const int32_t *pair_a, *pair_b;
+    const int32_t *perm;
+    const Tile *tiles;
+    int tile_begin, tile_end;
+    int *counter;
+    const long long *out_off;
+    double *out;
+    float2 omega, omega2;
+    const float4 *boys;
+    const float2 *boys_e;
+    ConstsMix km;
 };
 
 // Arguments of the three-index kernels (by value).
@@ -173,6 +221,10 @@ struct Args3c {
 cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, const int *d_bin_rank,
                               int *d_err, cudaStream_t s);
 cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
+cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s);
+cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s);
+int persistent_grid_2c_mixed(int op);
+int persistent_grid_2c_grad(int op, int precision);
 int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
                       cudaStream_t s);

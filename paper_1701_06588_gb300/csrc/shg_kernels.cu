@@ -24,73 +24,6 @@ namespace {
 using namespace dev;
 
 // ------------------------------------------------------------------------- //
-// Radial terms of one primitive pair, accumulated into the contracted        //
-// O[j] = O^{(kmax-j)}, j = 0..J-1 (Table S1 and Eq. O_rab2_deriv).          //
-//   w = w_alpha w_beta = N_a N_b c_alpha c_beta / ((2alpha)^la (2beta)^lb)  //
-// ------------------------------------------------------------------------- //
-template <int OP, int J>
-__device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec &pb, double R2, int kmax,
-                                                const Args2c &g, double (&O)[J])
-{
-    const int kmin = kmax - J + 1;
-    const double w = pa.w2c * pb.w2c;
-    const double c = pa.alpha + pb.alpha;
-    const double rc = rsqrt(c);
-    const double ic = rc * rc;
-    const double rho = pa.alpha * pb.alpha * ic;
-    const double T = rho * R2;
-    if (OP == OP_OVERLAP) {
-        // (pi/c)^{3/2} exp(-T) (-rho)^k
-        double q = w * kPi32 * ic * rc * exp(-T) * powi(-rho, kmin);
-#pragma unroll
-        for (int j = J - 1; j >= 0; --j) {
-            O[j] += q;
-            q *= -rho;
-        }
-    } else if (OP == OP_GAUSS) {
-        // (pi^2/(c (rho+w)))^{3/2} exp(-w T/(rho+w)) (-w rho/(rho+w))^k
-        const double rd = rsqrt(rho + g.omega);
-        const double id = rd * rd;
-        const double f = -g.omega * rho * id;
-        double q = w * kPi3 * ic * rc * id * rd * exp(-g.omega * T * id) * powi(f, kmin);
-#pragma unroll
-        for (int j = J - 1; j >= 0; --j) {
-            O[j] += q;
-            q *= f;
-        }
-    } else {
-        // Coulomb-type: 2 pi^{5/2} / (alpha beta sqrt(c)) * ...
-        const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
-        if (OP == OP_COULOMB || OP == OP_ERFC) {
-            double F[J];
-            boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, F);
-            double q = pre * powi(-rho, kmin);
-#pragma unroll
-            for (int j = J - 1; j >= 0; --j) {
-                O[j] += q * F[j];
-                q *= -rho;
-            }
-        }
-        if (OP == OP_ERF || OP == OP_ERFC) {
-            // omega/sqrt(omega^2+rho) (-omega^2 rho/(omega^2+rho))^k F_k(omega^2 T/(omega^2+rho))
-            const double w2 = g.omega * g.omega;
-            const double rw = rsqrt(w2 + rho);
-            const double s = w2 * rw * rw;
-            const double f = -rho * s;
-            double F[J];
-            boys_top<J>(s * T, kmax, g.boys, g.boys_e, g.k, F);
-            double q = pre * g.omega * rw * powi(f, kmin);
-            if (OP == OP_ERFC) q = -q;
-#pragma unroll
-            for (int j = J - 1; j >= 0; --j) {
-                O[j] += q * F[j];
-                q *= f;
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------------- //
 // One shell pair, FP64.                                                     //
 // ------------------------------------------------------------------------- //
 template <int OP, int J>
@@ -108,12 +41,12 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
     double O[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) O[j] = 0.0;
-    for (int ia = 0; ia < sa.nprim; ++ia) {
-        const PrimRec pa = g.prims[sa.prim_off + ia];
-        for (int ib = 0; ib < sb.nprim; ++ib) {
-            const PrimRec pb = g.prims[sb.prim_off + ib];
-            radial_acc_fp64<OP, J>(pa, pb, R2, kmax, g, O);
-        }
+    // one flat loop over the Ka*Kb primitive pairs: tiles hold pairs of equal
+    // Ka*Kb, so every lane of a warp runs the same trip count
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, g, O);
     }
 
     // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}, shared by z = c, s

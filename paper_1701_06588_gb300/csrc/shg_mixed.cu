@@ -1,0 +1,394 @@
+// Mixed-precision two-center SHG kernel: the same formula as the FP64 path
+// (Sec. II B and Table S1 of arXiv:1701.06588) evaluated in double-float
+// arithmetic on the FP32 pipes (GB300 issues FP32 at 74x its FP64 rate), with
+// FP64 used only to write the result.
+//
+// Range: the FP64 path forms w_a w_b (-rho)^k with w = N c (2 alpha)^-l, whose
+// factors leave the FP32 exponent range (rho^k reaches 1e44 for alpha, beta
+// ~ 5000).  Here every primitive term enters the assembly already multiplied
+// by the 2^{la+lb-j} of Eq. final_r12int_ab, and
+//   2^k (-rho)^k (2 alpha)^-la (2 beta)^-lb = (-1)^k (beta/c)^la (alpha/c)^lb (2 rho)^-j,
+// k = la+lb-j, whose factors are all bounded: (beta/c), (alpha/c) <= 1 and
+// (2 rho)^-j <= 4e9 on the synthetic sets.  So the accumulated quantity is
+//   S_j = sum (-1)^k N_a c_a N_b c_b (beta/c)^la (alpha/c)^lb (2 rho)^-j X_k
+// with X_k the operator part of (0_a|O|0_b)^{(k)} without its (-rho)^k.
+//
+// Precision: double-float (about 2^-44); Taylor tails of the Boys function and
+// of exp whose size is below 1e-7 of the leading term are summed in plain
+// FP32 (their rounding is below 1e-14 of the result).
+#include "shg_device.cuh"
+#include "shg_df.cuh"
+
+namespace shg {
+namespace {
+using namespace dev;
+using namespace dfm;
+
+__device__ __forceinline__ df ldf(float2 v) { return df{v.x, v.y}; }
+
+__device__ __forceinline__ df powi_df(df x, int n)
+{
+    df p = df_f(1.0f);
+    while (n) {
+        if (n & 1) p = mul(p, x);
+        x = mul(x, x);
+        n >>= 1;
+    }
+    return p;
+}
+
+// exp(-x), x >= 0, in double-float: x = n ln2 + r, |r| <= ln2/2, Taylor of
+// exp(-r) (degree 13; terms 7..13 in FP32), times 2^-n.  Below FP32 range for
+// x > 87 the result is flushed to zero (terms that small are far below the
+// absolute parity floor for the weights of the synthetic sets).
+__device__ __forceinline__ df exp_neg_df(df x, const ConstsMix &k)
+{
+    if (x.hi > 87.0f) return df_f(0.0f);
+    const float n = rintf(x.hi * 1.44269504088896341f);
+    const float ln2_hi = 0.693147182464599609375f;        // float(ln 2)
+    const float ln2_lo = -1.904654299957768e-09f;          // ln 2 - ln2_hi
+    const float ph = n * ln2_hi;
+    const df p = df{ph, fmaf(n, ln2_hi, -ph)};             // exact n ln2_hi
+    df r = sub(x, p);
+    r = add_f(r, -n * ln2_lo);
+    const df y = neg(r);                                   // exp(y), |y| <= 0.35
+    float t = k.inv_fact_f[13];
+    for (int i = 12; i >= 7; --i) t = fmaf(t, y.hi, k.inv_fact_f[i]);
+    df e = add(mul_f(y, t), ldf(k.inv_fact[6]));
+    for (int i = 5; i >= 0; --i) e = add(mul(y, e), ldf(k.inv_fact[i]));
+    const float s = exp2f(-n);                              // exact power of two (or 0 below range)
+    return df{e.hi * s, e.lo * s};
+}
+
+// Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}; same scheme as the FP64
+// path (Taylor about i/16 from the table, downward recursion; upward above 36).
+template <int J>
+__device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__restrict__ tab,
+                                             const float2 *__restrict__ etab, const ConstsMix &k, df (&F)[J])
+{
+    if (T.hi < (float)kBoysTmax) {
+        const int i = __float2int_rn(T.hi * 16.0f);
+        const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
+        const df y = two_sum(-d0, -T.lo);                          // -(T - T_i)
+        const float4 *c = tab + ((size_t)i * kBoysN + kmax) * 4;
+        const float4 q0 = __ldg(c), q1 = __ldg(c + 1), q2 = __ldg(c + 2);
+        float t = fmaf(q2.w, y.hi, q2.z);
+        t = fmaf(t, y.hi, q2.y);
+        t = fmaf(t, y.hi, q2.x);
+        df f = add(mul_f(y, t), df{q1.z, q1.w});
+        f = add(mul(y, f), df{q1.x, q1.y});
+        f = add(mul(y, f), df{q0.z, q0.w});
+        f = add(mul(y, f), df{q0.x, q0.y});
+        float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi, k.inv_fact_f[4]);
+        df e = add(mul_f(y, te), ldf(k.inv_fact[3]));
+        e = add(mul(y, e), ldf(k.inv_fact[2]));
+        e = add(mul(y, e), df_f(1.0f));
+        e = add(mul(y, e), df_f(1.0f));
+        e = mul(e, ldf(__ldg(etab + i)));
+        F[0] = f;
+        const df twoT = scale2(T, 2.0f);
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            const int kk = kmax - j + 1;
+            F[j] = mul(add(mul(twoT, F[j - 1]), e), ldf(k.inv_int[2 * kk - 1]));
+        }
+    } else {
+        const df rT = rsqrt_df(T);
+        const float e = expf(-T.hi) * (1.0f - T.lo);   // enters only as a small correction
+        const df h = scale2(mul(rT, rT), 0.5f);          // 1/(2T)
+        df f = mul(rT, ldf(k.sqrt_pi_half));             // F_0 = sqrt(pi/(4T))
+        const int kmin = kmax - J + 1;
+        for (int kk = 0; kk < kmin; ++kk) f = mul(add_f(mul_f(f, (float)(2 * kk + 1)), -e), h);
+        F[J - 1] = f;
+#pragma unroll
+        for (int t = 1; t < J; ++t) {
+            const int kk = kmin + t - 1;
+            f = mul(add_f(mul_f(f, (float)(2 * kk + 1)), -e), h);
+            F[J - 1 - t] = f;
+        }
+    }
+}
+
+// S_j += (-1)^k base (2 rho)^-j X_k for one primitive pair, k = la+lb-j.
+template <int OP, int J>
+__device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim &pb, df R2, int la, int lb,
+                                               const ArgsMix &g, df (&S)[J])
+{
+    const int kmax = la + lb;
+    const df a = ldf(pa.alpha), b = ldf(pb.alpha);
+    const df c = add(a, b);
+    const df rc = rsqrt_df(c);
+    const df ic = mul(rc, rc);
+    const df rho = mul(mul(a, b), ic);
+    const df T = mul(rho, R2);
+    df base = mul(ldf(pa.wN), powi_df(mul(b, ic), la));
+    base = mul(base, mul(ldf(pb.wN), powi_df(mul(a, ic), lb)));
+    const df h = scale2(mul(mul(c, ldf(pa.inv_alpha)), ldf(pb.inv_alpha)), 0.5f);   // 1/(2 rho)
+    df hp[J];                       // base (2 rho)^-j (-1)^{kmax-j}
+    hp[0] = (kmax & 1) ? neg(base) : base;
+#pragma unroll
+    for (int j = 1; j < J; ++j) hp[j] = neg(mul(hp[j - 1], h));
+    if (OP == OP_OVERLAP) {
+        const df X = mul(mul(ldf(g.km.pi32), mul(ic, rc)), exp_neg_df(T, g.km));
+#pragma unroll
+        for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(hp[j], X));
+    } else if (OP == OP_GAUSS) {
+        const df d = add(rho, ldf(g.omega));
+        const df rd = rsqrt_df(d);
+        const df id = mul(rd, rd);
+        const df wd = mul(ldf(g.omega), id);                               // omega / (rho + omega)
+        df X = mul(mul(ldf(g.km.pi3), mul(mul(ic, rc), mul(id, rd))), exp_neg_df(mul(T, wd), g.km));
+        X = mul(X, powi_df(wd, kmax - J + 1));
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            S[j] = add(S[j], mul(hp[j], X));
+            X = mul(X, wd);
+        }
+    } else {
+        const df pre = mul(mul(ldf(g.km.two_pi52), rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
+        if (OP == OP_COULOMB || OP == OP_ERFC) {
+            df F[J];
+            boys_top_mix<J>(T, kmax, g.boys, g.boys_e, g.km, F);
+#pragma unroll
+            for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(mul(hp[j], pre), F[j]));
+        }
+        if (OP == OP_ERF || OP == OP_ERFC) {
+            const df rw = rsqrt_df(add(ldf(g.omega2), rho));
+            const df s = mul(ldf(g.omega2), mul(rw, rw));                  // omega^2 / (omega^2 + rho)
+            df F[J];
+            boys_top_mix<J>(mul(s, T), kmax, g.boys, g.boys_e, g.km, F);
+            df X = mul(mul(pre, mul(ldf(g.omega), rw)), powi_df(s, kmax - J + 1));
+            if (OP == OP_ERFC) X = neg(X);
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                S[j] = add(S[j], mul(mul(hp[j], X), F[j]));
+                X = mul(X, s);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ df rcm(const df *Rc, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return df_f(0.0f);
+    const df v = Rc[L * (L + 1) / 2 + am];
+    return (m < 0 && (am & 1)) ? neg(v) : v;
+}
+__device__ __forceinline__ df rsm(const df *Rs, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return df_f(0.0f);
+    const df v = Rs[L * (L + 1) / 2 + am];
+    return (m < 0 && !(am & 1)) ? neg(v) : v;
+}
+
+__device__ __forceinline__ void scaled_harmonics_mix(df x, df y, df z, int lmax, const ConstsMix &k, df *Rc, df *Rs)
+{
+    const df r2 = add(add(mul(x, x), mul(y, y)), mul(z, z));
+    Rc[0] = df_f(1.0f);
+    Rs[0] = df_f(0.0f);
+    for (int l = 0; l < lmax; ++l) {
+        const int d0 = l * (l + 1) / 2, d1 = (l + 1) * (l + 2) / 2, dm = (l - 1) * l / 2;
+        const df cll = Rc[d0 + l], sll = Rs[d0 + l];
+        const df inv = ldf(k.inv_int[2 * l + 2]);
+        Rc[d1 + l + 1] = neg(mul(sub(mul(x, cll), mul(y, sll)), inv));
+        Rs[d1 + l + 1] = neg(mul(add(mul(y, cll), mul(x, sll)), inv));
+        const df zl = mul_f(z, (float)(2 * l + 1));
+        for (int m = 0; m <= l; ++m) {
+            const df im = ldf(k.inv_int[(l + m + 1) * (l - m + 1)]);
+            df vc = mul(zl, Rc[d0 + m]);
+            if (m <= l - 1) vc = sub(vc, mul(r2, Rc[dm + m]));
+            Rc[d1 + m] = mul(vc, im);
+            if (m == 0) {
+                Rs[d1] = df_f(0.0f);
+            } else {
+                df vs = mul(zl, Rs[d0 + m]);
+                if (m <= l - 1) vs = sub(vs, mul(r2, Rs[dm + m]));
+                Rs[d1 + m] = mul(vs, im);
+            }
+        }
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void w_row_mix(const df *Rc, const df *Rs, int l, int m, df (&w)[J * J])
+{
+    const int mu = m < 0 ? -m : m;
+    const bool sine = m < 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int L = l - j;
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            if (kp == 0) {
+                w[e0] = sine ? rsm(Rs, L, mu) : rcm(Rc, L, mu);
+            } else {
+                const df cm = rcm(Rc, L, mu - kp), cp = rcm(Rc, L, mu + kp);
+                const df sm = rsm(Rs, L, mu - kp), sp = rsm(Rs, L, mu + kp);
+                if (!sine) {
+                    w[e0] = (kp & 1) ? sub(cm, cp) : add(cm, cp);
+                    w[e0 + 1] = (kp & 1) ? neg(add(sm, sp)) : sub(sp, sm);
+                } else {
+                    w[e0] = (kp & 1) ? sub(sm, sp) : add(sm, sp);
+                    w[e0 + 1] = (kp & 1) ? add(cm, cp) : sub(cm, cp);
+                }
+            }
+        }
+    }
+}
+
+template <int OP, int J>
+__device__ void pair_2c_mix(const ArgsMix &g, int p)
+{
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l;
+    const MixCenter A = g.centers[sa.center];
+    const MixCenter B = g.centers[sb.center];
+    const df vx = sub(ldf(A.x), ldf(B.x)), vy = sub(ldf(A.y), ldf(B.y)), vz = sub(ldf(A.z), ldf(B.z));
+    const df R2 = add(add(mul(vx, vx), mul(vy, vy)), mul(vz, vz));
+
+    df S[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) S[j] = df_f(0.0f);
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        radial_acc_mix<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, la, lb, g, S);
+    }
+    df ge[J * J];
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const df v = mul(S[j], ldf(g.km.jB[j][kp]));
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            ge[e0] = v;
+            if (kp) ge[e0 + 1] = v;
+        }
+    df Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics_mix(vx, vy, vz, la > lb ? la : lb, g.km, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    df Ub[2 * kLmax2c + 1][J * J];
+    for (int mb = -lb; mb <= lb; ++mb) {
+        df w[J * J];
+        w_row_mix<J>(Rc, Rs, lb, mb, w);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) Ub[mb + lb][e] = w[e];
+    }
+    double *out = g.out + g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        df ua[J * J];
+        w_row_mix<J>(Rc, Rs, la, ma, ua);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) ua[e] = mul(ua[e], ge[e]);
+        df Aa = ldf(g.km.A[la][ma < 0 ? -ma : ma]);
+        if (lb & 1) Aa = neg(Aa);
+        for (int mb = -lb; mb <= lb; ++mb) {
+            df s = mul(ua[0], Ub[mb + lb][0]);
+#pragma unroll
+            for (int e = 1; e < J * J; ++e) s = add(s, mul(ua[e], Ub[mb + lb][e]));
+            out[(ma + la) * nb + (mb + lb)] = to_double(mul(Aa, mul(ldf(g.km.A[lb][mb < 0 ? -mb : mb]), s)));
+        }
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void mix_dispatch(const ArgsMix &g, int p, int J)
+{
+    switch (J) {
+    case 1: pair_2c_mix<OP, 1>(g, p); break;
+    case 2: pair_2c_mix<OP, 2>(g, p); break;
+    case 3: pair_2c_mix<OP, 3>(g, p); break;
+    case 4: pair_2c_mix<OP, 4>(g, p); break;
+    case 5: pair_2c_mix<OP, 5>(g, p); break;
+    case 6: pair_2c_mix<OP, 6>(g, p); break;
+    default: pair_2c_mix<OP, 7>(g, p); break;
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_2c_mixed_persistent(const ArgsMix g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        const Tile tl = g.tiles[t];
+        if (lane < tl.count) {
+            const int la = tl.cls / (kLmax2c + 1), lb = tl.cls % (kLmax2c + 1);
+            mix_dispatch<OP>(g, g.perm[tl.start + lane], (la < lb ? la : lb) + 1);
+        }
+        __syncwarp();
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_2c_mixed_static(const ArgsMix g)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = g.tile_begin + warp;
+    if (t >= g.tile_end) return;
+    const Tile tl = g.tiles[t];
+    if (lane < tl.count) {
+        const int la = tl.cls / (kLmax2c + 1), lb = tl.cls % (kLmax2c + 1);
+        mix_dispatch<OP>(g, g.perm[tl.start + lane], (la < lb ? la : lb) + 1);
+    }
+}
+
+template <int OP>
+static int grid_mix()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_persistent<OP>, 128, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    return (sms > 0 ? sms : 1) * per;
+}
+
+template <int OP>
+static cudaError_t launch_mix_op(const ArgsMix &a, int grid, bool persistent, cudaStream_t s)
+{
+    if (persistent) {
+        k_2c_mixed_persistent<OP><<<grid, 128, 0, s>>>(a);
+    } else {
+        const int tiles = a.tile_end - a.tile_begin;
+        if (tiles <= 0) return cudaSuccess;
+        k_2c_mixed_static<OP><<<(tiles + 3) / 4, 128, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent, cudaStream_t s)
+{
+    switch (op) {
+    case OP_OVERLAP: return launch_mix_op<OP_OVERLAP>(a, grid, persistent, s);
+    case OP_COULOMB: return launch_mix_op<OP_COULOMB>(a, grid, persistent, s);
+    case OP_ERFC: return launch_mix_op<OP_ERFC>(a, grid, persistent, s);
+    case OP_ERF: return launch_mix_op<OP_ERF>(a, grid, persistent, s);
+    case OP_GAUSS: return launch_mix_op<OP_GAUSS>(a, grid, persistent, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int persistent_grid_2c_mixed(int op)
+{
+    switch (op) {
+    case OP_OVERLAP: return grid_mix<OP_OVERLAP>();
+    case OP_COULOMB: return grid_mix<OP_COULOMB>();
+    case OP_ERFC: return grid_mix<OP_ERFC>();
+    case OP_ERF: return grid_mix<OP_ERF>();
+    default: return grid_mix<OP_GAUSS>();
+    }
+}
+
+}  // namespace shg

@@ -1,0 +1,117 @@
+"""GPU parity of the two-center gradient kernel (vector-Jacobian product with
+respect to both centers) against the oracle's analytic gradients, central
+finite differences and translation invariance; and the autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_06588_gb300 import workloads as W
+from tests.parity import normalised
+
+pytestmark = pytest.mark.gpu
+
+GRAD_OPS = [("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("overlap", 0, 0.0), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+
+
+@pytest.fixture(scope="module")
+def shg():
+    import torch
+    from paper_1701_06588_gb300 import api, build
+    build.build()
+    torch.cuda.init()
+    return api
+
+
+def _oracle_vjp(shells, pa, pb, op, omega, w):
+    """sum_e W_e dI_e/dR_a from the oracle Jacobian, and the bar scale
+    sum_e |W_e| |dI_e/dR_a| evaluated with |N c| (conditioning of the sum)."""
+    shn, sha = normalised(shells)
+    J, off, sz = oracle.eval_2c_grad(shn, pa, pb, op, omega, center="A", normalize=False)
+    if op == oracle.OP_ERFC:
+        J1, _, _ = oracle.eval_2c_grad(sha, pa, pb, oracle.OP_COULOMB, 0.0, center="A", normalize=False)
+        J2, _, _ = oracle.eval_2c_grad(sha, pa, pb, oracle.OP_ERF, omega, center="A", normalize=False)
+        Ja = np.abs(J1) + np.abs(J2)
+    else:
+        Ja, _, _ = oracle.eval_2c_grad(sha, pa, pb, op, omega, center="A", normalize=False)
+        Ja = np.abs(Ja)
+    g = np.zeros((len(pa), 3))
+    s = np.zeros((len(pa), 3))
+    for p in range(len(pa)):
+        blk = J[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
+        ablk = Ja[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
+        wp = w[off[p]: off[p] + sz[p]]
+        g[p] = blk @ wp
+        s[p] = (ablk.max(axis=1, keepdims=True) * np.ones_like(ablk)) @ np.abs(wp)
+    return g, s
+
+
+@pytest.mark.parametrize("name,n", [("c5_grad_500k_l5_k12", 1200), ("c2_200k_l4_k8", 800)])
+@pytest.mark.parametrize("opname,op,omega", GRAD_OPS)
+def test_grad_against_oracle(shg, name, n, opname, op, omega):
+    import torch
+    sh, pa, pb = W.make(name, n=n)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    rng = np.random.default_rng(4)
+    w = rng.uniform(-1, 1, total)
+    ga, gb = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega)
+    torch.cuda.synchronize()
+    ga, gb = ga.cpu().numpy(), gb.cpu().numpy()
+    np.testing.assert_array_equal(gb, -ga)
+    ref, scale = _oracle_vjp(sh, pa, pb, op, omega, w)
+    bar = 1e-10 * np.abs(ref) + 1e-12 + 1e-15 * scale
+    ex = np.abs(ga - ref) / bar
+    assert ex.max() <= 1.0, (opname, ex.max(), np.unravel_index(ex.argmax(), ex.shape))
+    b.close()
+
+
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+def test_grad_against_finite_differences_of_gpu_forward(shg, opname, op, omega):
+    """Central differences (h = 1e-5 bohr) of the GPU integrals themselves."""
+    import torch
+    sh, pa, pb = W.make("c5_grad_500k_l5_k12", n=300)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = np.random.default_rng(8).uniform(-1, 1, total)
+    ga, _ = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega)
+    ga = ga.cpu().numpy()
+    h = 1e-5
+    fd = np.zeros_like(ga)
+    ca = sh["center_of"][pa]
+    for d in range(3):
+        c = sh["centers"].copy()
+        c[ca, d] += h
+        b.set_centers(c)
+        vp, _ = shg.eval_2c(b, pa, pb, opname, omega=omega)
+        c[ca, d] -= 2 * h
+        b.set_centers(c)
+        vm, _ = shg.eval_2c(b, pa, pb, opname, omega=omega)
+        diff = ((vp - vm) / (2 * h)).cpu().numpy() * w
+        fd[:, d] = np.add.reduceat(diff, off)
+    err = np.abs(ga - fd)
+    assert np.all(err <= 1e-7 * np.maximum(1.0, np.abs(fd))), err.max()
+    b.close()
+
+
+def test_autograd_function_matches_finite_differences(shg):
+    import torch
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=40)
+    b = shg.Basis(sh)
+    centers = torch.tensor(sh["centers"], dtype=torch.float64, requires_grad=True)
+    out = shg.TwoCenterIntegrals.apply(centers, b, pa, pb, "coulomb", 0.0)
+    wt = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, out.numel())).cuda()
+    loss = (out * wt).sum()
+    loss.backward()
+    g = centers.grad.numpy()
+    h = 1e-5
+    for c_idx in [0, 1, 7, 30]:
+        for d in range(3):
+            cp = sh["centers"].copy(); cp[c_idx, d] += h
+            cm = sh["centers"].copy(); cm[c_idx, d] -= h
+            b.set_centers(cp)
+            lp = float((shg.eval_2c(b, pa, pb, "coulomb")[0] * wt).sum())
+            b.set_centers(cm)
+            lm = float((shg.eval_2c(b, pa, pb, "coulomb")[0] * wt).sum())
+            fd = (lp - lm) / (2 * h)
+            assert abs(g[c_idx, d] - fd) <= 1e-7 * max(1.0, abs(fd)), (c_idx, d, g[c_idx, d], fd)
+    b.close()
