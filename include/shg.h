@@ -168,6 +168,29 @@ int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thres
 /* Number of kernel launches one shg_plan_2c_exec issues (for accounting). */
 int shg_plan_launches(const shg_plan_t *plan);
 
+/*
+ * shg_plan_2c_set_launch - launch shape of later executions of a plan (the
+ * autotuner's knobs): threads per CTA (32, 64 or 128; each warp owns one
+ * tile of up to 32 pairs) and, for the persistent schedule, CTAs per SM
+ * (0 = as many as occupancy allows).  Returns SHG_EINVAL for other values.
+ */
+int shg_plan_2c_set_launch(shg_plan_t *plan, int threads_per_cta, int ctas_per_sm);
+
+/*
+ * CUDA-graph form of a plan: shg_graph_2c_create captures shg_plan_2c_exec of
+ * n_ops operators (ops[i], omegas[i], all with `precision`, block offsets
+ * d_out_offsets, outputs d_outs[i]) on a private stream and instantiates the
+ * graph; shg_graph_launch replays it on `stream`.  The graph keeps the
+ * pointers it was captured with; geometry changes made with
+ * shg_basis_set_centers are seen by later replays.  The plan must outlive
+ * the graph.
+ */
+typedef struct shg_graph shg_graph_t;
+int shg_graph_2c_create(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas, int precision,
+                        const int64_t *d_out_offsets, double *const *d_outs, shg_graph_t **out);
+int shg_graph_launch(shg_graph_t *graph, void *stream);
+void shg_graph_destroy(shg_graph_t *graph);
+
 /* shg_plan_destroy - free a plan (synchronises its stream first). NULL ok. */
 void shg_plan_destroy(shg_plan_t *plan);
 

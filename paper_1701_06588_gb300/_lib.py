@@ -39,6 +39,10 @@ SIGNATURES = [
     ("shg_plan_2c_exec", _I, [_P, _I, _D, _D, _I, _P, _P, _P]),
     ("shg_plan_launches", _I, [_P]),
     ("shg_plan_destroy", None, [_P]),
+    ("shg_plan_2c_set_launch", _I, [_P, _I, _I]),
+    ("shg_graph_2c_create", _I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
+    ("shg_graph_launch", _I, [_P, _P]),
+    ("shg_graph_destroy", None, [_P]),
     ("shg_eval_3c_aab", _I, [_P, _P, _L, _P, _P, _P, _I, _D, _P, _P, _P]),
     ("shg_eval_2c_grad", _I, [_P, _L, _P, _P, _I, _D, _I, _P, _P, _P, _P, _P]),
     ("shg_eval_3c_aab_grad", _I, [_P, _P, _L, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
@@ -144,6 +148,30 @@ def shg_plan_launches(plan):
 
 def shg_plan_destroy(plan):
     load().shg_plan_destroy(plan)
+
+
+def shg_plan_2c_set_launch(plan, threads_per_cta, ctas_per_sm):
+    return check(load().shg_plan_2c_set_launch(plan, threads_per_cta, ctas_per_sm))
+
+
+def shg_graph_2c_create(plan, ops, omegas, precision, d_out_offsets, d_outs):
+    import numpy as _np
+    n = len(ops)
+    ops_a = _np.ascontiguousarray(ops, dtype=_np.int32)
+    om_a = _np.ascontiguousarray(omegas, dtype=_np.float64)
+    outs_a = (ctypes.c_void_p * n)(*[_ptr(o) for o in d_outs])
+    h = _P()
+    check(load().shg_graph_2c_create(plan, n, _ptr(ops_a), _ptr(om_a), precision, _ptr(d_out_offsets),
+                                     ctypes.cast(outs_a, ctypes.c_void_p), ctypes.byref(h)))
+    return h.value
+
+
+def shg_graph_launch(graph, stream):
+    return check(load().shg_graph_launch(graph, stream))
+
+
+def shg_graph_destroy(graph):
+    load().shg_graph_destroy(graph)
 
 
 def shg_eval_3c_aab(orb, aux, n, d_a, d_atilde, d_b, precision, screen_thresh, d_out_offsets, d_out, stream):

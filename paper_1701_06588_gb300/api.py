@@ -182,3 +182,33 @@ class TwoCenterIntegrals(torch.autograd.Function):
         g.index_add_(0, ca, ga)
         g.index_add_(0, cb, gb)
         return g.to(ctx.device), None, None, None, None, None
+
+
+class Graph2c:
+    """A CUDA graph replaying one plan for several operators (C ABI
+    shg_graph_2c_create / shg_graph_launch)."""
+
+    def __init__(self, plan, ops, omegas, out_offsets, outs, precision="fp64"):
+        self.plan = plan
+        self.outs = list(outs)
+        self.out_offsets = out_offsets
+        self.handle = L.shg_graph_2c_create(plan.handle, [_op(o) for o in ops], [float(w) for w in omegas],
+                                            _prec(precision), out_offsets, self.outs)
+
+    def launch(self, stream=None):
+        L.shg_graph_launch(self.handle, _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.shg_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_launch(plan, threads_per_cta=128, ctas_per_sm=0):
+    L.shg_plan_2c_set_launch(plan.handle, int(threads_per_cta), int(ctas_per_sm))

@@ -745,6 +745,85 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
 
 int shg_plan_launches(const shg_plan_t *p) { return p ? p->launches : 0; }
 
+int shg_plan_2c_set_launch(shg_plan_t *p, int threads, int ctas_per_sm)
+{
+    g_err.clear();
+    if (!p) return fail(SHG_EINVAL, "plan is NULL");
+    if (threads != 32 && threads != 64 && threads != 128) return fail(SHG_EINVAL, "threads per CTA must be 32, 64 or 128");
+    if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(SHG_EINVAL, "ctas_per_sm must be 0..64");
+    p->d.threads = threads;
+    p->d.ctas_per_sm = ctas_per_sm;
+    return SHG_OK;
+}
+
+struct shg_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
+                        const int64_t *off, double *const *outs, shg_graph_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(SHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p || n_ops < 1 || !ops || !omegas || !outs) return fail(SHG_EINVAL, "bad argument");
+    for (int i = 0; i < n_ops; ++i) {
+        int r = check_op(ops[i], omegas[i], precision);
+        if (r) return r;
+    }
+    cudaStream_t s = nullptr;
+    SHG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return fail(SHG_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    int rc = SHG_OK;
+    for (int i = 0; i < n_ops && rc == SHG_OK; ++i) rc = shg_plan_2c_exec(p, ops[i], omegas[i], 0.0, precision, off, outs[i], s);
+    std::string msg = g_err;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    cudaStreamDestroy(s);
+    if (rc != SHG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(rc, "capture: %s", msg.c_str());
+    }
+    if (e != cudaSuccess) return fail(SHG_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(SHG_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    shg_graph_t *g = new (std::nothrow) shg_graph_t;
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(SHG_ENOMEM, "host allocation failed");
+    }
+    g->graph = graph;
+    g->exec = exec;
+    *out = g;
+    return SHG_OK;
+}
+
+int shg_graph_launch(shg_graph_t *g, void *stream)
+{
+    g_err.clear();
+    if (!g) return fail(SHG_EINVAL, "graph is NULL");
+    SHG_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return SHG_OK;
+}
+
+void shg_graph_destroy(shg_graph_t *g)
+{
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+}
+
 void shg_plan_destroy(shg_plan_t *p)
 {
     if (!p) return;
@@ -789,14 +868,14 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
             m.tile_begin = 0;
             m.tile_end = p->d.n_tiles;
             m.counter = p->d.counter;
-            SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op), true, s));
+            SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op, p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
         } else {
             m.counter = nullptr;
             for (int cls = 0; cls < kNClass; ++cls) {
                 m.tile_begin = p->d.class_tile_begin[cls];
                 m.tile_end = p->d.class_tile_begin[cls + 1];
                 if (m.tile_end <= m.tile_begin) continue;
-                SHG_CUDA(launch_2c_mixed(m, op, 0, false, s));
+                SHG_CUDA(launch_2c_mixed(m, op, 0, false, s, p->d.threads));
             }
         }
         return SHG_OK;
@@ -820,14 +899,15 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         a.tile_begin = 0;
         a.tile_end = p->d.n_tiles;
         a.counter = p->d.counter;
-        SHG_CUDA(launch_2c(a, op, precision, persistent_grid_2c(op, precision), true, s));
+        SHG_CUDA(launch_2c(a, op, precision, persistent_grid_2c(op, precision, p->d.threads, p->d.ctas_per_sm), true, s,
+                           p->d.threads));
     } else {
         a.counter = nullptr;
         for (int cls = 0; cls < kNClass; ++cls) {
             a.tile_begin = p->d.class_tile_begin[cls];
             a.tile_end = p->d.class_tile_begin[cls + 1];
             if (a.tile_end <= a.tile_begin) continue;
-            SHG_CUDA(launch_2c(a, op, precision, 0, false, s));
+            SHG_CUDA(launch_2c(a, op, precision, 0, false, s, p->d.threads));
         }
     }
     return SHG_OK;

@@ -155,6 +155,8 @@ struct PlanDev {
     int *counter = nullptr;        // device, persistent work counter
     int n_tiles = 0;
     int class_tile_begin[kNClass + 1] = {};   // host, per-class tile ranges (class-major)
+    int threads = 128;             // launch shape (autotuned): threads per CTA (32, 64 or 128)
+    int ctas_per_sm = 0;           // persistent CTAs per SM, 0 = occupancy limit
     void *owner_block = nullptr;   // device allocation holding all of the above
     cudaStream_t stream = nullptr;
 };
@@ -222,13 +224,14 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, 
                               int *d_err, cudaStream_t s);
 cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
 cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s);
-cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s);
-int persistent_grid_2c_mixed(int op);
+cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s,
+                            int threads = 128);
+int persistent_grid_2c_mixed(int op, int threads = 128, int ctas_per_sm = 0);
 int persistent_grid_2c_grad(int op, int precision);
 int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
-                      cudaStream_t s);
-int persistent_grid_2c(int op, int precision);
+                      cudaStream_t s, int threads = 128);
+int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
 cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t,
                               cudaStream_t s);
 cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s);

@@ -326,32 +326,33 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
 }
 
 template <int OP>
-static cudaError_t launch_2c_op(const Args2c &a, int n, bool persistent, cudaStream_t s)
+static cudaError_t launch_2c_op(const Args2c &a, int n, int threads, bool persistent, cudaStream_t s)
 {
     if (persistent) {
-        k_2c_fp64_persistent<OP><<<n, 128, 0, s>>>(a);
+        k_2c_fp64_persistent<OP><<<n, threads, 0, s>>>(a);
     } else {
         const int tiles = a.tile_end - a.tile_begin;
         if (tiles <= 0) return cudaSuccess;
-        k_2c_fp64_static<OP><<<(tiles + 3) / 4, 128, 0, s>>>(a);
+        const int wpb = threads / 32;
+        k_2c_fp64_static<OP><<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persistent, cudaStream_t s)
+cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persistent, cudaStream_t s, int threads)
 {
     (void)precision;
     switch (op) {
-    case OP_OVERLAP: return launch_2c_op<OP_OVERLAP>(a, n, persistent, s);
-    case OP_COULOMB: return launch_2c_op<OP_COULOMB>(a, n, persistent, s);
-    case OP_ERFC: return launch_2c_op<OP_ERFC>(a, n, persistent, s);
-    case OP_ERF: return launch_2c_op<OP_ERF>(a, n, persistent, s);
-    case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, persistent, s);
+    case OP_OVERLAP: return launch_2c_op<OP_OVERLAP>(a, n, threads, persistent, s);
+    case OP_COULOMB: return launch_2c_op<OP_COULOMB>(a, n, threads, persistent, s);
+    case OP_ERFC: return launch_2c_op<OP_ERFC>(a, n, threads, persistent, s);
+    case OP_ERF: return launch_2c_op<OP_ERF>(a, n, threads, persistent, s);
+    case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int persistent_grid_2c(int op, int precision)
+int persistent_grid_2c(int op, int precision, int threads, int ctas_per_sm)
 {
     (void)precision;
     int dev = 0, sms = 0, per = 0;
@@ -359,13 +360,14 @@ int persistent_grid_2c(int op, int precision)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaSuccess;
     switch (op) {
-    case OP_OVERLAP: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_OVERLAP>, 128, 0); break;
-    case OP_COULOMB: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_COULOMB>, 128, 0); break;
-    case OP_ERFC: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERFC>, 128, 0); break;
-    case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, 128, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, 128, 0); break;
+    case OP_OVERLAP: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_OVERLAP>, threads, 0); break;
+    case OP_COULOMB: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_COULOMB>, threads, 0); break;
+    case OP_ERFC: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERFC>, threads, 0); break;
+    case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, threads, 0); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     if (sms < 1) sms = 1;
     return sms * per;
 }

@@ -342,52 +342,54 @@ __global__ void __launch_bounds__(128) k_2c_mixed_static(const ArgsMix g)
 }
 
 template <int OP>
-static int grid_mix()
+static int grid_mix(int threads, int ctas_per_sm)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_persistent<OP>, 128, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_persistent<OP>, threads, 0) != cudaSuccess ||
         per < 1)
         per = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     return (sms > 0 ? sms : 1) * per;
 }
 
 template <int OP>
-static cudaError_t launch_mix_op(const ArgsMix &a, int grid, bool persistent, cudaStream_t s)
+static cudaError_t launch_mix_op(const ArgsMix &a, int grid, int threads, bool persistent, cudaStream_t s)
 {
     if (persistent) {
-        k_2c_mixed_persistent<OP><<<grid, 128, 0, s>>>(a);
+        k_2c_mixed_persistent<OP><<<grid, threads, 0, s>>>(a);
     } else {
         const int tiles = a.tile_end - a.tile_begin;
         if (tiles <= 0) return cudaSuccess;
-        k_2c_mixed_static<OP><<<(tiles + 3) / 4, 128, 0, s>>>(a);
+        const int wpb = threads / 32;
+        k_2c_mixed_static<OP><<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent, cudaStream_t s)
+cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent, cudaStream_t s, int threads)
 {
     switch (op) {
-    case OP_OVERLAP: return launch_mix_op<OP_OVERLAP>(a, grid, persistent, s);
-    case OP_COULOMB: return launch_mix_op<OP_COULOMB>(a, grid, persistent, s);
-    case OP_ERFC: return launch_mix_op<OP_ERFC>(a, grid, persistent, s);
-    case OP_ERF: return launch_mix_op<OP_ERF>(a, grid, persistent, s);
-    case OP_GAUSS: return launch_mix_op<OP_GAUSS>(a, grid, persistent, s);
+    case OP_OVERLAP: return launch_mix_op<OP_OVERLAP>(a, grid, threads, persistent, s);
+    case OP_COULOMB: return launch_mix_op<OP_COULOMB>(a, grid, threads, persistent, s);
+    case OP_ERFC: return launch_mix_op<OP_ERFC>(a, grid, threads, persistent, s);
+    case OP_ERF: return launch_mix_op<OP_ERF>(a, grid, threads, persistent, s);
+    case OP_GAUSS: return launch_mix_op<OP_GAUSS>(a, grid, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int persistent_grid_2c_mixed(int op)
+int persistent_grid_2c_mixed(int op, int threads, int ctas_per_sm)
 {
     switch (op) {
-    case OP_OVERLAP: return grid_mix<OP_OVERLAP>();
-    case OP_COULOMB: return grid_mix<OP_COULOMB>();
-    case OP_ERFC: return grid_mix<OP_ERFC>();
-    case OP_ERF: return grid_mix<OP_ERF>();
-    default: return grid_mix<OP_GAUSS>();
+    case OP_OVERLAP: return grid_mix<OP_OVERLAP>(threads, ctas_per_sm);
+    case OP_COULOMB: return grid_mix<OP_COULOMB>(threads, ctas_per_sm);
+    case OP_ERFC: return grid_mix<OP_ERFC>(threads, ctas_per_sm);
+    case OP_ERF: return grid_mix<OP_ERF>(threads, ctas_per_sm);
+    default: return grid_mix<OP_GAUSS>(threads, ctas_per_sm);
     }
 }
 

@@ -1,0 +1,106 @@
+"""GPU parity of the mixed-precision (double-float on FP32 pipes) two-center
+path against the oracle, with the mixed bar of tests/parity.py, and the
+per-(la, lb, operator) error table.  Set SHG_ERROR_TABLE=<path> to also write
+the table as JSON."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1701_06588_gb300 import workloads as W
+from tests.parity import TOL_MIXED, assert_parity, reference_2c
+
+pytestmark = pytest.mark.gpu
+
+OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+
+
+@pytest.fixture(scope="module")
+def shg():
+    import torch
+    from paper_1701_06588_gb300 import api, build
+    build.build()
+    torch.cuda.init()
+    return api
+
+
+def _run(api, shells, pa, pb, opname, omega, precision="mixed", schedule="persistent"):
+    import torch
+    b = api.Basis(shells)
+    off, total = b.pair_offsets(pa, pb)
+    plan = api.Plan2c(b, pa, pb, schedule=schedule)
+    out = torch.full((max(total, 1),), float("nan"), dtype=torch.float64, device="cuda")
+    plan.exec(opname, torch.from_numpy(off).cuda(), out, omega=omega, precision=precision)
+    torch.cuda.synchronize()
+    res = out[:total].cpu().numpy()
+    plan.close()
+    b.close()
+    return res, off
+
+
+@pytest.mark.parametrize("opname,op,omega", OPS)
+@pytest.mark.parametrize("schedule", ["per_class", "persistent"])
+def test_mixed_c1(shg, opname, op, omega, schedule):
+    sh, pa, pb = W.make("c1_2k_l3_k4")
+    got, _ = _run(shg, sh, pa, pb, opname, omega, schedule=schedule)
+    ref, scale = reference_2c(sh, pa, pb, op, omega)
+    assert_parity(got, ref, TOL_MIXED, "mixed c1 %s" % opname, scale)
+
+
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+def test_mixed_c3_high_l(shg, opname, op, omega):
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=1500)
+    got, _ = _run(shg, sh, pa, pb, opname, omega)
+    ref, scale = reference_2c(sh, pa, pb, op, omega)
+    assert_parity(got, ref, TOL_MIXED, "mixed c3 %s" % opname, scale)
+
+
+def test_mixed_one_center_all_classes(shg):
+    rng = np.random.default_rng(11)
+    ls = [l for la in range(7) for lb in range(7) for l in (la, lb)]
+    n = len(ls) // 2
+    for K in (1, 12):
+        shells = dict(l=np.array(ls, np.int32), nprim=np.full(2 * n, K, np.int32),
+                      exps=np.exp(rng.uniform(np.log(0.05), np.log(500), 2 * n * K)),
+                      coefs=rng.uniform(-1, 1, 2 * n * K), centers=np.zeros((1, 3)),
+                      center_of=np.zeros(2 * n, np.int32))
+        pa = np.arange(0, 2 * n, 2, dtype=np.int32)
+        pb = pa + 1
+        for opname, op, omega in OPS:
+            got, _ = _run(shg, shells, pa, pb, opname, omega)
+            ref, scale = reference_2c(shells, pa, pb, op, omega)
+            assert_parity(got, ref, TOL_MIXED, "mixed R=0 K=%d %s" % (K, opname), scale)
+
+
+def test_mixed_error_table_c2(shg):
+    """Per-(la, lb, operator) error of the mixed path on 3,000 pairs of the
+    200k recipe: max relative error over elements above 1e-8 of their block
+    maximum and above 1e-12 (blocks wholly below the absolute floor are
+    excluded from the relative column), and the max parity excess (<= 1 passes)."""
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=3000)
+    l = sh["l"]
+    table = {}
+    worst = 0.0
+    for opname, op, omega in OPS:
+        got, off = _run(shg, sh, pa, pb, opname, omega)
+        ref, scale = reference_2c(sh, pa, pb, op, omega)
+        bar = TOL_MIXED[0] * np.abs(ref) + TOL_MIXED[1] + TOL_MIXED[2] * scale
+        sizes = (2 * l[pa].astype(np.int64) + 1) * (2 * l[pb].astype(np.int64) + 1)
+        for la in range(5):
+            for lb in range(5):
+                sel = np.where((l[pa] == la) & (l[pb] == lb))[0]
+                if not len(sel):
+                    continue
+                idx = np.concatenate([np.arange(off[p], off[p] + sizes[p]) for p in sel])
+                r, g, bb, sc = ref[idx], got[idx], bar[idx], scale[idx]
+                big = np.abs(r) > np.maximum(1e-8 * sc, 1e-12)
+                rel = float(np.max(np.abs(g[big] - r[big]) / np.abs(r[big]))) if big.any() else 0.0
+                ex = float(np.max(np.abs(g - r) / bb))
+                table["%s l%d%d" % (opname, la, lb)] = {"max_rel": rel, "max_excess": ex, "pairs": int(len(sel))}
+                worst = max(worst, ex)
+    path = os.environ.get("SHG_ERROR_TABLE")
+    if path:
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    assert worst <= 1.0, worst
