@@ -31,7 +31,8 @@ UNIT = "shell-pair integrals/s"
 WORKLOAD = "c2_200k_l4_k8"
 OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
 FP64_NOMINAL_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, context)
-PROFILE = os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt")
+PROFILES = {"fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt"),
+            "mixed": os.path.join(ROOT, "profiles", "k_2c_mixed_persistent_c2_200k.txt")}
 
 
 def parse():
@@ -40,10 +41,16 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--schedule", default="persistent", choices=["persistent", "per_class"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--n-pairs", type=int, default=None, help="smaller case of the same recipe (profiling only)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                   help="precision of the headline path (the other forms are reported beside it)")
+    p.add_argument("--no-extras", action="store_true", help="time only the headline path (profiling)")
+    p.add_argument("--no-tune", action="store_true", help="default launch shape instead of the autotuner (profiling)")
+    p.add_argument("--configs", action="store_true",
+                   help="also time the other workloads (2k, 2M high-l, (aab) 20k atom pairs, gradients) and add "
+                        "them under other_configs")
     return p.parse_args()
 
 
@@ -173,12 +180,12 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
-def read_profile_traffic():
+def read_profile_traffic(precision):
     """DRAM bytes per step of the timed kernels from the committed ncu summary,
     or None when it is absent or was taken on other kernel sources."""
     try:
         kv = {}
-        for ln in open(PROFILE):
+        for ln in open(PROFILES[precision]):
             if ":" in ln:
                 k, v = ln.split(":", 1)
                 kv[k.strip()] = v.strip()
@@ -192,7 +199,7 @@ def read_profile_traffic():
 def run_ours(args, rank, world):
     import numpy as np
     import torch
-    from paper_1701_06588_gb300 import api, build, counts, workloads as W
+    from paper_1701_06588_gb300 import api, autotune, build, counts, workloads as W
     from paper_1701_06588_gb300 import _lib as L
 
     build.build()
@@ -209,25 +216,63 @@ def run_ours(args, rank, world):
     basis = api.Basis(shells)
     off, total = basis.pair_offsets(pa, pb)
     d_off = torch.from_numpy(off).cuda()
-    plan = api.Plan2c(basis, pa, pb, schedule=args.schedule)
     outs = [torch.empty(total, dtype=torch.float64, device="cuda") for _ in OPS]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     s_handle = stream.cuda_stream
+    names = [o[0] for o in OPS]
+    omegas = [o[2] for o in OPS]
 
-    peaks = [L.shg_measure_alu_peak(0, 4096, s_handle) for _ in range(3)]
-    fp64_peak = max(peaks)
+    fp64_peak = max(L.shg_measure_alu_peak(0, 4096, s_handle) for _ in range(3))
+    fp32_peak = max(L.shg_measure_alu_peak(1, 65536, s_handle) for _ in range(2))
 
-    def step():
-        for (name, _, om), o in zip(OPS, outs):
-            plan.exec(name, d_off, o, omega=om)
+    def time_steps(step_fn, steps, per_op=False):
+        """K steps, L2 flushed between steps outside the events; per-step ms
+        (and per-operator ms when per_op)."""
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in (OPS if per_op else [0])] for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()
+            step_fn(ev[s])
+        torch.cuda.synchronize()
+        if per_op:
+            per = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(steps)) for i in range(len(OPS))]
+            return sum(per), per
+        return statistics.mean(ev[s][0][0].elapsed_time(ev[s][0][1]) for s in range(steps)), None
 
+    def plan_step(plan, precision):
+        def fn(evs):
+            for (name, _, om), o, (e0, e1) in zip(OPS, outs, evs):
+                e0.record(stream)
+                plan.exec(name, d_off, o, omega=om, precision=precision)
+                e1.record(stream)
+        return fn
+
+    def graph_step(graph):
+        def fn(evs):
+            e0, e1 = evs[0]
+            e0.record(stream)
+            graph.launch()
+            e1.record(stream)
+        return fn
+
+    # autotuned launch shape for each precision (cached per GPU and workload)
+    tuned = {}
+    for prec in ("fp64", "mixed"):
+        if args.no_extras and prec != args.precision:
+            continue
+        if args.no_tune:
+            tuned[prec] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0}
+        else:
+            tuned[prec] = autotune.tune_2c(basis, pa, pb, names, omegas, d_off, outs, precision=prec)
+
+    # headline: the autotuned plan of the requested precision, replayed as one CUDA graph per step
+    plan = autotune.tuned_plan(basis, pa, pb, tuned[args.precision])
+    graph = api.Graph2c(plan, names, omegas, d_off, outs, precision=args.precision)
     for _ in range(max(args.warmup, 0)):
-        step()
+        graph.launch()
+        plan_step(plan, args.precision)([(torch.cuda.Event(enable_timing=True),) * 2 for _ in OPS])
     torch.cuda.synchronize()
-
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in OPS]
-          for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -235,20 +280,14 @@ def run_ours(args, rank, world):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        flush.zero_()                                   # evict L2 between steps (not timed by the events)
-        for (name, _, om), o, (e0, e1) in zip(OPS, outs, ev[s]):
-            e0.record(stream)
-            plan.exec(name, d_off, o, omega=om)
-            e1.record(stream)
+    ms_step, _ = time_steps(graph_step(graph), args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    per_op_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
-                 for i in range(len(OPS))]
-    ms_step = sum(per_op_ms)
+    # kernel time per operator of the same plan (same kernels, launched one by one)
+    kern_ms, per_op_ms = time_steps(plan_step(plan, args.precision), args.steps, per_op=True)
     if dist:
         t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -257,8 +296,42 @@ def run_ours(args, rank, world):
 
     flops = [counts.workload_flops(shells, pa, pb, op) for _, op, _ in OPS]
     flops_step = sum(flops)
-    achieved = flops_step / (sum(per_op_ms) * 1e-3) / 1e12
-    traffic = read_profile_traffic()
+    achieved = flops_step / (kern_ms * 1e-3) / 1e12
+    peak = (fp64_peak if args.precision == "fp64" else fp32_peak) / 1e12
+    traffic = read_profile_traffic(args.precision)
+
+    forms = {}
+    if not args.no_extras:
+        # plain per-class FP64 (the baseline the mixed, autotuned, graph form is compared with)
+        pc = api.Plan2c(basis, pa, pb, schedule="per_class")
+        plan_step(pc, "fp64")([(torch.cuda.Event(enable_timing=True),) * 2 for _ in OPS])
+        ms_pc, _ = time_steps(plan_step(pc, "fp64"), args.steps, per_op=True)
+        forms["fp64_per_class"] = {"ms_per_step": ms_pc, "value": units_per_step / (ms_pc * 1e-3),
+                                   "launches_per_step": len(OPS) * pc.launches}
+        pc.close()
+        pp = api.Plan2c(basis, pa, pb, schedule="persistent")
+        ms_pp, _ = time_steps(plan_step(pp, "fp64"), args.steps, per_op=True)
+        forms["fp64_persistent"] = {"ms_per_step": ms_pp, "value": units_per_step / (ms_pp * 1e-3)}
+        pp.close()
+        other = "mixed" if args.precision == "fp64" else "fp64"
+        po = autotune.tuned_plan(basis, pa, pb, tuned[other])
+        go = api.Graph2c(po, names, omegas, d_off, outs, precision=other)
+        go.launch()
+        torch.cuda.synchronize()
+        ms_o, _ = time_steps(graph_step(go), args.steps)
+        forms[other + "_tuned_graph"] = {"ms_per_step": ms_o, "value": units_per_step / (ms_o * 1e-3),
+                                         "launch": {k: tuned[other][k] for k in ("schedule", "threads_per_cta",
+                                                                                  "ctas_per_sm")}}
+        go.close()
+        po.close()
+        forms[args.precision + "_tuned_graph"] = {"ms_per_step": ms_step, "value": units_per_step / (ms_step * 1e-3),
+                                                  "launch": {k: tuned[args.precision][k] for k in
+                                                             ("schedule", "threads_per_cta", "ctas_per_sm")}}
+        if "mixed_tuned_graph" in forms:
+            forms["mixed_speedup_vs_fp64_per_class"] = ms_pc / forms["mixed_tuned_graph"]["ms_per_step"]
+            forms["mixed_speedup_vs_fp64_tuned_graph"] = (forms["fp64_tuned_graph"]["ms_per_step"] /
+                                                          forms["mixed_tuned_graph"]["ms_per_step"])
+        torch.cuda.synchronize()
 
     # end to end through the public API with host buffers
     cent_h = torch.from_numpy(np.ascontiguousarray(shells["centers"])).pin_memory()
@@ -270,6 +343,7 @@ def run_ours(args, rank, world):
     d_pb = torch.empty_like(pb_h, device="cuda")
     d_off2 = torch.empty_like(off_h, device="cuda")
     e2e_times = []
+    parts = {"h2d_and_set_centers": [], "plan_create": [], "exec_and_d2h": []}
     for it in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -277,14 +351,20 @@ def run_ours(args, rank, world):
         d_pb.copy_(pb_h, non_blocking=True)
         d_off2.copy_(off_h, non_blocking=True)
         basis.set_centers(cent_h.numpy())
-        p2 = api.Plan2c(basis, d_pa, d_pb, schedule=args.schedule)
+        t2 = time.perf_counter()
+        p2 = autotune.tuned_plan(basis, d_pa, d_pb, tuned[args.precision])
+        t3 = time.perf_counter()
         for (name, _, om), o, oh in zip(OPS, outs, outs_h):
-            p2.exec(name, d_off2, o, omega=om)
+            p2.exec(name, d_off2, o, omega=om, precision=args.precision)
             oh.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
+        t4 = time.perf_counter()
         p2.close()
         if it > 0:
-            e2e_times.append(time.perf_counter() - t1)
+            e2e_times.append(t4 - t1)
+            parts["h2d_and_set_centers"].append(t2 - t1)
+            parts["plan_create"].append(t3 - t2)
+            parts["exec_and_d2h"].append(t4 - t3)
     e2e_s = statistics.mean(e2e_times) if e2e_times else float("nan")
     if dist:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
@@ -293,38 +373,123 @@ def run_ours(args, rank, world):
     h2d = cent_h.numel() * 8 + pa_h.numel() * 4 + pb_h.numel() * 4 + off_h.numel() * 8
     d2h = sum(o.numel() * 8 for o in outs_h)
 
+    dtype = "f64" if args.precision == "fp64" else "f32x2 (double-float) with f64 output"
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": workload_description(n_pairs), "pairs": n_pairs, "operators": [o[0] for o in OPS],
-                   "schedule": args.schedule, "precision": "fp64", "units_per_step": units_per_step,
-                   "elements_per_step": total * len(OPS),
+        "config": {"workload": workload_description(n_pairs), "pairs": n_pairs, "operators": names,
+                   "precision": args.precision, "form": "autotuned launch shape, one CUDA graph per step",
+                   "launch": {k: tuned[args.precision][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
+                   "units_per_step": units_per_step, "elements_per_step": total * len(OPS),
                    "l2": "flushed between steps by a 512 MB device write outside the timed events",
                    "wall_s_timed_loop": wall},
-        "per_operator_ms": {o[0]: m for o, m in zip(OPS, per_op_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / (fp64_peak / 1e12), "traffic": traffic,
-                     "peak_source": "measured FP64 FMA-chain probe (shg_measure_alu_peak) in this run; nominal %.2f "
-                                    "TFLOP/s = 152 SMs x 2 FMA/clk x 2 x 2.07 GHz" % FP64_NOMINAL_TFLOPS,
-                     "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
-                     "algorithmic_flops_per_step": flops_step,
-                     "kernel": "k_2c_fp64_persistent<op> (5 launches per step)"},
+        "per_operator_kernel_ms": {n: m for n, m in zip(names, per_op_ms)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "peak_source": ("measured FP64 FMA-chain probe (shg_measure_alu_peak) in this run; nominal %.2f "
+                                     "TFLOP/s = 152 SMs x 2 FMA/clk x 2 x 2.07 GHz" % FP64_NOMINAL_TFLOPS)
+                     if args.precision == "fp64" else
+                     "measured FP32 FMA-chain probe (shg_measure_alu_peak) in this run; algorithmic flops are "
+                     "the FP64 formula count, each evaluated in double-float",
+                     "algorithmic_flops_per_step": flops_step, "kernel_ms_per_step": kern_ms,
+                     "kernel": "k_2c_%s_persistent<op> / static (5 operators per step)" %
+                               ("fp64" if args.precision == "fp64" else "mixed")},
+        "forms": forms,
         "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "what": "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
-                        "shg_plan_2c_create, 5 x shg_plan_2c_exec, D2H of all blocks to pinned memory"},
+                        "shg_plan_2c_create, 5 x shg_plan_2c_exec, D2H of all blocks to pinned memory",
+                "ms_parts": {k: 1e3 * statistics.mean(v) for k, v in parts.items() if v}},
         "gpu_launches": args.steps * len(OPS) * plan.launches,
         "clocks": clk,
+        "measured_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12},
     }
+    if args.configs:
+        result["other_configs"] = other_configs(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(shells, pa, pb)
     if rank == 0:
         print(json.dumps(result), flush=True)
+    graph.close()
     plan.close()
     basis.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _events_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_configs(args):
+    """Throughput of the other synthetic workloads (CUDA events, inputs resident)."""
+    import numpy as np
+    import torch
+    from paper_1701_06588_gb300 import api, workloads as W
+    res = {}
+    for name, ops in [("c1_2k_l3_k4", [("overlap", 0.0), ("coulomb", 0.0)]),
+                      ("c3_2m_l6_k20", [("coulomb", 0.0), ("erfc", 0.11)])]:
+        sh, pa, pb = W.make(name)
+        b = api.Basis(sh)
+        off, total = b.pair_offsets(pa, pb)
+        d_off = torch.from_numpy(off).cuda()
+        out = torch.empty(total, dtype=torch.float64, device="cuda")
+        plan = api.Plan2c(b, pa, pb)
+        entry = {"pairs": len(pa), "operators": [o[0] for o in ops]}
+        for prec in ("fp64", "mixed"):
+            ms = sum(_events_ms(lambda n=n, w=w: plan.exec(n, d_off, out, omega=w, precision=prec), 3 if len(pa) > 1e5
+                                else 50) for n, w in ops)
+            entry[prec] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3)}
+        res[name] = entry
+        plan.close()
+        b.close()
+        del out
+    # (aab): 20,000 atom pairs = 3,000,000 triples
+    sh, ta, tt, tb, per = W.make("c4_aab_20k")
+    b = api.Basis(sh)
+    off, total = b.triple_offsets(b, ta, tt, tb)
+    d_off = torch.from_numpy(off).cuda()
+    d_ta, d_tt, d_tb = (torch.from_numpy(x).cuda() for x in (ta, tt, tb))
+    out = torch.empty(total, dtype=torch.float64, device="cuda")
+    from paper_1701_06588_gb300 import _lib as L
+    st = torch.cuda.current_stream().cuda_stream
+    ms = _events_ms(lambda: L.shg_eval_3c_aab(b.handle, b.handle, len(ta), d_ta, d_tt, d_tb, 0, 0.0, d_off, out, st), 3)
+    res["c4_aab_20k"] = {"triples": len(ta), "atom_pairs": len(ta) // per, "fp64": {
+        "ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3), "elements": total}}
+    w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    ga = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
+    gb = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
+    ms = _events_ms(lambda: L.shg_eval_3c_aab_grad(b.handle, b.handle, len(ta), d_ta, d_tt, d_tb, 0, d_off, w, ga, gb,
+                                                   st), 2)
+    res["c4_aab_20k"]["grad_fp64"] = {"ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3)}
+    b.close()
+    del out, w
+    # gradients: 500,000 pairs, Coulomb and erfc(0.11)
+    sh, pa, pb = W.make("c5_grad_500k_l5_k12")
+    b = api.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    d_off = torch.from_numpy(off).cuda()
+    d_pa, d_pb = torch.from_numpy(pa).cuda(), torch.from_numpy(pb).cuda()
+    w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    ga = torch.empty((len(pa), 3), dtype=torch.float64, device="cuda")
+    gb = torch.empty((len(pa), 3), dtype=torch.float64, device="cuda")
+    entry = {"pairs": len(pa)}
+    for opn, op, om in [("coulomb", 1, 0.0), ("erfc", 2, 0.11)]:
+        ms = _events_ms(lambda: L.shg_eval_2c_grad(b.handle, len(pa), d_pa, d_pb, op, om, 0, d_off, w, ga, gb, st), 3)
+        entry[opn] = {"ms_per_pass": ms, "pair_gradients_per_s": len(pa) / (ms * 1e-3)}
+    res["c5_grad_500k_l5_k12"] = entry
+    b.close()
+    return res
 
 
 def main():

@@ -212,3 +212,17 @@ class Graph2c:
 
 def set_launch(plan, threads_per_cta=128, ctas_per_sm=0):
     L.shg_plan_2c_set_launch(plan.handle, int(threads_per_cta), int(ctas_per_sm))
+
+
+def eval_3c_aab_grad(orb, aux, t_a, t_atilde, t_b, upstream, offsets=None, precision="fp64", stream=None):
+    """Vector-Jacobian product of the (a b a~) blocks with upstream weights (flat
+    tensor in the layout of eval_3c_aab): per-triple gradients with respect to
+    R_a (the common center of a and a~) and R_b, each (n, 3) CUDA tensors."""
+    if offsets is None:
+        offsets, _ = orb.triple_offsets(aux, t_a, t_atilde, t_b)
+    n = len(offsets)
+    ga = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    gb = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    L.shg_eval_3c_aab_grad(orb.handle, aux.handle, n, _dev_i32(t_a), _dev_i32(t_atilde), _dev_i32(t_b),
+                           _prec(precision), _dev_i64(offsets), upstream.contiguous(), ga, gb, _stream(stream))
+    return ga, gb

@@ -176,6 +176,221 @@ __device__ void triple_aab_fp64(const Args3c &g, int p)
         }
 }
 
+// d R^{c/s}_{l,m} / dv_d (d = x, y, z) for 0 <= m <= l <= lmax from the (l-1)
+// harmonics (lowering rules of the regular scaled solid harmonics).
+__device__ __forceinline__ void harmonic_gradients3(const double *Rc, const double *Rs, int lmax, double (*dRc)[66],
+                                                    double (*dRs)[66])
+{
+    for (int l = 0; l <= lmax; ++l)
+        for (int m = 0; m <= l; ++m) {
+            const int i = l * (l + 1) / 2 + m;
+            if (l == 0) {
+                for (int d = 0; d < 3; ++d) dRc[d][i] = dRs[d][i] = 0.0;
+                continue;
+            }
+            const double cp = rc_get(Rc, l - 1, m + 1), cm = rc_get(Rc, l - 1, m - 1);
+            const double sp = rs_get(Rs, l - 1, m + 1), sm = rs_get(Rs, l - 1, m - 1);
+            dRc[0][i] = 0.5 * (cp - cm);
+            dRs[0][i] = 0.5 * (sp - sm);
+            dRc[1][i] = 0.5 * (sp + sm);
+            dRs[1][i] = -0.5 * (cp + cm);
+            dRc[2][i] = rc_get(Rc, l - 1, m);
+            dRs[2][i] = rs_get(Rs, l - 1, m);
+        }
+}
+
+// Vector-Jacobian product of one (a b a~) block with respect to the common
+// center R_a of a and a~: the upstream block U is projected through the real
+// Gaunt coefficients onto each L_a term, U_L[M][mb] = sum G U[ma][ma~][mb],
+// and each term contributes the two-center VJP of Eq. dev_ab with P_L:
+//   2 (R_a - R_b) sum_j P_L^{(L+lb-j+1)} <U_L, Q~_j> + sum_j P_L^{(L+lb-j)} <U_L, dQ~_j>.
+__device__ void triple_aab_grad_fp64(const Args3c &g, int p)
+{
+    const ShellRec sa = g.orb_shells[g.t_a[p]];
+    const ShellRec st = g.orb_shells[g.t_t[p]];
+    const ShellRec sb = g.aux_shells[g.t_b[p]];
+    const int la = sa.l, lt = st.l, lb = sb.l;
+    const Vec4 A = g.orb_centers[sa.center];
+    const Vec4 B = g.aux_centers[sb.center];
+    const double v[3] = {A.x - B.x, A.y - B.y, A.z - B.z};
+    const double R2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const int Lmin = la > lt ? la - lt : lt - la;
+    const int Lmax = la + lt;
+    const int nL = (Lmax - Lmin) / 2 + 1;
+    const int pmax = nL - 1;
+    const int kmaxA = Lmax + lb + 1;
+    const int kminA = Lmin > lb ? Lmin : lb;
+
+    // P[iL][j] = P_L^{(L+lb+1-j)}, j = 0..J_L
+    double P[kNL][kJmax + 1];
+    for (int i = 0; i < kNL; ++i)
+        for (int j = 0; j <= kJmax; ++j) P[i][j] = 0.0;
+    const int Ka = sa.nprim, Kt = st.nprim, Kb = sb.nprim;
+    const int ntrip = Ka * Kt * Kb;
+    for (int q = 0; q < ntrip; ++q) {
+        const int ib = q % Kb;
+        const int it = (q / Kb) % Kt;
+        const int ia = q / (Kb * Kt);
+        const PrimRec pa = g.orb_prims[sa.prim_off + ia];
+        const PrimRec pt = g.orb_prims[st.prim_off + it];
+        const PrimRec pb = g.aux_prims[sb.prim_off + ib];
+        const double ap = pa.alpha + pt.alpha;
+        const double be = pb.alpha;
+        const double c = ap + be;
+        const double rc = rsqrt(c);
+        const double ic = rc * rc;
+        const double rho = ap * be * ic;
+        const double gg = be * be * ic;
+        const double x = gg * R2;
+        const double h = 0.5 * ic;
+        const double rap = rsqrt(ap);
+        const double iap = rap * rap;
+        const double w0 = pa.wN * pt.wN * pb.w2c * kPi32 * ic * rc * exp(-rho * R2);
+        double D[kPmax + 1][kPmax + 1];
+        for (int m = 0; m <= pmax; ++m)
+            for (int i = 0; i <= m; ++i) {
+                double s = g.k3.dd[m][i][m];
+                for (int j = m - 1; j >= i; --j) s = fma(s, x, g.k3.dd[m][i][j]);
+                D[m][i] = s;
+            }
+        double nr[kKmax3 + 2];
+        nr[0] = 1.0;
+        for (int n = 1; n <= kmaxA; ++n) nr[n] = nr[n - 1] * -rho;
+        double gp[kPmax + 1], hm[kPmax + 1], ia_p[kPmax + 1];
+        gp[0] = hm[0] = ia_p[0] = 1.0;
+        for (int m = 1; m <= pmax; ++m) {
+            gp[m] = gp[m - 1] * gg;
+            hm[m] = hm[m - 1] * h;
+            ia_p[m] = ia_p[m - 1] * iap;
+        }
+        double V[kPmax + 1][kKmax3 + 2];
+        for (int m = 0; m <= pmax; ++m)
+            for (int k = kminA; k <= kmaxA; ++k) {
+                double vv = 0.0;
+                const int imax = m < k ? m : k;
+                for (int i = 0; i <= imax; ++i) vv = fma(g.k3.binom[k][i] * nr[k - i], gp[i] * D[m][i], vv);
+                V[m][k] = hm[m] * vv;
+            }
+        const double i2ap = 0.5 * iap;
+        double wL = w0 * powi(i2ap, Lmin);
+        const double i2ap2 = i2ap * i2ap;
+        for (int iL = 0; iL < nL; ++iL) {
+            const int L = Lmin + 2 * iL;
+            const int pL = pmax - iL;
+            const int J = (L < lb ? L : lb) + 1;
+            const int kmaxL = L + lb + 1;
+            for (int j = 0; j <= J; ++j) {
+                const int k = kmaxL - j;
+                double s = 0.0;
+                for (int jj = 0; jj <= pL; ++jj) s = fma(g.k3.bj[L][pL][jj] * ia_p[jj], V[pL - jj][k], s);
+                P[iL][j] = fma(wL, s, P[iL][j]);
+            }
+            wL *= i2ap2;
+        }
+    }
+
+    double Rc[66], Rs[66];
+    const int lR = Lmax > lb ? Lmax : lb;
+    scaled_harmonics(v[0], v[1], v[2], lR, g.k, Rc, Rs);
+    double dRc[3][66], dRs[3][66];
+    harmonic_gradients3(Rc, Rs, lR, dRc, dRs);
+    const int nb = 2 * lb + 1, nt = 2 * lt + 1;
+    const int Jmax = (Lmax < lb ? Lmax : lb) + 1;
+    double Wb[2 * kLmax2c + 1][kJmax * kJmax];
+    for (int mb = -lb; mb <= lb; ++mb) w_row_rt(Rc, Rs, lb, mb, Jmax, Wb[mb + lb]);
+
+    // U_L[M][mb]: upstream block projected through the Gaunt coefficients
+    double Ust[(1 + 5 + 9 + 13 + 17 + 21) * (2 * kLmax2c + 1)];
+    int ntot = 0;
+    for (int iL = 0; iL < nL; ++iL) ntot += (2 * (Lmin + 2 * iL) + 1) * nb;
+    for (int i = 0; i < ntot; ++i) Ust[i] = 0.0;
+    const double *Wup = g.w + g.w_off[p];
+    const int rbase = g.gaunt_base[la * 7 + lt];
+    for (int ma = 0; ma < 2 * la + 1; ++ma)
+        for (int mt = 0; mt < nt; ++mt) {
+            const int r = rbase + ma * nt + mt;
+            const double *u = Wup + (ma * nt + mt) * nb;
+            for (int q = g.gaunt_row[r]; q < g.gaunt_row[r + 1]; ++q) {
+                const GauntEnt ge = g.gaunt[q];
+                const int iL = (ge.L - Lmin) / 2;
+                double *ul = Ust + iL * (2 * Lmin + 1 + 2 * (iL - 1)) * nb + (ge.M + ge.L) * nb;
+                for (int mb = 0; mb < nb; ++mb) ul[mb] = fma(ge.g, u[mb], ul[mb]);
+            }
+        }
+
+    const double sgn_b = (lb & 1) ? -1.0 : 1.0;
+    const double lam0 = 3.5449077018110320545963349666822903 / (g.k3.sqrt_int[2 * la + 1] * g.k3.sqrt_int[2 * lt + 1]);
+    double G1 = 0.0, G2[3] = {0.0, 0.0, 0.0};
+    for (int iL = 0; iL < nL; ++iL) {
+        const int L = Lmin + 2 * iL;
+        const int J = (L < lb ? L : lb) + 1;
+        const int JJ = J * J;
+        const double lamK = lam0 * g.k3.sqrt_int[2 * L + 1];
+        double f0[kJmax * kJmax], f1[kJmax * kJmax];
+        for (int j = 0; j < J; ++j) {
+            const double b2 = lamK * g.k.pow2[L + lb - j];
+            for (int kp = 0; kp <= j; ++kp) {
+                const double bb = b2 * g.k.jB[j][kp];
+                const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+                f0[e0] = bb * P[iL][j + 1];
+                f1[e0] = bb * P[iL][j];
+                if (kp) {
+                    f0[e0 + 1] = f0[e0];
+                    f1[e0 + 1] = f1[e0];
+                }
+            }
+        }
+        const double *UL = Ust + iL * (2 * Lmin + 1 + 2 * (iL - 1)) * nb;
+        double Y[2 * kLmax2c + 1][kJmax * kJmax];
+        for (int mb = 0; mb < nb; ++mb)
+            for (int e = 0; e < JJ; ++e) Y[mb][e] = 0.0;
+        for (int M = -L; M <= L; ++M) {
+            double wa[kJmax * kJmax], z[kJmax * kJmax];
+            w_row_rt(Rc, Rs, L, M, J, wa);
+            const double Aa = g.k.A[L][M < 0 ? -M : M] * sgn_b;
+            for (int e = 0; e < JJ; ++e) z[e] = 0.0;
+            for (int mb = -lb; mb <= lb; ++mb) {
+                const double ua = UL[(M + L) * nb + (mb + lb)] * Aa * g.k.A[lb][mb < 0 ? -mb : mb];
+                for (int e = 0; e < JJ; ++e) {
+                    z[e] = fma(ua, Wb[mb + lb][e], z[e]);
+                    Y[mb + lb][e] = fma(ua, wa[e], Y[mb + lb][e]);
+                }
+            }
+            for (int e = 0; e < JJ; ++e) G1 = fma(f1[e] * wa[e], z[e], G1);
+            for (int d = 0; d < 3; ++d) {
+                double dw[kJmax * kJmax];
+                w_row_rt(dRc[d], dRs[d], L, M, J, dw);
+                for (int e = 0; e < JJ; ++e) G2[d] = fma(f0[e] * dw[e], z[e], G2[d]);
+            }
+        }
+        for (int mb = -lb; mb <= lb; ++mb)
+            for (int d = 0; d < 3; ++d) {
+                double dw[kJmax * kJmax];
+                w_row_rt(dRc[d], dRs[d], lb, mb, J, dw);
+                for (int e = 0; e < JJ; ++e) G2[d] = fma(f0[e] * dw[e], Y[mb + lb][e], G2[d]);
+            }
+    }
+    for (int d = 0; d < 3; ++d) {
+        const double gd = fma(2.0 * v[d], G1, G2[d]);
+        g.grad_a[3 * (int64_t)p + d] = gd;
+        if (g.grad_b) g.grad_b[3 * (int64_t)p + d] = -gd;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_3c_grad_fp64_persistent(const Args3c g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        const Tile tl = g.tiles[t];
+        if (lane < tl.count) triple_aab_grad_fp64(g, g.perm[tl.start + lane]);
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(128) k_3c_fp64_persistent(const Args3c g)
 {
     const int lane = threadIdx.x & 31;
@@ -195,7 +410,10 @@ __global__ void __launch_bounds__(128) k_3c_fp64_persistent(const Args3c g)
 cudaError_t launch_3c(const Args3c &a, int precision, int grid, cudaStream_t s)
 {
     (void)precision;
-    k_3c_fp64_persistent<<<grid, 128, 0, s>>>(a);
+    if (a.grad_a)
+        k_3c_grad_fp64_persistent<<<grid, 128, 0, s>>>(a);
+    else
+        k_3c_fp64_persistent<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -205,7 +423,7 @@ int persistent_grid_3c(int precision)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_fp64_persistent, 128, 0) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_grad_fp64_persistent, 128, 0) != cudaSuccess || per < 1)
         per = 1;
     return (sms > 0 ? sms : 1) * per;
 }

@@ -63,6 +63,11 @@ void fill_consts(Consts &k)
     for (int i = 0; i < 32; ++i) k.pow2[i] = std::ldexp(1.0, i);
     for (int i = 0; i < 64; ++i) k.dint[i] = (double)i;
     for (int i = 1; i < 192; ++i) k.inv_int[i] = (double)(1.0L / (long double)i);
+    long double df = 1;
+    for (int n = 0; n < 32; ++n) {
+        k.dfact[n] = (double)df;                 // (2n-1)!!
+        df *= (2 * n + 1);
+    }
 }
 
 // Boys table, computed in long double: F_N(T) from its power series
@@ -71,12 +76,12 @@ void fill_consts(Consts &k)
 //   F_{n-1}(T) = (2T F_n(T) + exp(-T)) / (2n-1).
 void make_boys_table(double *tab, double *etab)
 {
-    const int ntop = 40;
+    const int ntop = 48;
     for (int i = 0; i < kBoysGrid; ++i) {
         const long double T = (long double)i / 16.0L;
         const long double e = std::exp(-T);
         long double term = 1.0L / (2 * ntop + 1), sum = term;
-        for (int k = 1; k < 4000; ++k) {
+        for (int k = 1; k < 20000; ++k) {
             term *= 2 * T / (long double)(2 * ntop + 2 * k + 1);
             sum += term;
             if (term < sum * 1e-24L) break;
@@ -99,6 +104,13 @@ static float2 split2(long double v)
 {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (long double)hi));
+}
+
+// same for a double: v - hi is exact in double (hi holds v's leading 24 bits)
+static inline float2 split2d(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
 }
 
 void fill_consts_mix(ConstsMix &k)
@@ -124,6 +136,11 @@ void fill_consts_mix(ConstsMix &k)
     k.pi3 = split2(pi * pi * pi);
     k.two_pi52 = split2(2 * std::pow(pi, 2.5L));
     k.sqrt_pi_half = split2(std::sqrt(pi) / 2);
+    long double dfc = 1;
+    for (int n = 0; n < kBoysN; ++n) {
+        k.dfact[n] = split2(dfc);
+        dfc *= (2 * n + 1);
+    }
 }
 
 void fill_consts3(Consts3 &k)
@@ -299,13 +316,18 @@ static void make_ranks(int schedule, std::vector<int> &rank, std::vector<int> &i
             return (x % kKbins2c) > (y % kKbins2c);
         });
     } else {
-        // estimated cost descending (longest tiles first)
-        std::vector<double> cost(kNBins);
-        for (int b = 0; b < kNBins; ++b) {
-            const int cls = b / kKbins2c, kk = b % kKbins2c + 1;
-            cost[b] = class_cost(cls / (kLmax2c + 1), cls % (kLmax2c + 1), kk);
-        }
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        // class-major, classes by decreasing estimated cost of their heaviest
+        // pairs, Ka*Kb descending inside a class: longest tiles first, and the
+        // warps resident on one SM mostly run one class's code at a time
+        // (instruction-cache locality)
+        std::vector<double> ccost(kNClass);
+        for (int cls = 0; cls < kNClass; ++cls)
+            ccost[cls] = class_cost(cls / (kLmax2c + 1), cls % (kLmax2c + 1), 64);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const int cx = x / kKbins2c, cy = y / kKbins2c;
+            if (cx != cy) return ccost[cx] > ccost[cy] || (ccost[cx] == ccost[cy] && cx < cy);
+            return (x % kKbins2c) > (y % kKbins2c);
+        });
     }
     for (int r = 0; r < kNBins; ++r) {
         rank[order[r]] = r;
@@ -553,7 +575,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
     std::vector<MixCenter> mctr(n_centers);
     for (int c = 0; c < n_centers; ++c) {
         ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
-        mctr[c] = MixCenter{split2(centers[3 * c]), split2(centers[3 * c + 1]), split2(centers[3 * c + 2]),
+        mctr[c] = MixCenter{split2d(centers[3 * c]), split2d(centers[3 * c + 1]), split2d(centers[3 * c + 2]),
                             make_float2(0, 0)};
     }
     std::vector<MixPrim> mpr(n_prims);
@@ -615,7 +637,7 @@ int shg_basis_set_centers(shg_basis_t *b, const double *centers)
     std::vector<MixCenter> mctr(b->d.n_centers);
     for (int c = 0; c < b->d.n_centers; ++c) {
         ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
-        mctr[c] = MixCenter{split2(centers[3 * c]), split2(centers[3 * c + 1]), split2(centers[3 * c + 2]),
+        mctr[c] = MixCenter{split2d(centers[3 * c]), split2d(centers[3 * c + 1]), split2d(centers[3 * c + 2]),
                             make_float2(0, 0)};
     }
     SHG_CUDA(cudaMemcpy(b->d.centers, ctr.data(), sizeof(Vec4) * b->d.n_centers, cudaMemcpyHostToDevice));
@@ -928,16 +950,15 @@ int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const in
     return r;
 }
 
-int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta, const int32_t *tt,
-                    const int32_t *tb, int precision, double screen, const int64_t *off, double *out, void *stream)
+static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta,
+                          const int32_t *tt, const int32_t *tb, int precision, const int64_t *off, double *out,
+                          const double *w, double *grad_a, double *grad_b, void *stream)
 {
-    g_err.clear();
     if (!orb || !aux) return fail(SHG_EINVAL, "basis is NULL");
     if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available for (aab)", precision);
-    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
     if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_triples %lld out of range", (long long)n);
     if (n == 0) return SHG_OK;
-    if (!ta || !tt || !tb || !off || !out) return fail(SHG_EINVAL, "NULL device pointer");
+    if (!ta || !tt || !tb || !off || (!out && !grad_a)) return fail(SHG_EINVAL, "NULL device pointer");
     int r = current_device_matches(orb->d.device);
     if (r) return r;
     if (aux->d.device != orb->d.device) return fail(SHG_EINVAL, "orb and aux bases live on different devices");
@@ -1005,6 +1026,10 @@ int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, c
     a.gaunt_base = t->gaunt_base;
     a.gaunt_row = t->gaunt_row;
     a.gaunt = t->gaunt;
+    a.w_off = grad_a ? reinterpret_cast<const long long *>(off) : nullptr;
+    a.w = w;
+    a.grad_a = grad_a;
+    a.grad_b = grad_b;
     a.k = consts();
     a.k3 = consts3();
     e = cudaMemsetAsync(d.counter, 0, sizeof(int), s);
@@ -1012,6 +1037,15 @@ int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, c
     cudaFreeAsync(blk, s);
     if (e != cudaSuccess) return fail(SHG_ECUDA, "(aab) launch: %s", cudaGetErrorString(e));
     return SHG_OK;
+}
+
+int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta, const int32_t *tt,
+                    const int32_t *tb, int precision, double screen, const int64_t *off, double *out, void *stream)
+{
+    g_err.clear();
+    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
+    if (n > 0 && !out) return fail(SHG_EINVAL, "NULL output");
+    return eval_3c_common(orb, aux, n, ta, tt, tb, precision, off, out, nullptr, nullptr, nullptr, stream);
 }
 
 int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,
@@ -1055,10 +1089,13 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
     return SHG_OK;
 }
 
-int shg_eval_3c_aab_grad(const shg_basis_t *, const shg_basis_t *, int64_t, const int32_t *, const int32_t *,
-                         const int32_t *, int, const int64_t *, const double *, double *, double *, void *)
+int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta,
+                         const int32_t *tt, const int32_t *tb, int precision, const int64_t *w_off, const double *w,
+                         double *grad_a, double *grad_b, void *stream)
 {
-    return fail(SHG_EINVAL, "shg_eval_3c_aab_grad: not available in this build");
+    g_err.clear();
+    if (n > 0 && (!w || !w_off || !grad_a)) return fail(SHG_EINVAL, "NULL device pointer");
+    return eval_3c_common(orb, aux, n, ta, tt, tb, precision, w_off, nullptr, w, grad_a, grad_b, stream);
 }
 
 int shg_debug_boys(int64_t n, const double *T, int nmax, double *F, void *stream)

@@ -16,23 +16,28 @@ enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
 
 // ------------------------------------------------------------------------- //
 // Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
-// T < 36: Taylor expansion of F_kmax about the nearest grid point          //
+// T < 120: Taylor expansion of F_kmax about the nearest grid point         //
 //   F_n(T_i + d) = sum_t F_{n+t}(T_i) (-d)^t / t!  (dF_n/dT = -F_{n+1}, SI  //
-//   Eq. 4), exp(-T) = exp(-T_i) exp(-d), then the downward recursion       //
+//   Eq. 4) and exp(-T) = exp(-T_i) exp(-d);                                //
+// T >= 120: the asymptotic F_kmax (terms with exp(-T) < 1e-52 dropped);    //
+// then, for both, the stable downward recursion                            //
 //   F_{k-1} = (2T F_k + exp(-T)) / (2k-1).                                 //
-// T >= 36: F_0 = sqrt(pi/(4T)) (erf(sqrt T) = 1 to 2e-17) and the upward    //
-//   recursion F_{k+1} = ((2k+1) F_k - exp(-T)) / (2T), stable for T > k.   //
+// The two branches differ only in how F_kmax and exp(-T) are obtained, so  //
+// a warp whose lanes straddle T = 120 runs both short heads and one tail.  //
 // ------------------------------------------------------------------------- //
+__device__ __forceinline__ double powi(double x, int n);
+
 template <int J>
 __device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
                                          const double *__restrict__ etab, const Consts &k, double (&F)[J])
 {
+    double f, e;
     if (T < kBoysTmax) {
         const int i = __double2int_rn(T * 16.0);
         const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
         const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
         const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
-        double f = fma(c67.y, y, c67.x);
+        f = fma(c67.y, y, c67.x);
         f = fma(f, y, c45.y);
         f = fma(f, y, c45.x);
         f = fma(f, y, c23.y);
@@ -40,7 +45,7 @@ __device__ __forceinline__ void boys_top(double T, int kmax, const double *__res
         f = fma(f, y, c01.y);
         f = fma(f, y, c01.x);
         // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
-        double e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
+        e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
         e = fma(e, y, 1.0 / 120.0);
         e = fma(e, y, 1.0 / 24.0);
         e = fma(e, y, 1.0 / 6.0);
@@ -48,27 +53,19 @@ __device__ __forceinline__ void boys_top(double T, int kmax, const double *__res
         e = fma(e, y, 1.0);
         e = fma(e, y, 1.0);
         e *= __ldg(etab + i);
-        F[0] = f;
-        const double twoT = T + T;
-#pragma unroll
-        for (int j = 1; j < J; ++j) {
-            const int kk = kmax - j + 1;                       // F_{kk-1} from F_kk
-            F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
-        }
     } else {
+        // F_kmax = (2kmax-1)!! (2T)^-kmax sqrt(pi/(4T)); exp(-T) < 1e-52 is dropped
         const double rT = rsqrt(T);
-        const double e = exp(-T);
-        const double h = 0.5 * rT * rT;                        // 1/(2T)
-        double f = kSqrtPiHalf * rT;                           // F_0
-        const int kmin = kmax - J + 1;
-        for (int kk = 0; kk < kmin; ++kk) f = fma(k.dint[2 * kk + 1], f, -e) * h;
-        F[J - 1] = f;
+        f = k.dfact[kmax] * powi(0.5 * rT * rT, kmax) * (kSqrtPiHalf * rT);
+        e = 0.0;
+    }
+    // downward recursion F_{k-1} = (2T F_k + exp(-T)) / (2k-1), shared by both branches
+    F[0] = f;
+    const double twoT = T + T;
 #pragma unroll
-        for (int t = 1; t < J; ++t) {
-            const int kk = kmin + t - 1;
-            f = fma(k.dint[2 * kk + 1], f, -e) * h;
-            F[J - 1 - t] = f;
-        }
+    for (int j = 1; j < J; ++j) {
+        const int kk = kmax - j + 1;
+        F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
     }
 }
 

@@ -18,8 +18,10 @@ constexpr int kTile = 32;         // pairs per warp tile
 
 // Boys table: F_{n+t}(T_i)/t!, T_i = i/16, i = 0..kBoysGrid-1, n < kBoysN,
 // t = 0..7; Taylor expansion about the nearest grid point (|delta| <= 1/32).
-constexpr int kBoysGrid = 577;    // covers T < 36
-constexpr double kBoysTmax = 36.0;
+// Above kBoysTmax, F_n(T) = (2n-1)!! / (2T)^n sqrt(pi/(4T)) to better than
+// 1e-30 relative for n <= 16 (the neglected terms carry exp(-T)).
+constexpr int kBoysGrid = 1921;   // covers T < 120
+constexpr double kBoysTmax = 120.0;
 constexpr int kBoysN = 16;        // orders n = 0..15 from the table
 constexpr int kBoysTerms = 8;
 
@@ -62,6 +64,7 @@ struct Consts {
     double pow2[32];                       // 2^k
     double dint[64];                       // (double) n
     double inv_int[192];                   // 1/n (0 for n = 0)
+    double dfact[32];                      // (2n-1)!!, (-1)!! = 1
 };
 
 void fill_consts(Consts &k);
@@ -74,6 +77,7 @@ struct ConstsMix {
     float2 inv_fact[14];                   // 1/t!
     float inv_fact_f[14];
     float2 pi32, pi3, two_pi52, sqrt_pi_half;
+    float2 dfact[kBoysN];                  // (2n-1)!!
 };
 
 void fill_consts_mix(ConstsMix &k);
@@ -215,6 +219,10 @@ struct Args3c {
     double *out;
     const int *gaunt_base, *gaunt_row;
     const GauntEnt *gaunt;
+    // gradient kernels only (grad_a != null selects the VJP kernel)
+    const long long *w_off;
+    const double *w;
+    double *grad_a, *grad_b;
     Consts k;
     Consts3 k3;
 };

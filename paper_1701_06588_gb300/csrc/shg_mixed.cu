@@ -41,7 +41,7 @@ __device__ __forceinline__ df powi_df(df x, int n)
 // exp(-r) (degree 13; terms 7..13 in FP32), times 2^-n.  Below FP32 range for
 // x > 87 the result is flushed to zero (terms that small are far below the
 // absolute parity floor for the weights of the synthetic sets).
-__device__ __forceinline__ df exp_neg_df(df x, const ConstsMix &k)
+__device__ __noinline__ df exp_neg_df(df x, const ConstsMix &k)
 {
     if (x.hi > 87.0f) return df_f(0.0f);
     const float n = rintf(x.hi * 1.44269504088896341f);
@@ -61,11 +61,13 @@ __device__ __forceinline__ df exp_neg_df(df x, const ConstsMix &k)
 }
 
 // Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}; same scheme as the FP64
-// path (Taylor about i/16 from the table, downward recursion; upward above 36).
+// path: Taylor head from the table below T = 120, asymptotic head above, then
+// one shared downward recursion.
 template <int J>
 __device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__restrict__ tab,
                                              const float2 *__restrict__ etab, const ConstsMix &k, df (&F)[J])
 {
+    df f, e;
     if (T.hi < (float)kBoysTmax) {
         const int i = __float2int_rn(T.hi * 16.0f);
         const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
@@ -75,37 +77,29 @@ __device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__res
         float t = fmaf(q2.w, y.hi, q2.z);
         t = fmaf(t, y.hi, q2.y);
         t = fmaf(t, y.hi, q2.x);
-        df f = add(mul_f(y, t), df{q1.z, q1.w});
+        f = add(mul_f(y, t), df{q1.z, q1.w});
         f = add(mul(y, f), df{q1.x, q1.y});
         f = add(mul(y, f), df{q0.z, q0.w});
         f = add(mul(y, f), df{q0.x, q0.y});
-        float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi, k.inv_fact_f[4]);
-        df e = add(mul_f(y, te), ldf(k.inv_fact[3]));
+        const float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi,
+                              k.inv_fact_f[4]);
+        e = add(mul_f(y, te), ldf(k.inv_fact[3]));
         e = add(mul(y, e), ldf(k.inv_fact[2]));
         e = add(mul(y, e), df_f(1.0f));
         e = add(mul(y, e), df_f(1.0f));
         e = mul(e, ldf(__ldg(etab + i)));
-        F[0] = f;
-        const df twoT = scale2(T, 2.0f);
-#pragma unroll
-        for (int j = 1; j < J; ++j) {
-            const int kk = kmax - j + 1;
-            F[j] = mul(add(mul(twoT, F[j - 1]), e), ldf(k.inv_int[2 * kk - 1]));
-        }
     } else {
+        // (2kmax-1)!! (2T)^-kmax sqrt(pi/(4T)); exp(-T) is below FP32 range here
         const df rT = rsqrt_df(T);
-        const float e = expf(-T.hi) * (1.0f - T.lo);   // enters only as a small correction
-        const df h = scale2(mul(rT, rT), 0.5f);          // 1/(2T)
-        df f = mul(rT, ldf(k.sqrt_pi_half));             // F_0 = sqrt(pi/(4T))
-        const int kmin = kmax - J + 1;
-        for (int kk = 0; kk < kmin; ++kk) f = mul(add_f(mul_f(f, (float)(2 * kk + 1)), -e), h);
-        F[J - 1] = f;
+        f = mul(mul(ldf(k.dfact[kmax]), powi_df(scale2(mul(rT, rT), 0.5f), kmax)), mul(rT, ldf(k.sqrt_pi_half)));
+        e = df_f(0.0f);
+    }
+    F[0] = f;
+    const df twoT = scale2(T, 2.0f);
 #pragma unroll
-        for (int t = 1; t < J; ++t) {
-            const int kk = kmin + t - 1;
-            f = mul(add_f(mul_f(f, (float)(2 * kk + 1)), -e), h);
-            F[J - 1 - t] = f;
-        }
+    for (int j = 1; j < J; ++j) {
+        const int kk = kmax - j + 1;
+        F[j] = mul(add(mul(twoT, F[j - 1]), e), ldf(k.inv_int[2 * kk - 1]));
     }
 }
 
@@ -138,7 +132,7 @@ __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim 
         const df id = mul(rd, rd);
         const df wd = mul(ldf(g.omega), id);                               // omega / (rho + omega)
         df X = mul(mul(ldf(g.km.pi3), mul(mul(ic, rc), mul(id, rd))), exp_neg_df(mul(T, wd), g.km));
-        X = mul(X, powi_df(wd, kmax - J + 1));
+        X = mul(X, powi_df(wd, kmax - J + 1));                            // X_k at k = kmax - J + 1
 #pragma unroll
         for (int j = J - 1; j >= 0; --j) {
             S[j] = add(S[j], mul(hp[j], X));
@@ -183,7 +177,7 @@ __device__ __forceinline__ df rsm(const df *Rs, int L, int m)
     return (m < 0 && !(am & 1)) ? neg(v) : v;
 }
 
-__device__ __forceinline__ void scaled_harmonics_mix(df x, df y, df z, int lmax, const ConstsMix &k, df *Rc, df *Rs)
+__device__ __noinline__ void scaled_harmonics_mix(df x, df y, df z, int lmax, const ConstsMix &k, df *Rc, df *Rs)
 {
     const df r2 = add(add(mul(x, x), mul(y, y)), mul(z, z));
     Rc[0] = df_f(1.0f);
@@ -211,30 +205,60 @@ __device__ __forceinline__ void scaled_harmonics_mix(df x, df y, df z, int lmax,
     }
 }
 
-template <int J>
-__device__ __forceinline__ void w_row_mix(const df *Rc, const df *Rs, int l, int m, df (&w)[J * J])
+// Runtime-J row of W (compact code: one copy serves every class).
+__device__ __noinline__ void w_row_mix_rt(const df *Rc, const df *Rs, int l, int m, int J, df *w)
 {
     const int mu = m < 0 ? -m : m;
     const bool sine = m < 0;
-#pragma unroll
     for (int j = 0; j < J; ++j) {
         const int L = l - j;
-#pragma unroll
-        for (int kp = 0; kp <= j; ++kp) {
-            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
-            if (kp == 0) {
-                w[e0] = sine ? rsm(Rs, L, mu) : rcm(Rc, L, mu);
+        w[j * j] = sine ? rsm(Rs, L, mu) : rcm(Rc, L, mu);
+        for (int kp = 1; kp <= j; ++kp) {
+            const int e0 = j * j + 2 * kp - 1;
+            const df cm = rcm(Rc, L, mu - kp), cp = rcm(Rc, L, mu + kp);
+            const df sm = rsm(Rs, L, mu - kp), sp = rsm(Rs, L, mu + kp);
+            const bool odd = kp & 1;
+            if (!sine) {
+                w[e0] = odd ? sub(cm, cp) : add(cm, cp);
+                w[e0 + 1] = odd ? neg(add(sm, sp)) : sub(sp, sm);
             } else {
-                const df cm = rcm(Rc, L, mu - kp), cp = rcm(Rc, L, mu + kp);
-                const df sm = rsm(Rs, L, mu - kp), sp = rsm(Rs, L, mu + kp);
-                if (!sine) {
-                    w[e0] = (kp & 1) ? sub(cm, cp) : add(cm, cp);
-                    w[e0 + 1] = (kp & 1) ? neg(add(sm, sp)) : sub(sp, sm);
-                } else {
-                    w[e0] = (kp & 1) ? sub(sm, sp) : add(sm, sp);
-                    w[e0 + 1] = (kp & 1) ? add(cm, cp) : sub(cm, cp);
-                }
+                w[e0] = odd ? sub(sm, sp) : add(sm, sp);
+                w[e0 + 1] = odd ? add(cm, cp) : sub(cm, cp);
             }
+        }
+    }
+}
+
+// Angular part and store of one pair from its contracted S_j (runtime J).
+__device__ __noinline__ void assemble_mix(const ArgsMix &g, int p, int la, int lb, df vx, df vy, df vz, const df *S,
+                                          int J)
+{
+    const int JJ = J * J;
+    df ge[kJmax * kJmax];
+    for (int j = 0; j < J; ++j)
+        for (int kp = 0; kp <= j; ++kp) {
+            const df v = mul(S[j], ldf(g.km.jB[j][kp]));
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            ge[e0] = v;
+            if (kp) ge[e0 + 1] = v;
+        }
+    df Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics_mix(vx, vy, vz, la > lb ? la : lb, g.km, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    df Ub[2 * kLmax2c + 1][kJmax * kJmax];
+    for (int mb = -lb; mb <= lb; ++mb) w_row_mix_rt(Rc, Rs, lb, mb, J, Ub[mb + lb]);
+    double *out = g.out + g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        df ua[kJmax * kJmax];
+        w_row_mix_rt(Rc, Rs, la, ma, J, ua);
+        for (int e = 0; e < JJ; ++e) ua[e] = mul(ua[e], ge[e]);
+        df Aa = ldf(g.km.A[la][ma < 0 ? -ma : ma]);
+        if (lb & 1) Aa = neg(Aa);
+        for (int mb = -lb; mb <= lb; ++mb) {
+            const df *ub = Ub[mb + lb];
+            df s = mul(ua[0], ub[0]);
+            for (int e = 1; e < JJ; ++e) s = add(s, mul(ua[e], ub[e]));
+            out[(ma + la) * nb + (mb + lb)] = to_double(mul(Aa, mul(ldf(g.km.A[lb][mb < 0 ? -mb : mb]), s)));
         }
     }
 }
@@ -258,41 +282,10 @@ __device__ void pair_2c_mix(const ArgsMix &g, int p)
         const int ia = q / Kb, ib = q - ia * Kb;
         radial_acc_mix<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, la, lb, g, S);
     }
-    df ge[J * J];
+    df Sr[kJmax];
 #pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-        for (int kp = 0; kp <= j; ++kp) {
-            const df v = mul(S[j], ldf(g.km.jB[j][kp]));
-            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
-            ge[e0] = v;
-            if (kp) ge[e0 + 1] = v;
-        }
-    df Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
-    scaled_harmonics_mix(vx, vy, vz, la > lb ? la : lb, g.km, Rc, Rs);
-    const int nb = 2 * lb + 1;
-    df Ub[2 * kLmax2c + 1][J * J];
-    for (int mb = -lb; mb <= lb; ++mb) {
-        df w[J * J];
-        w_row_mix<J>(Rc, Rs, lb, mb, w);
-#pragma unroll
-        for (int e = 0; e < J * J; ++e) Ub[mb + lb][e] = w[e];
-    }
-    double *out = g.out + g.out_off[p];
-    for (int ma = -la; ma <= la; ++ma) {
-        df ua[J * J];
-        w_row_mix<J>(Rc, Rs, la, ma, ua);
-#pragma unroll
-        for (int e = 0; e < J * J; ++e) ua[e] = mul(ua[e], ge[e]);
-        df Aa = ldf(g.km.A[la][ma < 0 ? -ma : ma]);
-        if (lb & 1) Aa = neg(Aa);
-        for (int mb = -lb; mb <= lb; ++mb) {
-            df s = mul(ua[0], Ub[mb + lb][0]);
-#pragma unroll
-            for (int e = 1; e < J * J; ++e) s = add(s, mul(ua[e], Ub[mb + lb][e]));
-            out[(ma + la) * nb + (mb + lb)] = to_double(mul(Aa, mul(ldf(g.km.A[lb][mb < 0 ? -mb : mb]), s)));
-        }
-    }
+    for (int j = 0; j < J; ++j) Sr[j] = S[j];
+    assemble_mix(g, p, la, lb, vx, vy, vz, Sr, J);
 }
 
 template <int OP>

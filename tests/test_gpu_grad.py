@@ -115,3 +115,66 @@ def test_autograd_function_matches_finite_differences(shg):
             fd = (lp - lm) / (2 * h)
             assert abs(g[c_idx, d] - fd) <= 1e-7 * max(1.0, abs(fd)), (c_idx, d, g[c_idx, d], fd)
     b.close()
+
+
+def _oracle_vjp_3c(shells, ta, tt, tb, w):
+    from tests.parity import normalised
+    shn, sha = normalised(shells)
+    J, off, sz = oracle.eval_3c_aab_grad(shn, ta, tt, tb, center="A", normalize=False)
+    Ja, _, _ = oracle.eval_3c_aab_grad(sha, ta, tt, tb, center="A", normalize=False)
+    g = np.zeros((len(ta), 3))
+    s = np.zeros((len(ta), 3))
+    for p in range(len(ta)):
+        blk = J[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
+        ablk = np.abs(Ja[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p]))
+        wp = w[off[p]: off[p] + sz[p]]
+        g[p] = blk @ wp
+        s[p] = ablk.max(axis=1) * np.abs(wp).sum()
+    return g, s
+
+
+@pytest.mark.parametrize("layout", ["orbital_pairs_on_A", "aux_on_A"])
+def test_aab_grad_against_oracle_and_translation(shg, layout):
+    import torch
+    sh, ta, tt, tb, per = W.aab_workload(6, seed=4, layout=layout)
+    b = shg.Basis(sh)
+    off, total = b.triple_offsets(b, ta, tt, tb)
+    w = np.random.default_rng(14).uniform(-1, 1, total)
+    ga, gb = shg.eval_3c_aab_grad(b, b, ta, tt, tb, torch.from_numpy(w).cuda(), offsets=off)
+    torch.cuda.synchronize()
+    ga, gb = ga.cpu().numpy(), gb.cpu().numpy()
+    np.testing.assert_array_equal(gb, -ga)
+    ref, scale = _oracle_vjp_3c(sh, ta, tt, tb, w)
+    ex = np.abs(ga - ref) / (1e-10 * np.abs(ref) + 1e-12 + 1e-15 * scale)
+    assert ex.max() <= 1.0, (layout, ex.max())
+    b.close()
+
+
+def test_aab_grad_against_finite_differences_of_gpu_forward(shg):
+    import torch
+    sh, ta, tt, tb, per = W.aab_workload(3, seed=6)
+    b = shg.Basis(sh)
+    off, total = b.triple_offsets(b, ta, tt, tb)
+    w = np.random.default_rng(15).uniform(-1, 1, total)
+    ga, _ = shg.eval_3c_aab_grad(b, b, ta, tt, tb, torch.from_numpy(w).cuda(), offsets=off)
+    ga = ga.cpu().numpy()
+    h = 1e-5
+    cb = sh["center_of"][tb]
+    fd = np.zeros_like(ga)
+    for d in range(3):
+        c = sh["centers"].copy()
+        c[cb, d] += h
+        b.set_centers(c)
+        vp, _ = shg.eval_3c_aab(b, b, ta, tt, tb)
+        c[cb, d] -= 2 * h
+        b.set_centers(c)
+        vm, _ = shg.eval_3c_aab(b, b, ta, tt, tb)
+        diff = ((vp - vm) / (2 * h)).cpu().numpy() * w
+        fd[:, d] = -np.add.reduceat(diff, off)      # d/dR_a = -d/dR_b
+    # only triples whose B center is nobody's A center see a pure shift of B
+    a_centers = set(sh["center_of"][ta].tolist())
+    ok = np.array([c not in a_centers for c in cb])
+    assert ok.sum() > 50
+    err = np.abs(ga - fd)[ok]
+    assert np.all(err <= 1e-7 * np.maximum(1.0, np.abs(fd[ok]))), err.max()
+    b.close()
