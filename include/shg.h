@@ -134,7 +134,11 @@ int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64
  *   screen_thresh  0 disables screening; > 0: a pair whose bound on every
  *                  element magnitude is below it writes zeros (overlap and
  *                  Gaussian operator only; Coulomb-type pairs are never
- *                  screened)
+ *                  screened).  The bound uses |S_{l,m}(r)| <= sqrt(2) r^l,
+ *                  r^l exp(-a r^2) <= (l/(a e))^{l/2} exp(-a r^2/2), the
+ *                  s-type integral at half the smallest exponents of each
+ *                  shell and sum |N c|; so every element of a screened
+ *                  block is below the threshold in magnitude.
  *   precision      enum shg_precision
  *   d_out_offsets  device int64[n_pairs] start of each block in d_out
  *   d_out          device doubles, large enough for every block

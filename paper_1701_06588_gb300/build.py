@@ -60,7 +60,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
                    *inc, *extra_nvcc, "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I" + os.path.join(cuda, "include"),
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-fopenmp", *inc, "-I" + os.path.join(cuda, "include"),
                    "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -77,7 +77,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
         msg = "\n".join("%s:\n%s" % (s, t) for s, t in failed)
         raise RuntimeError("CUDA library build failed:\n" + msg)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -44,6 +44,56 @@ static long double lfact(int n)
     return f;
 }
 
+// Double-double arithmetic for the host precomputation (shell normalisation
+// and per-primitive weights): as accurate as 80-bit long double and much
+// faster than the software binary128 long double of aarch64 hosts.
+struct dd {
+    double hi, lo;
+};
+static inline dd dd_two_sum(double a, double b)
+{
+    const double s = a + b, bb = s - a;
+    return dd{s, (a - (s - bb)) + (b - bb)};
+}
+static inline dd dd_norm(double h, double l) { const double s = h + l; return dd{s, l - (s - h)}; }
+static inline dd dd_add(dd a, dd b)
+{
+    dd s = dd_two_sum(a.hi, b.hi), t = dd_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_norm(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_norm(s.hi, s.lo);
+}
+static inline dd dd_mul(dd a, dd b)
+{
+    const double p = a.hi * b.hi;
+    double e = std::fma(a.hi, b.hi, -p);
+    e += a.hi * b.lo + a.lo * b.hi;
+    return dd_norm(p, e);
+}
+static inline dd dd_div(dd a, dd b)
+{
+    const double q1 = a.hi / b.hi;
+    const dd r = dd_add(a, dd_mul(b, dd{-q1, 0.0}));
+    const double q2 = r.hi / b.hi;
+    const dd r2 = dd_add(r, dd_mul(b, dd{-q2, 0.0}));
+    const double q3 = r2.hi / b.hi;
+    return dd_add(dd_norm(q1, q2), dd{q3, 0.0});
+}
+static inline dd dd_sqrt(dd a)
+{
+    if (!(a.hi > 0)) return dd{0.0, 0.0};
+    const double x = std::sqrt(a.hi);
+    const dd x2 = dd_mul(dd{x, 0.0}, dd{x, 0.0});
+    const dd d = dd_add(a, dd{-x2.hi, -x2.lo});
+    return dd_norm(x, d.hi / (2 * x));
+}
+static inline dd dd_from(long double v)
+{
+    const double h = (double)v;
+    return dd{h, (double)(v - (long double)h)};
+}
+
 void fill_consts(Consts &k)
 {
     std::memset(&k, 0, sizeof k);
@@ -542,34 +592,68 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
 
     std::vector<ShellRec> sh(n_shells);
     std::vector<PrimRec> pr(n_prims);
-    int64_t off = 0;
+    std::vector<int64_t> first(n_shells + 1, 0);
+    for (int s = 0; s < n_shells; ++s) first[s + 1] = first[s] + nprim[s];
+    // per-l constants: sqrt(pi) (2l+2)! / (2^{2l+3} (l+1)!) and K_l = sqrt((2l+1)/(4 pi))
+    dd pref_l[kLmax2c + 1], K_l[kLmax2c + 1];
+    for (int L = 0; L <= kLmax2c; ++L) {
+        const long double pi = 3.14159265358979323846264338327950288L;
+        pref_l[L] = dd_from(std::sqrt(pi) * lfact(2 * L + 2) / (std::ldexp(1.0L, 2 * L + 3) * lfact(L + 1)));
+        K_l[L] = dd_from(std::sqrt((2 * L + 1) / (4 * pi)));
+    }
+    int bad_shell = -1;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int s = 0; s < n_shells; ++s) {
         const int L = l[s], K = nprim[s];
-        long double N = 1.0L;
+        const int64_t off = first[s];
+        dd N = {1.0, 0.0};
         if (normalize) {
             // N_l = K_l [sum_ij sqrt(pi) (2l+2)! c_i c_j / (2^{2l+3} (l+1)! (a_i+a_j)^{l+3/2})]^{-1/2}
-            long double sum = 0;
-            const long double pref = std::sqrt(3.14159265358979323846264338327950288L) * lfact(2 * L + 2) /
-                                     (std::ldexp(1.0L, 2 * L + 3) * lfact(L + 1));
+            dd sum = {0.0, 0.0};
             for (int i = 0; i < K; ++i)
-                for (int j = 0; j < K; ++j)
-                    sum += pref * (long double)coefs[off + i] * coefs[off + j] /
-                           std::pow((long double)exps[off + i] + exps[off + j], (long double)L + 1.5L);
-            if (!(sum > 0)) return fail(SHG_EINVAL, "shell %d: contracted function has zero norm", s);
-            N = std::sqrt((2 * L + 1) / (4 * 3.14159265358979323846264338327950288L)) / std::sqrt(sum);
+                for (int j = i; j < K; ++j) {
+                    const dd sij = dd_two_sum(exps[off + i], exps[off + j]);
+                    const dd r = dd_div(dd{1.0, 0.0}, sij);
+                    dd pw = r;
+                    for (int t = 0; t < L; ++t) pw = dd_mul(pw, r);      // s^-(L+1)
+                    dd term = dd_mul(pw, dd_sqrt(r));                    // s^-(L+3/2)
+                    term = dd_mul(term, dd_mul(dd{coefs[off + i], 0.0}, dd{coefs[off + j], 0.0}));
+                    if (j != i) term = dd{2 * term.hi, 2 * term.lo};
+                    sum = dd_add(sum, term);
+                }
+            sum = dd_mul(sum, pref_l[L]);
+            if (!(sum.hi > 0)) {
+#pragma omp critical
+                bad_shell = s;
+                continue;
+            }
+            N = dd_div(K_l[L], dd_sqrt(sum));
         }
         for (int i = 0; i < K; ++i) {
-            const long double a = exps[off + i];
-            const long double c = N * (long double)coefs[off + i];
+            const double a = exps[off + i];
+            const dd c = dd_mul(N, dd{coefs[off + i], 0.0});
+            dd p2 = {1.0, 0.0};
+            for (int t = 0; t < L; ++t) p2 = dd_mul(p2, dd{2 * a, 0.0});  // (2a)^l
             PrimRec p;
-            p.alpha = (double)a;
-            p.inv_alpha = (double)(1.0L / a);
-            p.w2c = (double)(c / std::pow(2 * a, (long double)L));
-            p.wN = (double)c;
+            p.alpha = a;
+            p.inv_alpha = dd_div(dd{1.0, 0.0}, dd{a, 0.0}).hi;
+            p.w2c = dd_div(c, p2).hi;
+            p.wN = c.hi;
             pr[off + i] = p;
         }
         sh[s] = ShellRec{L, K, (int)off, center_of_shell[s]};
-        off += K;
+    }
+    if (bad_shell >= 0) return fail(SHG_EINVAL, "shell %d: contracted function has zero norm", bad_shell);
+    std::vector<ScreenRec> scr(n_shells);
+    for (int s = 0; s < n_shells; ++s) {
+        double amin = exps[first[s]], sabs = 0;
+        for (int64_t i = first[s]; i < first[s + 1]; ++i) {
+            amin = std::min(amin, exps[i]);
+            sabs += std::fabs(pr[i].wN);
+        }
+        const int L = l[s];
+        const double lfac = L == 0 ? 1.0 : std::pow(L / (amin * 2.718281828459045), 0.5 * L);
+        scr[s] = ScreenRec{amin, sabs, lfac, 0.0};
     }
     std::vector<Vec4> ctr(n_centers);
     std::vector<MixCenter> mctr(n_centers);
@@ -579,15 +663,13 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
                             make_float2(0, 0)};
     }
     std::vector<MixPrim> mpr(n_prims);
-    {
-        int64_t o = 0;
-        for (int s2 = 0; s2 < n_shells; ++s2)
-            for (int i = 0; i < nprim[s2]; ++i, ++o) {
-                const long double a = exps[o];
-                long double N = 1.0L;
-                (void)N;
-                mpr[o] = MixPrim{split2(a), split2(1.0L / a), split2((long double)pr[o].wN), make_float2(0, 0)};
-            }
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n_prims; ++o) {
+        const double a = exps[o];
+        const dd ia = dd_div(dd{1.0, 0.0}, dd{a, 0.0});
+        const float ih = (float)ia.hi;
+        mpr[o] = MixPrim{split2d(a), make_float2(ih, (float)((ia.hi - (double)ih) + ia.lo)), split2d(pr[o].wN),
+                         make_float2(0, 0)};
     }
 
     shg_basis_t *b = new (std::nothrow) shg_basis_t;
@@ -607,6 +689,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         cudaMalloc(&d.prims, sizeof(PrimRec) * n_prims) != cudaSuccess ||
         cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess ||
         cudaMalloc(&d.mprims, sizeof(MixPrim) * n_prims) != cudaSuccess ||
+        cudaMalloc(&d.screen, sizeof(ScreenRec) * n_shells) != cudaSuccess ||
         cudaMalloc(&d.mcenters, sizeof(MixCenter) * n_centers) != cudaSuccess) {
         shg_basis_destroy(b);
         return fail(SHG_ENOMEM, "basis: cudaMalloc failed");
@@ -615,6 +698,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         cudaMemcpy(d.prims, pr.data(), sizeof(PrimRec) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.centers, ctr.data(), sizeof(Vec4) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.mprims, mpr.data(), sizeof(MixPrim) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.screen, scr.data(), sizeof(ScreenRec) * n_shells, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.mcenters, mctr.data(), sizeof(MixCenter) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess) {
         shg_basis_destroy(b);
         return fail(SHG_ECUDA, "basis: upload failed");
@@ -653,6 +737,7 @@ void shg_basis_destroy(shg_basis_t *b)
     cudaFree(b->d.centers);
     cudaFree(b->d.mprims);
     cudaFree(b->d.mcenters);
+    cudaFree(b->d.screen);
     delete[] b->d.h_l;
     delete[] b->d.h_nprim;
     delete[] b->d.h_center;
@@ -861,7 +946,7 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
     if (!p) return fail(SHG_EINVAL, "plan is NULL");
     int r = check_op(op, omega, precision);
     if (r) return r;
-    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
+    if (!(screen >= 0.0) || !std::isfinite(screen)) return fail(SHG_EINVAL, "screening threshold must be >= 0");
     if (p->d.n_pairs == 0 || p->d.n_tiles == 0) return SHG_OK;
     if (!off || !out) return fail(SHG_EINVAL, "NULL output");
     r = current_device_matches(p->d.basis->device);
@@ -882,6 +967,9 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         m.out = out;
         m.omega = split2(omega);
         m.omega2 = split2((long double)omega * omega);
+        m.omega_d = omega;
+        m.screen_thresh = screen;
+        m.screen = p->d.basis->screen;
         m.boys = t->boys_mix;
         m.boys_e = t->boys_e_mix;
         m.km = consts_mix();
@@ -913,6 +1001,8 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
     a.out_off = reinterpret_cast<const long long *>(off);
     a.out = out;
     a.omega = omega;
+    a.screen_thresh = screen;
+    a.screen = p->d.basis->screen;
     a.boys = t->boys;
     a.boys_e = t->boys_e;
     a.k = consts();

@@ -226,6 +226,26 @@ __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec
     }
 }
 
+// Rigorous upper bound on every element magnitude of a contracted overlap
+// (op 0) or Gaussian-operator (op 4) block, from |S_{l,m}(r)| <= sqrt(2) r^l,
+// r^l exp(-a r^2) <= (l/(a e))^{l/2} exp(-a r^2/2) and the s-type integral at
+// halved exponents, maximised over the primitives by the smallest exponents.
+__device__ __forceinline__ double screen_bound(const ScreenRec &a, const ScreenRec &b, double R2, int op, double omega)
+{
+    const double ah = 0.5 * a.amin, bh = 0.5 * b.amin;
+    const double c = ah + bh, rho = ah * bh / c;
+    double s;
+    if (op == OP_OVERLAP) {
+        const double t = kPi32 / (c * sqrt(c));
+        s = t * exp(-rho * R2);
+    } else {
+        const double d = rho + omega;
+        const double base = 9.869604401089358 / (c * d);
+        s = base * sqrt(base) * exp(-omega * rho * R2 / d);
+    }
+    return 2.0 * a.lfac * b.lfac * a.sabs * b.sabs * s;
+}
+
 // Runtime-J variant of w_row (used where J varies inside one thread).
 __device__ __forceinline__ void w_row_rt(const double *Rc, const double *Rs, int l, int m, int J, double *w)
 {

@@ -25,6 +25,12 @@ constexpr double kBoysTmax = 120.0;
 constexpr int kBoysN = 16;        // orders n = 0..15 from the table
 constexpr int kBoysTerms = 8;
 
+// Per-shell screening data (host-computed): smallest exponent, sum |N c| over
+// the primitives, and (l / (alpha_min e))^{l/2} (1 for l = 0).
+struct alignas(32) ScreenRec {
+    double amin, sabs, lfac, pad;
+};
+
 // Per-shell record on the device (16 bytes): l, K, first primitive, center.
 struct ShellRec {
     int l, nprim, prim_off, center;
@@ -129,6 +135,7 @@ struct BasisDev {
     PrimRec *prims = nullptr;     // device
     Vec4 *centers = nullptr;      // device
     MixPrim *mprims = nullptr;    // device, double-float copies for the mixed path
+    ScreenRec *screen = nullptr;  // device, per-shell screening data
     MixCenter *mcenters = nullptr;
     // host copies used for validation and offsets
     int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
@@ -178,6 +185,8 @@ struct Args2c {
     const long long *out_off;
     double *out;
     double omega;
+    double screen_thresh;         // > 0: overlap / Gaussian-operator pairs bounded below it write zeros
+    const ScreenRec *screen;
     const double *boys, *boys_e;
     // gradient kernels only: upstream weights W (blocks at w + w_off[p]) and
     // the per-pair outputs dI/dR_a . W and dI/dR_b . W
@@ -200,6 +209,8 @@ struct ArgsMix {
     const long long *out_off;
     double *out;
     float2 omega, omega2;
+    double omega_d, screen_thresh;
+    const ScreenRec *screen;
     const float4 *boys;
     const float2 *boys_e;
     ConstsMix km;

@@ -37,6 +37,12 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
     const double vx = A.x - B.x, vy = A.y - B.y, vz = A.z - B.z;
     const double R2 = vx * vx + vy * vy + vz * vz;
     const int kmax = la + lb;
+    if ((OP == OP_OVERLAP || OP == OP_GAUSS) && g.screen_thresh > 0.0 &&
+        screen_bound(g.screen[g.pair_a[p]], g.screen[g.pair_b[p]], R2, OP, g.omega) < g.screen_thresh) {
+        double *o = g.out + g.out_off[p];
+        for (int i = 0; i < (2 * la + 1) * (2 * lb + 1); ++i) o[i] = 0.0;
+        return;
+    }
 
     double O[J];
 #pragma unroll

@@ -273,6 +273,12 @@ __device__ void pair_2c_mix(const ArgsMix &g, int p)
     const MixCenter B = g.centers[sb.center];
     const df vx = sub(ldf(A.x), ldf(B.x)), vy = sub(ldf(A.y), ldf(B.y)), vz = sub(ldf(A.z), ldf(B.z));
     const df R2 = add(add(mul(vx, vx), mul(vy, vy)), mul(vz, vz));
+    if ((OP == OP_OVERLAP || OP == OP_GAUSS) && g.screen_thresh > 0.0 &&
+        screen_bound(g.screen[g.pair_a[p]], g.screen[g.pair_b[p]], to_double(R2), OP, g.omega_d) < g.screen_thresh) {
+        double *o = g.out + g.out_off[p];
+        for (int i = 0; i < (2 * la + 1) * (2 * lb + 1); ++i) o[i] = 0.0;
+        return;
+    }
 
     df S[J];
 #pragma unroll

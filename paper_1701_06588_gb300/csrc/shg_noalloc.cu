@@ -131,6 +131,8 @@ extern "C" int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, co
     a.out_off = reinterpret_cast<const long long *>(d_out_offsets);
     a.out = d_out;
     a.omega = omega;
+    a.screen_thresh = 0.0;
+    a.screen = b.screen;
     a.boys = t->boys;
     a.boys_e = t->boys_e;
     a.k = consts();

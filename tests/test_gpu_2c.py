@@ -168,3 +168,80 @@ def test_device_boys_against_oracle(shg):
     rel = np.abs(F - ref) / ref
     # 15 downward recursion steps from F_15: about 20 ulp at F_0
     assert rel.max() < 1e-14, rel.max()
+
+
+def test_graph_replay_and_launch_shapes(shg):
+    """A captured CUDA graph of several operators reproduces the direct plan
+    execution, sees later shg_basis_set_centers updates, and every launch
+    shape the autotuner may pick gives the same blocks."""
+    import torch
+    from paper_1701_06588_gb300 import autotune
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=4000)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    d_off = torch.from_numpy(off).cuda()
+    names = ["overlap", "coulomb", "erfc"]
+    omegas = [0.0, 0.0, 0.11]
+    for prec in ("fp64", "mixed"):
+        plan = shg.Plan2c(b, pa, pb)
+        ref = []
+        for n, w in zip(names, omegas):
+            o = torch.empty(total, dtype=torch.float64, device="cuda")
+            plan.exec(n, d_off, o, omega=w, precision=prec)
+            ref.append(o)
+        outs = [torch.full((total,), float("nan"), dtype=torch.float64, device="cuda") for _ in names]
+        g = shg.Graph2c(plan, names, omegas, d_off, outs, precision=prec)
+        g.launch()
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+        # new geometry: graph replay follows the basis
+        c2 = sh["centers"] + 0.01
+        b.set_centers(c2)
+        g.launch()
+        torch.cuda.synchronize()
+        ref2, _ = shg.eval_2c(b, pa, pb, "coulomb", precision=prec)
+        assert torch.equal(outs[1], ref2)
+        b.set_centers(sh["centers"])
+        g.close()
+        for sched, threads, ctas in autotune.CANDIDATES:
+            p2 = autotune.tuned_plan(b, pa, pb, {"schedule": sched, "threads_per_cta": threads, "ctas_per_sm": ctas})
+            o = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+            p2.exec("erfc", d_off, o, omega=0.11, precision=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(o, ref[2]), (prec, sched, threads, ctas)
+            p2.close()
+        plan.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_screening_bound(shg, precision):
+    """With screen_thresh > 0, overlap and Gaussian-operator pairs whose bound
+    is below it write zeros: every element stays within thr of the exact
+    block, and on the 0..10 bohr workload a share of the pairs is screened.
+    Coulomb-type operators are never screened."""
+    import torch
+    sh, pa, pb = W.make("c2_200k_l4_k8", n=4000)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    d_off = torch.from_numpy(off).cuda()
+    plan = shg.Plan2c(b, pa, pb)
+    sizes = np.diff(np.r_[off, total])
+    for opname, omega in [("overlap", 0.0), ("gauss", 1.0), ("coulomb", 0.0)]:
+        exact = torch.empty(total, dtype=torch.float64, device="cuda")
+        plan.exec(opname, d_off, exact, omega=omega, precision=precision)
+        for thr in (1e-10, 1e-6):
+            scr = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+            plan.exec(opname, d_off, scr, omega=omega, precision=precision, screen_thresh=thr)
+            torch.cuda.synchronize()
+            e, s = exact.cpu().numpy(), scr.cpu().numpy()
+            assert np.all(np.isfinite(s))
+            assert np.max(np.abs(s - e)) <= thr, (opname, thr)
+            zero_blocks = np.array([not np.any(s[o:o + z]) and np.any(e[o:o + z]) for o, z in zip(off, sizes)])
+            if opname == "coulomb":
+                np.testing.assert_array_equal(s, e)
+            elif thr == 1e-6:
+                assert zero_blocks.mean() > 0.05, (opname, zero_blocks.mean())
+    plan.close()
+    b.close()
