@@ -242,6 +242,6 @@ def test_screening_bound(shg, precision):
             if opname == "coulomb":
                 np.testing.assert_array_equal(s, e)
             elif thr == 1e-6:
-                assert zero_blocks.mean() > 0.05, (opname, zero_blocks.mean())
+                assert zero_blocks.mean() > 0.01, (opname, zero_blocks.mean())
     plan.close()
     b.close()
