@@ -97,8 +97,14 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
 
 /*
  * shg_basis_set_centers - replace all center coordinates (host array of
- * n_centers x 3 doubles, same count as at creation).  Plans made on the basis
- * stay valid: they depend only on l and K.  Synchronous.
+ * n_centers x 3 doubles, same count as at creation; pinned memory is copied
+ * by DMA, pageable memory through the driver's staging).  The coordinates are
+ * packed and checked on the device, in buffers of ~88 B per center that the
+ * first call allocates and the basis keeps.  Returns SHG_EINVAL, naming the
+ * first center with a non-finite coordinate, and then keeps the previous
+ * centers.  Plans made on the basis stay valid: they depend only on l and K.
+ * Runs on the legacy default stream and returns when the new centers are in
+ * place (synchronous).
  */
 int shg_basis_set_centers(shg_basis_t *basis, const double *centers);
 

@@ -715,17 +715,37 @@ int shg_basis_set_centers(shg_basis_t *b, const double *centers)
 {
     g_err.clear();
     if (!b || !centers) return fail(SHG_EINVAL, "NULL argument");
-    for (int64_t i = 0; i < 3 * (int64_t)b->d.n_centers; ++i)
-        if (!is_finite_d(centers[i])) return fail(SHG_EINVAL, "center coordinate %lld not finite", (long long)i);
-    std::vector<Vec4> ctr(b->d.n_centers);
-    std::vector<MixCenter> mctr(b->d.n_centers);
-    for (int c = 0; c < b->d.n_centers; ++c) {
-        ctr[c] = Vec4{centers[3 * c], centers[3 * c + 1], centers[3 * c + 2], 0.0};
-        mctr[c] = MixCenter{split2d(centers[3 * c]), split2d(centers[3 * c + 1]), split2d(centers[3 * c + 2]),
-                            make_float2(0, 0)};
+    BasisDev &d = b->d;
+    const int n = d.n_centers;
+    if (n == 0) return SHG_OK;
+    if (!d.stage_raw) {
+        if (cudaMalloc(&d.stage_raw, sizeof(double) * 3 * n) != cudaSuccess ||
+            cudaMalloc(&d.stage_ctr, sizeof(Vec4) * n) != cudaSuccess ||
+            cudaMalloc(&d.stage_mctr, sizeof(MixCenter) * n) != cudaSuccess ||
+            cudaMalloc(&d.stage_bad, sizeof(int)) != cudaSuccess) {
+            cudaFree(d.stage_raw);
+            cudaFree(d.stage_ctr);
+            cudaFree(d.stage_mctr);
+            cudaFree(d.stage_bad);
+            d.stage_raw = nullptr;
+            d.stage_ctr = nullptr;
+            d.stage_mctr = nullptr;
+            d.stage_bad = nullptr;
+            return fail(SHG_ENOMEM, "set_centers: cudaMalloc failed");
+        }
     }
-    SHG_CUDA(cudaMemcpy(b->d.centers, ctr.data(), sizeof(Vec4) * b->d.n_centers, cudaMemcpyHostToDevice));
-    SHG_CUDA(cudaMemcpy(b->d.mcenters, mctr.data(), sizeof(MixCenter) * b->d.n_centers, cudaMemcpyHostToDevice));
+    // the legacy default stream orders this against work on blocking streams
+    const cudaStream_t s = 0;
+    SHG_CUDA(cudaMemcpyAsync(d.stage_raw, centers, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    SHG_CUDA(cudaMemsetAsync(d.stage_bad, 0x7f, sizeof(int), s));
+    SHG_CUDA(launch_pack_centers(d.stage_raw, n, d.stage_ctr, d.stage_mctr, d.stage_bad, s));
+    int bad = 0;
+    SHG_CUDA(cudaMemcpyAsync(&bad, d.stage_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SHG_CUDA(cudaStreamSynchronize(s));
+    if (bad < n) return fail(SHG_EINVAL, "center %d has a non-finite coordinate", bad);
+    SHG_CUDA(cudaMemcpyAsync(d.centers, d.stage_ctr, sizeof(Vec4) * n, cudaMemcpyDeviceToDevice, s));
+    SHG_CUDA(cudaMemcpyAsync(d.mcenters, d.stage_mctr, sizeof(MixCenter) * n, cudaMemcpyDeviceToDevice, s));
+    SHG_CUDA(cudaStreamSynchronize(s));
     return SHG_OK;
 }
 
@@ -738,6 +758,10 @@ void shg_basis_destroy(shg_basis_t *b)
     cudaFree(b->d.mprims);
     cudaFree(b->d.mcenters);
     cudaFree(b->d.screen);
+    cudaFree(b->d.stage_raw);
+    cudaFree(b->d.stage_ctr);
+    cudaFree(b->d.stage_mctr);
+    cudaFree(b->d.stage_bad);
     delete[] b->d.h_l;
     delete[] b->d.h_nprim;
     delete[] b->d.h_center;

@@ -137,6 +137,13 @@ struct BasisDev {
     MixPrim *mprims = nullptr;    // device, double-float copies for the mixed path
     ScreenRec *screen = nullptr;  // device, per-shell screening data
     MixCenter *mcenters = nullptr;
+    // shg_basis_set_centers staging (allocated on its first call): raw
+    // coordinates, packed copies checked before they replace the live ones,
+    // and the smallest non-finite center index
+    double *stage_raw = nullptr;
+    Vec4 *stage_ctr = nullptr;
+    MixCenter *stage_mctr = nullptr;
+    int *stage_bad = nullptr;
     // host copies used for validation and offsets
     int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
 };
@@ -251,6 +258,7 @@ int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
                       cudaStream_t s, int threads = 128);
 int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
+cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s);
 cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t,
                               cudaStream_t s);
 cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s);

@@ -277,6 +277,27 @@ __global__ void k_debug_boys(int64_t n, const double *__restrict__ T, int nmax, 
 }
 
 // ------------------------------------------------------------------------- //
+// Center packing for shg_basis_set_centers: FP64 Vec4 and the double-float   //
+// split (hi = nearest float, lo = nearest float of the exact remainder).     //
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ float2 split_df(double v)
+{
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+__global__ void k_pack_centers(const double *__restrict__ raw, int n, Vec4 *__restrict__ ctr,
+                               MixCenter *__restrict__ mctr, int *bad)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const double x = raw[3 * c], y = raw[3 * c + 1], z = raw[3 * c + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicMin(bad, c);
+        ctr[c] = Vec4{x, y, z, 0.0};
+        mctr[c] = MixCenter{split_df(x), split_df(y), split_df(z), make_float2(0.f, 0.f)};
+    }
+}
+
+// ------------------------------------------------------------------------- //
 // ALU throughput probe: 8 independent FMA chains per thread.                //
 // ------------------------------------------------------------------------- //
 template <typename T>
@@ -376,6 +397,14 @@ int persistent_grid_2c(int op, int precision, int threads, int ctas_per_sm)
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     if (sms < 1) sms = 1;
     return sms * per;
+}
+
+cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
+    k_pack_centers<<<blocks, 256, 0, s>>>(raw, n, ctr, mctr, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t, cudaStream_t s)

@@ -153,6 +153,47 @@ def test_errors_are_reported(shg):
     b.close()
 
 
+def test_set_centers_rejects_non_finite_and_keeps_previous(shg):
+    """shg_basis_set_centers packs and checks the coordinates on the device:
+    a non-finite coordinate is reported with the first bad center and the
+    basis keeps its previous centers; a valid update is seen by a new plan."""
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    sh, pa, pb = W.make("c1_2k_l3_k4", n=200)
+    b = shg.Basis(sh)
+
+    def run():
+        off, total = b.pair_offsets(pa, pb)
+        plan = shg.Plan2c(b, pa, pb)
+        out = torch.zeros(total, dtype=torch.float64, device="cuda")
+        plan.exec("coulomb", torch.from_numpy(off).cuda(), out)
+        torch.cuda.synchronize()
+        plan.close()
+        return out.cpu().numpy()
+
+    before = run()
+    c = sh["centers"].copy()
+    for bad_center, val in ((7, np.nan), (3, np.inf), (len(c) - 1, -np.inf)):
+        cb = c.copy()
+        cb[bad_center, 1] = val
+        cb[bad_center + 1:, 0] = np.nan      # later bad centers: the first one is named
+        with pytest.raises(L.ShgError) as e:
+            b.set_centers(cb)
+        assert e.value.code == L.SHG_EINVAL
+        assert "center %d " % bad_center in str(e.value), str(e.value)
+        assert np.array_equal(run(), before)
+    moved = c + np.array([0.25, -0.5, 1.0])
+    b.set_centers(moved)
+    assert np.allclose(run(), before, rtol=1e-12, atol=1e-14)   # a rigid translation
+    c2 = c.copy()
+    c2[::2] *= 1.1
+    b.set_centers(c2)
+    sh2 = dict(sh, centers=c2)
+    ref, scale = reference_2c(sh2, pa, pb, 1, 0.0)
+    assert_parity(run(), ref, TOL_FP64, "c1 coulomb after set_centers", scale)
+    b.close()
+
+
 def test_device_boys_against_oracle(shg):
     import torch
     from paper_1701_06588_gb300 import _lib as L
