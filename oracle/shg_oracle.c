@@ -48,7 +48,7 @@ typedef double real;
 #define R_PI 3.141592653589793238462643383279502884
 #endif
 
-enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5 };
 
 #define MAXLA 11  /* |a| on center A: la + la~ <= 10, plus one for gradients */
 #define MAXLB 7   /* |b| on center B: lb <= 6, plus one for gradients        */
@@ -153,6 +153,28 @@ static void ss_deriv(int op, real a, real b, real omega, real R2, int mmax, real
         real pre = base * R_SQRT(base) * R_EXP(-omega * T / d);
         real f = 1;
         for (int m = 0; m <= mmax; ++m) { G[m] = f * pre; f *= -omega * rho / d; }
+        break;
+    }
+    case OP_GCOUL: {
+        /* exp(-omega r^2)/r (Table S1): (pi/c)^{3/2} 2 pi/d exp(-omega T/d) times, for
+         * the n-th derivative, sum_j C(n,j) p^{n-j} q^j F_j(T rho/d) with d = rho + omega,
+         * p = -omega rho/d, q = -rho^2/d                                           */
+        real d = rho + omega;
+        real pre = R_SQRT(R_PI / c);
+        pre = pre * pre * pre * (2 * R_PI / d) * R_EXP(-omega * T / d);
+        real p = -omega * rho / d, q = -rho * rho / d;
+        real pp[MAXM + 2], qq[MAXM + 2];
+        boys(mmax, T * rho / d, F);
+        pp[0] = qq[0] = 1;
+        for (int m = 1; m <= mmax; ++m) { pp[m] = pp[m - 1] * p; qq[m] = qq[m - 1] * q; }
+        for (int m = 0; m <= mmax; ++m) {
+            real sum = 0, binom = 1;             /* C(m, j) */
+            for (int j = 0; j <= m; ++j) {
+                sum += binom * pp[m - j] * qq[j] * F[j];
+                binom = binom * (m - j) / (j + 1);
+            }
+            G[m] = pre * sum;
+        }
         break;
     }
     default:
@@ -621,7 +643,7 @@ int oracle_eval_2c(int n_shells, const int32_t *l, const int32_t *nprim, const i
 {
     shells_t S = {n_shells, l, nprim, prim_off, exps, coefs, centers, center_of};
     if (check_shells(&S, 6)) return -1;
-    if (op < 0 || op > 4) return -2;
+    if (op < 0 || op > 5) return -2;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
     {
         work_t w;

@@ -4,8 +4,9 @@ Every integral here is a product over x, y, z of one- or two-variable Gaussian
 integrals evaluated with Gauss-Hermite quadrature after diagonalising the
 quadratic exponent; the rule is exact for the polynomial factors used here.
 Coulomb-type kernels are reduced to the Gaussian kernel through
-    1/r        = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt,
-    erf(w r)/r = (2/sqrt(pi)) int_0^w   exp(-t^2 r^2) dt,
+    1/r              = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt,
+    erf(w r)/r       = (2/sqrt(pi)) int_0^w   exp(-t^2 r^2) dt,
+    exp(-w r^2)/r    = (2/sqrt(pi)) int_0^inf exp(-(w + t^2) r^2) dt,
 with the t-integral done by adaptive quadrature.  None of this uses the Boys
 function, Table S1 or any recursion, so it pins the oracle from outside.
 """
@@ -68,9 +69,10 @@ def cart_gauss_op(a, b, alpha, beta, omega, A, B):
     return np.prod([gauss_op_1d(a[d], b[d], alpha, beta, omega, A[d], B[d]) for d in range(3)])
 
 
-def cart_attenuated(a, b, alpha, beta, A, B, t_max):
-    """(2/sqrt(pi)) int_0^t_max  (a| exp(-t^2 r12^2) |b) dt; t_max = inf gives 1/r."""
-    f = lambda t: cart_gauss_op(a, b, alpha, beta, t * t, A, B)
+def cart_attenuated(a, b, alpha, beta, A, B, t_max, omega0=0.0):
+    """(2/sqrt(pi)) int_0^t_max  (a| exp(-(omega0 + t^2) r12^2) |b) dt; t_max = inf gives
+    exp(-omega0 r^2)/r (1/r for omega0 = 0)."""
+    f = lambda t: cart_gauss_op(a, b, alpha, beta, omega0 + t * t, A, B)
     if math.isinf(t_max):
         # t = s / (1 - s) maps [0, 1) onto [0, inf)
         h = lambda s: f(s / (1.0 - s)) / (1.0 - s) ** 2 if s < 1.0 else 0.0
@@ -96,6 +98,8 @@ def cart_integral(op, a, b, alpha, beta, omega, A, B):
                 - cart_attenuated(a, b, alpha, beta, A, B, omega))
     if op == 4:
         return cart_gauss_op(a, b, alpha, beta, omega, A, B)
+    if op == 5:
+        return cart_attenuated(a, b, alpha, beta, A, B, math.inf, omega0=omega)
     raise ValueError(op)
 
 

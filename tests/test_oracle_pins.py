@@ -16,7 +16,7 @@ import oracle
 from paper_1701_06588_gb300 import workloads as W
 from tests import quadrature as Q
 
-OPS = [(0, 0.0), (1, 0.0), (2, 0.11), (3, 0.11), (4, 1.0)]
+OPS = [(0, 0.0), (1, 0.0), (2, 0.11), (3, 0.11), (4, 1.0), (5, 0.3)]
 
 
 # --------------------------------------------------------------------------- #
@@ -177,6 +177,12 @@ def test_ss_closed_form_limits():
     g = oracle.ss_deriv(4, a, b, 1e8, R2, 0)[0] * (1e8 / math.pi) ** 1.5
     s = oracle.ss_deriv(0, a, b, 0, R2, 0)[0]
     assert abs(g - s) < 1e-6 * s
+    # exp(-omega r^2)/r: omega = 0 is the Coulomb operator, every derivative order
+    np.testing.assert_allclose(oracle.ss_deriv(5, a, b, 0.0, R2, 6), c, rtol=1e-14)
+    # omega -> inf: exp(-omega r^2)/r ~ (2 pi / omega) delta(r) on smooth densities
+    w = 1e8
+    gd = oracle.ss_deriv(5, a, b, w, R2, 0)[0] * w / (2 * math.pi)
+    assert abs(gd - s) < 1e-6 * s
 
 
 def test_ss_derivatives_by_finite_differences():
