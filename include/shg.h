@@ -5,7 +5,8 @@
  * solid-harmonic Gaussian shells by the SHG scheme of Golze, Benedikter,
  * Iannuzzi, Wilhelm and Hutter (arXiv:1701.06588):
  *   - two-center integrals (a|O|b) for O = delta (overlap), 1/r, erfc(w r)/r,
- *     erf(w r)/r and exp(-w r^2)  (Sec. II B, Eq. final_r12int_ab; Table S1),
+ *     erf(w r)/r, exp(-w r^2) and exp(-w r^2)/r (Sec. II B, Eq.
+ *     final_r12int_ab; Table S1, whose s-type rows define all six),
  *   - three-index overlaps (a b a~) with a and a~ on one center (Sec. II D),
  *   - gradients of both with respect to the centers (Sec. II E, Eq. dev_ab).
  *
@@ -57,7 +58,8 @@ enum shg_operator {
     SHG_OP_COULOMB = 1, /* 1/r12                                                  */
     SHG_OP_ERFC = 2,    /* erfc(w r12)/r12, short range, w > 0                    */
     SHG_OP_ERF = 3,     /* erf(w r12)/r12, long range, w > 0                      */
-    SHG_OP_GAUSS = 4    /* exp(-w r12^2), w > 0                                   */
+    SHG_OP_GAUSS = 4,   /* exp(-w r12^2), w > 0                                   */
+    SHG_OP_GAUSS_COULOMB = 5 /* exp(-w r12^2)/r12, Gaussian-damped Coulomb, w > 0 */
 };
 
 enum shg_precision {
@@ -136,7 +138,8 @@ int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64
  *   basis          shells for both sides
  *   n_pairs        number of pairs (0 is allowed and does nothing)
  *   d_pair_a/b     device int32[n_pairs] shell indices
- *   op, omega      operator (enum shg_operator); omega > 0 for ERF, ERFC, GAUSS
+ *   op, omega      operator (enum shg_operator); omega > 0 for ERF, ERFC, GAUSS,
+ *                  GAUSS_COULOMB
  *   screen_thresh  0 disables screening; > 0: a pair whose bound on every
  *                  element magnitude is below it writes zeros (overlap and
  *                  Gaussian operator only; Coulomb-type pairs are never

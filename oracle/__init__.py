@@ -13,7 +13,7 @@ Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, exact quadrature, symmetry relations and brute force.
 """
 from .oracle import (  # noqa: F401
-    OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS,
+    OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS, OP_GCOUL,
     build, lib_path, boys, ss_deriv, sph_coef, cart_2c, shell_norms,
     eval_2c, eval_2c_grad, eval_3c_aab, eval_3c_aab_grad, ncart,
 )

@@ -6,7 +6,7 @@ import threading
 
 import numpy as np
 
-OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS = 0, 1, 2, 3, 4
+OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS, OP_GCOUL = 0, 1, 2, 3, 4, 5
 
 # The contracted integrals are taken from the long-double build by default:
 # in FP64 the Cartesian recursion loses up to ~1e-13 absolute accuracy on the

@@ -15,7 +15,7 @@
 """
 import numpy as np
 
-OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS = 0, 1, 2, 3, 4
+OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS, OP_GCOUL = 0, 1, 2, 3, 4, 5
 
 
 def shg_contracted_elements(l_a, l_b, k_a, k_b, gradients=False):
@@ -45,6 +45,12 @@ def _radial_flops(op, J, kmin):
         return setup + 4 + powk + J * (1 + 1)
     if op == OP_GAUSS:
         return setup + 10 + powk + J * (1 + 1)
+    if op == OP_GCOUL:
+        # d, 1/d, p, q, prefactor, exp argument; Boys head and the full downward
+        # recursion to F_0; kmax applications of v_i <- p v_i + q v_{i+1} over a
+        # shrinking vector; J accumulations
+        kmax = kmin + J - 1
+        return setup + 12 + _BOYS + 3 * kmax + 3 * kmax * (kmax + 1) // 2 + J * (1 + 1)
     coul = 4 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
     att = 6 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
     if op == OP_COULOMB:
@@ -56,7 +62,7 @@ def _radial_flops(op, J, kmin):
 
 def _radial_special(op):
     """Special-function calls per primitive pair (rsqrt, exp)."""
-    return {OP_OVERLAP: 2, OP_GAUSS: 3, OP_COULOMB: 1, OP_ERF: 2, OP_ERFC: 2}[op]
+    return {OP_OVERLAP: 2, OP_GAUSS: 3, OP_COULOMB: 1, OP_ERF: 2, OP_ERFC: 2, OP_GCOUL: 3}[op]
 
 
 def pair_flops(la, lb, ka, kb, op):

@@ -186,6 +186,7 @@ void fill_consts_mix(ConstsMix &k)
     k.pi3 = split2(pi * pi * pi);
     k.two_pi52 = split2(2 * std::pow(pi, 2.5L));
     k.sqrt_pi_half = split2(std::sqrt(pi) / 2);
+    k.two_pi = split2(2 * pi);
     long double dfc = 1;
     for (int n = 0; n < kBoysN; ++n) {
         k.dfact[n] = split2(dfc);
@@ -544,8 +545,8 @@ static int current_device_matches(int dev)
 
 int check_op(int op, double omega, int precision)
 {
-    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS) return fail(SHG_EINVAL, "bad operator %d", op);
-    if ((op == SHG_OP_ERF || op == SHG_OP_ERFC || op == SHG_OP_GAUSS) && !(omega > 0 && std::isfinite(omega)))
+    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS_COULOMB) return fail(SHG_EINVAL, "bad operator %d", op);
+    if (op != SHG_OP_OVERLAP && op != SHG_OP_COULOMB && !(omega > 0 && std::isfinite(omega)))
         return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
     if (precision != SHG_PREC_FP64 && precision != SHG_PREC_MIXED)
         return fail(SHG_EINVAL, "precision %d not available", precision);

@@ -11,8 +11,9 @@ constexpr double kPi32 = 5.568327996831707845284817982118835702;      // pi^{3/2
 constexpr double kTwoPi52 = 34.98683665524972497843742820021;         // 2 pi^{5/2}
 constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
 constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
+constexpr double kPi = 3.141592653589793238462643383279502884;        // pi
 
-enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5 };
 
 // ------------------------------------------------------------------------- //
 // Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
@@ -27,11 +28,10 @@ enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4 };
 // ------------------------------------------------------------------------- //
 __device__ __forceinline__ double powi(double x, int n);
 
-template <int J>
-__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
-                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+// F_kmax and exp(-T) (0 where it is below 1e-52).
+__device__ __forceinline__ void boys_head(double T, int kmax, const double *__restrict__ tab,
+                                          const double *__restrict__ etab, const Consts &k, double &f, double &e)
 {
-    double f, e;
     if (T < kBoysTmax) {
         const int i = __double2int_rn(T * 16.0);
         const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
@@ -59,6 +59,14 @@ __device__ __forceinline__ void boys_top(double T, int kmax, const double *__res
         f = k.dfact[kmax] * powi(0.5 * rT * rT, kmax) * (kSqrtPiHalf * rT);
         e = 0.0;
     }
+}
+
+template <int J>
+__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
+                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+{
+    double f, e;
+    boys_head(T, kmax, tab, etab, k, f, e);
     // downward recursion F_{k-1} = (2T F_k + exp(-T)) / (2k-1), shared by both branches
     F[0] = f;
     const double twoT = T + T;
@@ -67,6 +75,18 @@ __device__ __forceinline__ void boys_top(double T, int kmax, const double *__res
         const int kk = kmax - j + 1;
         F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
     }
+}
+
+// All of F_0 .. F_kmax (F[n] = F_n, runtime kmax <= kBoysN - 1): the same head
+// and the same downward recursion, run to n = 0.
+__device__ __forceinline__ void boys_all(double T, int kmax, const double *__restrict__ tab,
+                                         const double *__restrict__ etab, const Consts &k, double *F)
+{
+    double f, e;
+    boys_head(T, kmax, tab, etab, k, f, e);
+    F[kmax] = f;
+    const double twoT = T + T;
+    for (int n = kmax; n > 0; --n) F[n - 1] = fma(twoT, F[n], e) * k.inv_int[2 * n - 1];
 }
 
 __device__ __forceinline__ double powi(double x, int n)
@@ -193,6 +213,29 @@ __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec
         for (int j = J - 1; j >= 0; --j) {
             O[j] += q;
             q *= f;
+        }
+    } else if (OP == OP_GCOUL) {
+        // exp(-w r^2)/r: (pi/c)^{3/2} (2 pi/d) exp(-w T/d) sum_i C(k,i) p^{k-i} q^i F_i(T rho/d),
+        // d = rho + w, p = -w rho/d, q = -rho^2/d.  Every order comes from one vector
+        // F_0..F_kmax by k applications of v_i <- p v_i + q v_{i+1} (p, q < 0: no
+        // cancellation); the first kmin run over the whole vector, the last J-1
+        // over a J-wide register window.
+        const double id = 1.0 / (rho + g.omega);
+        const double p = -g.omega * rho * id, q = -rho * rho * id;
+        const double pre = w * kPi32 * ic * rc * (2.0 * kPi) * id * exp(-g.omega * T * id);
+        double F[kBoysN];
+        boys_all(T * rho * id, kmax, g.boys, g.boys_e, g.k, F);
+        for (int m = 1; m <= kmin; ++m)
+            for (int i = 0; i <= kmax - m; ++i) F[i] = fma(p, F[i], q * F[i + 1]);
+        double v[J];
+#pragma unroll
+        for (int i = 0; i < J; ++i) v[i] = F[i];
+        O[J - 1] += pre * v[0];
+#pragma unroll
+        for (int t = 1; t < J; ++t) {
+#pragma unroll
+            for (int i = 0; i < J - t; ++i) v[i] = fma(p, v[i], q * v[i + 1]);
+            O[J - 1 - t] += pre * v[0];
         }
     } else {
         // Coulomb-type: 2 pi^{5/2} / (alpha beta sqrt(c)) * ...

@@ -198,6 +198,7 @@ cudaError_t launch_2c_grad(const Args2c &a, int op, int precision, int grid, cud
     case OP_ERFC: k_2c_grad_fp64_persistent<OP_ERFC><<<grid, 128, 0, s>>>(a); break;
     case OP_ERF: k_2c_grad_fp64_persistent<OP_ERF><<<grid, 128, 0, s>>>(a); break;
     case OP_GAUSS: k_2c_grad_fp64_persistent<OP_GAUSS><<<grid, 128, 0, s>>>(a); break;
+    case OP_GCOUL: k_2c_grad_fp64_persistent<OP_GCOUL><<<grid, 128, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -211,7 +212,8 @@ int persistent_grid_2c_grad(int op, int precision)
     case OP_COULOMB: return grid_for<OP_COULOMB>();
     case OP_ERFC: return grid_for<OP_ERFC>();
     case OP_ERF: return grid_for<OP_ERF>();
-    default: return grid_for<OP_GAUSS>();
+    case OP_GAUSS: return grid_for<OP_GAUSS>();
+    default: return grid_for<OP_GCOUL>();
     }
 }
 

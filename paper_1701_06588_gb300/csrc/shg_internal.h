@@ -82,7 +82,7 @@ struct ConstsMix {
     float2 inv_int[64];                    // 1/n
     float2 inv_fact[14];                   // 1/t!
     float inv_fact_f[14];
-    float2 pi32, pi3, two_pi52, sqrt_pi_half;
+    float2 pi32, pi3, two_pi52, sqrt_pi_half, two_pi;
     float2 dfact[kBoysN];                  // (2n-1)!!
 };
 

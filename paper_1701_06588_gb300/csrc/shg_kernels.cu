@@ -122,7 +122,8 @@ __device__ __forceinline__ void run_tile_fp64(const Args2c &g, int op, const Til
     case OP_COULOMB: pair_2c_fp64_dispatch<OP_COULOMB>(g, p, J); break;
     case OP_ERFC: pair_2c_fp64_dispatch<OP_ERFC>(g, p, J); break;
     case OP_ERF: pair_2c_fp64_dispatch<OP_ERF>(g, p, J); break;
-    default: pair_2c_fp64_dispatch<OP_GAUSS>(g, p, J); break;
+    case OP_GAUSS: pair_2c_fp64_dispatch<OP_GAUSS>(g, p, J); break;
+    default: pair_2c_fp64_dispatch<OP_GCOUL>(g, p, J); break;
     }
 }
 
@@ -375,6 +376,7 @@ cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persis
     case OP_ERFC: return launch_2c_op<OP_ERFC>(a, n, threads, persistent, s);
     case OP_ERF: return launch_2c_op<OP_ERF>(a, n, threads, persistent, s);
     case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, threads, persistent, s);
+    case OP_GCOUL: return launch_2c_op<OP_GCOUL>(a, n, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -391,7 +393,8 @@ int persistent_grid_2c(int op, int precision, int threads, int ctas_per_sm)
     case OP_COULOMB: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_COULOMB>, threads, 0); break;
     case OP_ERFC: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERFC>, threads, 0); break;
     case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, threads, 0); break;
+    case OP_GAUSS: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GCOUL>, threads, 0); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;

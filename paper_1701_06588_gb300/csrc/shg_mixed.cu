@@ -60,14 +60,12 @@ __device__ __noinline__ df exp_neg_df(df x, const ConstsMix &k)
     return df{e.hi * s, e.lo * s};
 }
 
-// Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}; same scheme as the FP64
-// path: Taylor head from the table below T = 120, asymptotic head above, then
-// one shared downward recursion.
-template <int J>
-__device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__restrict__ tab,
-                                             const float2 *__restrict__ etab, const ConstsMix &k, df (&F)[J])
+// Boys head in double-float: F_kmax and exp(-T) (0 above the table range),
+// the same scheme as the FP64 path: Taylor head from the table below T = 120,
+// asymptotic head above.
+__device__ __forceinline__ void boys_head_mix(df T, int kmax, const float4 *__restrict__ tab,
+                                              const float2 *__restrict__ etab, const ConstsMix &k, df &f, df &e)
 {
-    df f, e;
     if (T.hi < (float)kBoysTmax) {
         const int i = __float2int_rn(T.hi * 16.0f);
         const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
@@ -94,6 +92,16 @@ __device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__res
         f = mul(mul(ldf(k.dfact[kmax]), powi_df(scale2(mul(rT, rT), 0.5f), kmax)), mul(rT, ldf(k.sqrt_pi_half)));
         e = df_f(0.0f);
     }
+}
+
+// Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}: head, then one shared
+// downward recursion.
+template <int J>
+__device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__restrict__ tab,
+                                             const float2 *__restrict__ etab, const ConstsMix &k, df (&F)[J])
+{
+    df f, e;
+    boys_head_mix(T, kmax, tab, etab, k, f, e);
     F[0] = f;
     const df twoT = scale2(T, 2.0f);
 #pragma unroll
@@ -101,6 +109,17 @@ __device__ __forceinline__ void boys_top_mix(df T, int kmax, const float4 *__res
         const int kk = kmax - j + 1;
         F[j] = mul(add(mul(twoT, F[j - 1]), e), ldf(k.inv_int[2 * kk - 1]));
     }
+}
+
+// All of F_0 .. F_kmax (F[n] = F_n, runtime kmax <= kBoysN - 1).
+__device__ __forceinline__ void boys_all_mix(df T, int kmax, const float4 *__restrict__ tab,
+                                             const float2 *__restrict__ etab, const ConstsMix &k, df *F)
+{
+    df f, e;
+    boys_head_mix(T, kmax, tab, etab, k, f, e);
+    F[kmax] = f;
+    const df twoT = scale2(T, 2.0f);
+    for (int n = kmax; n > 0; --n) F[n - 1] = mul(add(mul(twoT, F[n]), e), ldf(k.inv_int[2 * n - 1]));
 }
 
 // S_j += (-1)^k base (2 rho)^-j X_k for one primitive pair, k = la+lb-j.
@@ -137,6 +156,31 @@ __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim 
         for (int j = J - 1; j >= 0; --j) {
             S[j] = add(S[j], mul(hp[j], X));
             X = mul(X, wd);
+        }
+    } else if (OP == OP_GCOUL) {
+        // exp(-w r^2)/r without the (-rho)^k carried by hp:
+        //   X_k = (pi/c)^{3/2} (2 pi/d) exp(-w T/d) sum_i C(k,i) (w/d)^{k-i} (rho/d)^i F_i(T rho/d),
+        // d = rho + w: binomial weights of a convex combination, applied as
+        // v_i <- (w/d) v_i + (rho/d) v_{i+1} (kmin times over F_0..F_kmax, then
+        // over a J-wide register window)
+        const int kmin = kmax - J + 1;
+        const df rd = rsqrt_df(add(rho, ldf(g.omega)));
+        const df id = mul(rd, rd);
+        const df sw = mul(ldf(g.omega), id), sr = mul(rho, id);
+        const df pre = mul(mul(ldf(g.km.pi32), mul(ic, rc)), mul(mul(ldf(g.km.two_pi), id), exp_neg_df(mul(T, sw), g.km)));
+        df F[kBoysN];
+        boys_all_mix(mul(T, sr), kmax, g.boys, g.boys_e, g.km, F);
+        for (int m = 1; m <= kmin; ++m)
+            for (int i = 0; i <= kmax - m; ++i) F[i] = add(mul(sw, F[i]), mul(sr, F[i + 1]));
+        df v[J];
+#pragma unroll
+        for (int i = 0; i < J; ++i) v[i] = F[i];
+        S[J - 1] = add(S[J - 1], mul(hp[J - 1], mul(pre, v[0])));
+#pragma unroll
+        for (int t = 1; t < J; ++t) {
+#pragma unroll
+            for (int i = 0; i < J - t; ++i) v[i] = add(mul(sw, v[i]), mul(sr, v[i + 1]));
+            S[J - 1 - t] = add(S[J - 1 - t], mul(hp[J - 1 - t], mul(pre, v[0])));
         }
     } else {
         const df pre = mul(mul(ldf(g.km.two_pi52), rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
@@ -377,6 +421,7 @@ cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent,
     case OP_ERFC: return launch_mix_op<OP_ERFC>(a, grid, threads, persistent, s);
     case OP_ERF: return launch_mix_op<OP_ERF>(a, grid, threads, persistent, s);
     case OP_GAUSS: return launch_mix_op<OP_GAUSS>(a, grid, threads, persistent, s);
+    case OP_GCOUL: return launch_mix_op<OP_GCOUL>(a, grid, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -388,7 +433,8 @@ int persistent_grid_2c_mixed(int op, int threads, int ctas_per_sm)
     case OP_COULOMB: return grid_mix<OP_COULOMB>(threads, ctas_per_sm);
     case OP_ERFC: return grid_mix<OP_ERFC>(threads, ctas_per_sm);
     case OP_ERF: return grid_mix<OP_ERF>(threads, ctas_per_sm);
-    default: return grid_mix<OP_GAUSS>(threads, ctas_per_sm);
+    case OP_GAUSS: return grid_mix<OP_GAUSS>(threads, ctas_per_sm);
+    default: return grid_mix<OP_GCOUL>(threads, ctas_per_sm);
     }
 }
 

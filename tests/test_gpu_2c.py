@@ -8,7 +8,8 @@ from tests.parity import TOL_FP64, assert_parity, reference_2c
 
 pytestmark = pytest.mark.gpu
 
-OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0),
+       ("gauss_coulomb", 5, 0.3)]
 _REF = {}
 
 
@@ -64,7 +65,7 @@ def test_c2_subset(shg, opname, op, omega):
     assert_parity(got, ref, TOL_FP64, "c2 %s" % opname, scale)
 
 
-@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("gauss_coulomb", 5, 0.3)])
 def test_c3_subset_high_l_long_contractions(shg, opname, op, omega):
     """l up to 6, K up to 20, exponents to 5000."""
     sh, pa, pb = W.make("c3_2m_l6_k20", n=1500)
@@ -146,7 +147,7 @@ def test_errors_are_reported(shg):
     plan = shg.Plan2c(b, good, good)
     out = torch.zeros(100, dtype=torch.float64, device="cuda")
     off = torch.zeros(4, dtype=torch.int64, device="cuda")
-    for op, om in [("erf", 0.0), ("gauss", -1.0), (7, 1.0)]:
+    for op, om in [("erf", 0.0), ("gauss", -1.0), ("gauss_coulomb", 0.0), (7, 1.0)]:
         with pytest.raises(L.ShgError):
             plan.exec(op, off, out, omega=om)
     plan.close()

@@ -10,7 +10,8 @@ from tests.parity import normalised
 
 pytestmark = pytest.mark.gpu
 
-GRAD_OPS = [("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("overlap", 0, 0.0), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+GRAD_OPS = [("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("overlap", 0, 0.0), ("erf", 3, 0.11), ("gauss", 4, 1.0),
+            ("gauss_coulomb", 5, 0.3)]
 
 
 @pytest.fixture(scope="module")

@@ -13,7 +13,8 @@ from tests.parity import TOL_MIXED, assert_parity, reference_2c
 
 pytestmark = pytest.mark.gpu
 
-OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0),
+       ("gauss_coulomb", 5, 0.3)]
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +49,7 @@ def test_mixed_c1(shg, opname, op, omega, schedule):
     assert_parity(got, ref, TOL_MIXED, "mixed c1 %s" % opname, scale)
 
 
-@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("gauss_coulomb", 5, 0.3)])
 def test_mixed_c3_high_l(shg, opname, op, omega):
     sh, pa, pb = W.make("c3_2m_l6_k20", n=1500)
     got, _ = _run(shg, sh, pa, pb, opname, omega)
