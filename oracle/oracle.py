@@ -57,6 +57,7 @@ def _lib(long_double=False):
             lib.oracle_shell_norms.argtypes = [i32, P, P, P, P, P, P]
             lib.oracle_eval_2c.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i32, f64, i32, i32, P, P, i32]
             lib.oracle_eval_3c_aab.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, P, i32, i32, P, P, i32]
+            lib.oracle_eval_2c_ra2n.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i32, i32, i32, P, P, i32]
             _libs[long_double] = lib
         return _libs[long_double]
 
@@ -131,7 +132,7 @@ def _threads(nthreads):
     return int(nthreads) if nthreads else (os.cpu_count() or 1)
 
 
-def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double, normalize=True):
+def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double, normalize=True, ra2n=None):
     s = _Shells(shells)
     pa = np.ascontiguousarray(pair_a, dtype=np.int32)
     pb = np.ascontiguousarray(pair_b, dtype=np.int32)
@@ -141,10 +142,14 @@ def _eval2c(shells, pair_a, pair_b, op, omega, deriv, nthreads, long_double, nor
         offsets[1:] = np.cumsum(sizes[:-1])
     total = int(sizes.sum())
     out = np.zeros(total * (3 if deriv else 1))
-    r = _lib(long_double).oracle_eval_2c(*s.args(), len(pa), _p(pa), _p(pb), int(op), float(omega), int(deriv),
-                                         int(bool(normalize)), _p(offsets), _p(out), _threads(nthreads))
+    if ra2n is None:
+        r = _lib(long_double).oracle_eval_2c(*s.args(), len(pa), _p(pa), _p(pb), int(op), float(omega), int(deriv),
+                                             int(bool(normalize)), _p(offsets), _p(out), _threads(nthreads))
+    else:
+        r = _lib(long_double).oracle_eval_2c_ra2n(*s.args(), len(pa), _p(pa), _p(pb), int(ra2n), int(deriv),
+                                                  int(bool(normalize)), _p(offsets), _p(out), _threads(nthreads))
     if r:
-        raise ValueError("oracle_eval_2c failed: %d" % r)
+        raise ValueError("oracle two-center evaluation failed: %d" % r)
     return out, offsets, sizes
 
 
@@ -166,6 +171,17 @@ def eval_2c_grad(shells, pair_a, pair_b, op, omega=0.0, center="A", nthreads=Non
     laid out [xyz][m_a][m_b].
     """
     return _eval2c(shells, pair_a, pair_b, op, omega, 1 if center == "A" else 2, nthreads, long_double, normalize)
+
+
+def eval_2c_ra2n(shells, pair_a, pair_b, n, nthreads=None, long_double=None, normalize=True):
+    """Contracted normalised blocks (a|r_a^{2n}|b) (Sec. II C), laid out as eval_2c."""
+    return _eval2c(shells, pair_a, pair_b, 0, 0.0, 0, nthreads, long_double, normalize, ra2n=n)
+
+
+def eval_2c_ra2n_grad(shells, pair_a, pair_b, n, center="A", nthreads=None, long_double=None, normalize=True):
+    """Jacobian of the (a|r_a^{2n}|b) blocks with respect to R_a or R_b, laid out as eval_2c_grad."""
+    return _eval2c(shells, pair_a, pair_b, 0, 0.0, 1 if center == "A" else 2, nthreads, long_double, normalize,
+                   ra2n=n)
 
 
 def _eval3c(shells, ta, tt, tb, deriv, nthreads, long_double, normalize=True):

@@ -517,6 +517,114 @@ static void pair_2c(work_t *w, const shells_t *S, int sa, int sb, int op, real o
     free(C);
 }
 
+/* ------------------------------------------------------------------------ */
+/* (a|r_a^{2n}|b) (Sec. II C) by a route independent of the SHG formula:     */
+/* r_A^{2n} = (x_A^2 + y_A^2 + z_A^2)^n is expanded multinomially, each term  */
+/* raising the Cartesian powers on A by (2p, 2q, 2s); the overlap of two      */
+/* Cartesian Gaussians factorises over x, y, z and each 1-D factor has the    */
+/* textbook closed form (Gaussian product theorem, binomial expansion about   */
+/* P = (alpha A + beta B)/c, even moments of exp(-c t^2)):                     */
+/*   int (x-A)^i (x-B)^j exp(-alpha (x-A)^2 - beta (x-B)^2) dx                */
+/*     = exp(-rho X^2) sum_{k<=i, l<=j} C(i,k) C(j,l) (P-A)^{i-k} (P-B)^{j-l}  */
+/*       M_{k+l},   M_t = sqrt(pi/c) (t-1)!! / (2c)^{t/2} (t even), 0 (t odd). */
+/* ------------------------------------------------------------------------ */
+static real ipow(real x, int n) { real r = 1; for (int i = 0; i < n; ++i) r *= x; return r; }
+
+static real ov1d(int i, int j, real alpha, real beta, real A, real B)
+{
+    if (i < 0 || j < 0) return 0;
+    real c = alpha + beta, rho = alpha * beta / c;
+    real P = (alpha * A + beta * B) / c, X = A - B;
+    real sum = 0;
+    for (int k = 0; k <= i; ++k)
+        for (int l = 0; l <= j; ++l) {
+            int t = k + l;
+            if (t & 1) continue;
+            real m = R_SQRT(R_PI / c);
+            for (int u = t - 1; u > 0; u -= 2) m *= u;
+            for (int u = 0; u < t / 2; ++u) m /= 2 * c;
+            sum += binom(i, k) * binom(j, l) * ipow(P - A, i - k) * ipow(P - B, j - l) * m;
+        }
+    return R_EXP(-rho * X * X) * sum;
+}
+
+/* Cartesian primitive integral of g_a r_A^{2n} against g_b; deriv = 1: d/dA_dir,
+ * deriv = 2: d/dB_dir (d/dA_x of (x-A)^e exp(-alpha (x-A)^2) is
+ * 2 alpha (x-A)^{e+1} exp(..) - e (x-A)^{e-1} exp(..), the same on B). */
+static real cart_ra2n(const int *a, const int *b, int n, real al, real be, const real *A, const real *B, int deriv,
+                      int dir)
+{
+    real tot = 0;
+    for (int p = 0; p <= n; ++p)
+        for (int q = 0; q <= n - p; ++q) {
+            int r = n - p - q;
+            real mult = fact(n) / (fact(p) * fact(q) * fact(r));
+            int e[3] = {a[0] + 2 * p, a[1] + 2 * q, a[2] + 2 * r};
+            real f = 1;
+            for (int d = 0; d < 3; ++d) {
+                real v;
+                if (deriv == 1 && d == dir)
+                    v = 2 * al * ov1d(e[d] + 1, b[d], al, be, A[d], B[d]) - e[d] * ov1d(e[d] - 1, b[d], al, be, A[d], B[d]);
+                else if (deriv == 2 && d == dir)
+                    v = 2 * be * ov1d(e[d], b[d] + 1, al, be, A[d], B[d]) - b[d] * ov1d(e[d], b[d] - 1, al, be, A[d], B[d]);
+                else
+                    v = ov1d(e[d], b[d], al, be, A[d], B[d]);
+                f *= v;
+            }
+            tot += mult * f;
+        }
+    return tot;
+}
+
+/* Contracted, normalised block of (a|r_a^{2n}|b) (deriv as in pair_2c). */
+static void pair_ra2n(work_t *w, const shells_t *S, int sa, int sb, int n, int deriv, int normalize, double *out)
+{
+    int la = S->l[sa], lb = S->l[sb];
+    int nca = ncart(la), ncb = ncart(lb);
+    int na = 2 * la + 1, nb = 2 * lb + 1;
+    real A[3], B[3];
+    get_center(S, sa, A);
+    get_center(S, sb, B);
+    real Na = normalize ? shell_norm(w->c, S, sa, w->tsph[la]) : 1;
+    real Nb = normalize ? shell_norm(w->c, S, sb, w->tsph[lb]) : 1;
+    int ncomp = deriv ? 3 : 1;
+    real *C = (real *)calloc((size_t)ncomp * nca * ncb, sizeof(real));
+    for (int i = 0; i < S->nprim[sa]; ++i)
+        for (int j = 0; j < S->nprim[sb]; ++j) {
+            real al = S->exps[S->prim_off[sa] + i], be = S->exps[S->prim_off[sb] + j];
+            real cc = (real)S->coefs[S->prim_off[sa] + i] * (real)S->coefs[S->prim_off[sb] + j];
+            for (int ax = la; ax >= 0; --ax)
+                for (int ay = la - ax; ay >= 0; --ay) {
+                    int a[3] = {ax, ay, la - ax - ay};
+                    int pa = cpos(a[0], a[1], a[2]);
+                    for (int bx = lb; bx >= 0; --bx)
+                        for (int by = lb - bx; by >= 0; --by) {
+                            int b[3] = {bx, by, lb - bx - by};
+                            int pb = cpos(b[0], b[1], b[2]);
+                            for (int d = 0; d < ncomp; ++d)
+                                C[((size_t)d * nca + pa) * ncb + pb] += cc * cart_ra2n(a, b, n, al, be, A, B, deriv, d);
+                        }
+                }
+        }
+    const real *Ta = w->tsph[la], *Tb = w->tsph[lb];
+    for (int d = 0; d < ncomp; ++d)
+        for (int ma = 0; ma < na; ++ma)
+            for (int mb = 0; mb < nb; ++mb) {
+                real acc = 0;
+                for (int pa = 0; pa < nca; ++pa) {
+                    real ta = Ta[ma * nca + pa];
+                    if (ta == 0) continue;
+                    for (int pb = 0; pb < ncb; ++pb) {
+                        real tb = Tb[mb * ncb + pb];
+                        if (tb == 0) continue;
+                        acc += ta * tb * C[((size_t)d * nca + pa) * ncb + pb];
+                    }
+                }
+                out[(size_t)d * na * nb + ma * nb + mb] = (double)(Na * Nb * acc);
+            }
+    free(C);
+}
+
 /*
  * Contracted, normalised three-index overlap (a b a~) = int phi_a phi_a~ phi_b,
  * with a and a~ on the same center A.  Output block [m_a][m_a~][m_b].
@@ -651,6 +759,30 @@ int oracle_eval_2c(int n_shells, const int32_t *l, const int32_t *nprim, const i
 #pragma omp for schedule(dynamic, 4)
         for (int64_t p = 0; p < n_pairs; ++p)
             pair_2c(&w, &S, pa[p], pb[p], op, (real)omega, deriv, normalize, out + (deriv ? 3 : 1) * offsets[p]);
+        work_free(&w);
+    }
+    return 0;
+}
+
+/*
+ * (a|r_a^{2n}|b) blocks, 0 <= n <= 8 (n = 0 is the overlap); layout and
+ * deriv/normalize as oracle_eval_2c.
+ */
+int oracle_eval_2c_ra2n(int n_shells, const int32_t *l, const int32_t *nprim, const int64_t *prim_off,
+                        const double *exps, const double *coefs, const double *centers, const int32_t *center_of,
+                        int64_t n_pairs, const int32_t *pa, const int32_t *pb, int n, int deriv, int normalize,
+                        const int64_t *offsets, double *out, int nthreads)
+{
+    shells_t S = {n_shells, l, nprim, prim_off, exps, coefs, centers, center_of};
+    if (check_shells(&S, 6)) return -1;
+    if (n < 0 || n > 8) return -2;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+    {
+        work_t w;
+        work_init(&w);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t p = 0; p < n_pairs; ++p)
+            pair_ra2n(&w, &S, pa[p], pb[p], n, deriv, normalize, out + (deriv ? 3 : 1) * offsets[p]);
         work_free(&w);
     }
     return 0;

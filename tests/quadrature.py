@@ -106,3 +106,22 @@ def cart_integral(op, a, b, alpha, beta, omega, A, B):
 def cart_triple_overlap(a, t, b, alpha, alpha_t, beta, A, B):
     """int g_a(alpha) g_t(alpha_t) g_b(beta), g_a and g_t on A."""
     return np.prod([overlap_1d(a[d] + t[d], b[d], alpha + alpha_t, beta, A[d], B[d]) for d in range(3)])
+
+
+def cart_ra2n(a, b, alpha, beta, A, B, n):
+    """int g_a(alpha) |r - A|^{2n} g_b(beta) over R^3 by a 3-D Gauss-Hermite
+    product rule about the Gaussian product center (exact: the integrand is a
+    polynomial of degree < 48 per variable times the product Gaussian)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    c = alpha + beta
+    P = (alpha * A + beta * B) / c
+    rho = alpha * beta / c
+    x, w = _GH[24]
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    pts = P[None, :] + np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1) / math.sqrt(c)
+    W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).ravel()
+    da, db = pts - A[None, :], pts - B[None, :]
+    poly = np.prod(da ** np.asarray(a)[None, :], axis=1) * np.prod(db ** np.asarray(b)[None, :], axis=1)
+    poly = poly * np.sum(da * da, axis=1) ** n
+    return math.exp(-rho * float(np.dot(A - B, A - B))) * float(np.sum(W * poly)) / c ** 1.5

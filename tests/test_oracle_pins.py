@@ -348,6 +348,79 @@ def test_operator_limits_on_contracted_blocks():
 
 
 # --------------------------------------------------------------------------- #
+# (a|r_a^{2n}|b) (Sec. II C)                                                  #
+# --------------------------------------------------------------------------- #
+def test_ra2n_zero_is_the_overlap():
+    """n = 0: the closed-form 1-D route equals the recursion-based overlap."""
+    sh, pa, pb = _small_two_center(41, n=10, lmax=4, kmax=3)
+    v, _, _ = oracle.eval_2c_ra2n(sh, pa, pb, 0)
+    s, _, _ = oracle.eval_2c(sh, pa, pb, 0)
+    np.testing.assert_allclose(v, s, rtol=0, atol=1e-13 * np.abs(s).max())
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_ra2n_contracted_blocks_against_3d_quadrature(n):
+    """Contracted blocks vs 3-D quadrature of g_a |r - A|^{2n} g_b (no
+    multinomial expansion, no 1-D closed form)."""
+    sh, pa, pb = _small_two_center(50 + n, n=3, lmax=2, kmax=2)
+    v, o, z = oracle.eval_2c_ra2n(sh, pa, pb, n)
+    N = oracle.shell_norms(sh)
+    off = np.r_[0, np.cumsum(sh["nprim"])]
+    for p, blk in enumerate(_blocks(v, o, z, sh, pa, pb)):
+        a, b = pa[p], pb[p]
+        la, lb = int(sh["l"][a]), int(sh["l"][b])
+        A = sh["centers"][sh["center_of"][a]]
+        B = sh["centers"][sh["center_of"][b]]
+        C = np.zeros((len(Q.cart_list(la)), len(Q.cart_list(lb))))
+        for i in range(off[a], off[a + 1]):
+            for j in range(off[b], off[b + 1]):
+                for ia, ca in enumerate(Q.cart_list(la)):
+                    for ib, cb in enumerate(Q.cart_list(lb)):
+                        C[ia, ib] += sh["coefs"][i] * sh["coefs"][j] * Q.cart_ra2n(
+                            ca, cb, sh["exps"][i], sh["exps"][j], A, B, n)
+        ref = N[a] * N[b] * oracle.sph_coef(la) @ C @ oracle.sph_coef(lb).T
+        np.testing.assert_allclose(blk, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_ra2n_s_functions_match_the_printed_closed_form():
+    """(0_a|r_a^{2m}|0_b) = pi^{3/2} exp(-rho R^2) / (2^m c^{m+3/2}) sum_j I_j
+    with I_j = 2^j (2m+1)!! C(m,j) / (2j+1)!! beta^{2j} R^{2j} / c^j (Eq. sra2ms, I_jab)."""
+    def dfact(k):
+        return math.prod(range(k, 0, -2)) if k > 0 else 1
+    for (al, be, R) in [(0.7, 1.9, 1.3), (3.0, 0.2, 2.5), (0.05, 11.0, 0.4)]:
+        c, rho = al + be, al * be / (al + be)
+        sh = dict(l=np.array([0, 0], np.int32), nprim=np.array([1, 1], np.int32), exps=np.array([al, be]),
+                  coefs=np.array([1.0, 1.0]), centers=np.array([[0.0, 0.0, 0.0], [0.3 * R, -0.4 * R, math.sqrt(0.75) * R]]),
+                  center_of=np.array([0, 1], np.int32))
+        for m in range(6):
+            v, _, _ = oracle.eval_2c_ra2n(sh, [0], [1], m, normalize=False)
+            I = sum(2 ** j * dfact(2 * m + 1) * math.comb(m, j) / dfact(2 * j + 1) * be ** (2 * j) * R ** (2 * j) / c ** j
+                    for j in range(m + 1))
+            ref = math.pi ** 1.5 * math.exp(-rho * R * R) / (2 ** m * c ** (m + 1.5)) * I
+            assert abs(v[0] - ref) <= 1e-13 * ref, (al, be, R, m, v[0], ref)
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_ra2n_gradient_against_finite_differences_and_translation(n):
+    sh, pa, pb = _small_two_center(60 + n, n=4, lmax=3, kmax=2)
+    ga, o, z = oracle.eval_2c_ra2n_grad(sh, pa, pb, n, center="A")
+    gb, _, _ = oracle.eval_2c_ra2n_grad(sh, pa, pb, n, center="B")
+    np.testing.assert_allclose(ga, -gb, rtol=0, atol=1e-12 * np.abs(ga).max())
+    h = 1e-5
+    for p in range(len(pa)):
+        ca = sh["center_of"][pa[p]]
+        for d in range(3):
+            cp, cm = sh["centers"].copy(), sh["centers"].copy()
+            cp[ca, d] += h
+            cm[ca, d] -= h
+            vp, _, _ = oracle.eval_2c_ra2n(dict(sh, centers=cp), pa[p:p + 1], pb[p:p + 1], n)
+            vm, _, _ = oracle.eval_2c_ra2n(dict(sh, centers=cm), pa[p:p + 1], pb[p:p + 1], n)
+            fd = (vp - vm) / (2 * h)
+            an = ga[3 * o[p] + d * z[p]: 3 * o[p] + (d + 1) * z[p]]
+            np.testing.assert_allclose(an, fd, rtol=0, atol=2e-7 * max(np.abs(fd).max(), 1e-3))
+
+
+# --------------------------------------------------------------------------- #
 # Three-index overlap                                                         #
 # --------------------------------------------------------------------------- #
 def test_aab_against_quadrature():
