@@ -445,9 +445,11 @@ def other_configs(args):
     from paper_1701_06588_gb300 import api, workloads as W
     from paper_1701_06588_gb300 import counts
     res = {}
-    for key, name, ops in [("c1_2k_l3_k4", "c1_2k_l3_k4", [("overlap", 0.0), ("coulomb", 0.0)]),
-                           ("c3_2m_l6_k20", "c3_2m_l6_k20", [("coulomb", 0.0), ("erfc", 0.11)]),
-                           ("c2_200k_l4_k8 exp(-0.3 r^2)/r", "c2_200k_l4_k8", [("gauss_coulomb", 0.3)])]:
+    for key, name, ops, precs in [
+            ("c1_2k_l3_k4", "c1_2k_l3_k4", [("overlap", 0.0), ("coulomb", 0.0)], ("fp64", "mixed")),
+            ("c3_2m_l6_k20", "c3_2m_l6_k20", [("coulomb", 0.0), ("erfc", 0.11)], ("fp64", "mixed")),
+            ("c2_200k_l4_k8 exp(-0.3 r^2)/r", "c2_200k_l4_k8", [("gauss_coulomb", 0.3)], ("fp64", "mixed")),
+            ("c2_200k_l4_k8 r_a^4 (n = 2)", "c2_200k_l4_k8", [("ra2n", 2.0)], ("fp64",))]:
         sh, pa, pb = W.make(name)
         b = api.Basis(sh)
         off, total = b.pair_offsets(pa, pb)
@@ -456,7 +458,7 @@ def other_configs(args):
         plan = api.Plan2c(b, pa, pb)
         entry = {"pairs": len(pa), "operators": [o[0] for o in ops]}
         flops = sum(counts.workload_flops(sh, pa, pb, api.L.OPERATORS[n]) for n, _ in ops)
-        for prec in ("fp64", "mixed"):
+        for prec in precs:
             ms = sum(_events_ms(lambda n=n, w=w: plan.exec(n, d_off, out, omega=w, precision=prec), 3 if len(pa) > 1e5
                                 else 50) for n, w in ops)
             entry[prec] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),

@@ -6,7 +6,8 @@
  * Iannuzzi, Wilhelm and Hutter (arXiv:1701.06588):
  *   - two-center integrals (a|O|b) for O = delta (overlap), 1/r, erfc(w r)/r,
  *     erf(w r)/r, exp(-w r^2) and exp(-w r^2)/r (Sec. II B, Eq.
- *     final_r12int_ab; Table S1, whose s-type rows define all six),
+ *     final_r12int_ab; Table S1, whose s-type rows define all six), and
+ *     (a|r_a^{2n}|b) (Sec. II C, Eq. ara2nb),
  *   - three-index overlaps (a b a~) with a and a~ on one center (Sec. II D),
  *   - gradients of both with respect to the centers (Sec. II E, Eq. dev_ab).
  *
@@ -59,7 +60,10 @@ enum shg_operator {
     SHG_OP_ERFC = 2,    /* erfc(w r12)/r12, short range, w > 0                    */
     SHG_OP_ERF = 3,     /* erf(w r12)/r12, long range, w > 0                      */
     SHG_OP_GAUSS = 4,   /* exp(-w r12^2), w > 0                                   */
-    SHG_OP_GAUSS_COULOMB = 5 /* exp(-w r12^2)/r12, Gaussian-damped Coulomb, w > 0 */
+    SHG_OP_GAUSS_COULOMB = 5, /* exp(-w r12^2)/r12, Gaussian-damped Coulomb, w > 0 */
+    SHG_OP_RA2N = 6     /* r_a^{2n} = |r - R_a|^{2n}: (a|r_a^{2n}|b) of Sec. II C;
+                           n = 0..5 is passed in omega as an exact integer; FP64
+                           only (SHG_EINVAL for SHG_PREC_MIXED)                 */
 };
 
 enum shg_precision {
@@ -139,7 +143,8 @@ int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64
  *   n_pairs        number of pairs (0 is allowed and does nothing)
  *   d_pair_a/b     device int32[n_pairs] shell indices
  *   op, omega      operator (enum shg_operator); omega > 0 for ERF, ERFC, GAUSS,
- *                  GAUSS_COULOMB
+ *                  GAUSS_COULOMB; omega = n (0..5) for RA2N, whose radial
+ *                  term is T^{(k)} of Eq. T_rab2_deriv in place of O^{(k)}
  *   screen_thresh  0 disables screening; > 0: a pair whose bound on every
  *                  element magnitude is below it writes zeros (overlap and
  *                  Gaussian operator only; Coulomb-type pairs are never

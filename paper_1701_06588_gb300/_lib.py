@@ -12,12 +12,12 @@ import threading
 from . import build as _build
 
 SHG_OK, SHG_EINVAL, SHG_ENOMEM, SHG_ECUDA, SHG_ETIMEOUT, SHG_ERANGE = 0, -1, -2, -3, -4, -5
-SHG_OP_OVERLAP, SHG_OP_COULOMB, SHG_OP_ERFC, SHG_OP_ERF, SHG_OP_GAUSS, SHG_OP_GAUSS_COULOMB = 0, 1, 2, 3, 4, 5
+SHG_OP_OVERLAP, SHG_OP_COULOMB, SHG_OP_ERFC, SHG_OP_ERF, SHG_OP_GAUSS, SHG_OP_GAUSS_COULOMB, SHG_OP_RA2N = range(7)
 SHG_PREC_FP64, SHG_PREC_MIXED = 0, 1
 SHG_SCHED_PER_CLASS, SHG_SCHED_PERSISTENT = 0, 1
 
 OPERATORS = {"overlap": SHG_OP_OVERLAP, "coulomb": SHG_OP_COULOMB, "erfc": SHG_OP_ERFC, "erf": SHG_OP_ERF,
-             "gauss": SHG_OP_GAUSS, "gauss_coulomb": SHG_OP_GAUSS_COULOMB}
+             "gauss": SHG_OP_GAUSS, "gauss_coulomb": SHG_OP_GAUSS_COULOMB, "ra2n": SHG_OP_RA2N}
 PRECISIONS = {"fp64": SHG_PREC_FP64, "mixed": SHG_PREC_MIXED}
 SCHEDULES = {"per_class": SHG_SCHED_PER_CLASS, "persistent": SHG_SCHED_PERSISTENT}
 

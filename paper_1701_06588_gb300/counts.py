@@ -15,7 +15,7 @@
 """
 import numpy as np
 
-OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS, OP_GCOUL = 0, 1, 2, 3, 4, 5
+OP_OVERLAP, OP_COULOMB, OP_ERFC, OP_ERF, OP_GAUSS, OP_GCOUL, OP_RA2N = 0, 1, 2, 3, 4, 5, 6
 
 
 def shg_contracted_elements(l_a, l_b, k_a, k_b, gradients=False):
@@ -45,6 +45,12 @@ def _radial_flops(op, J, kmin):
         return setup + 4 + powk + J * (1 + 1)
     if op == OP_GAUSS:
         return setup + 10 + powk + J * (1 + 1)
+    if op == OP_RA2N:
+        # algorithmic count of the FP64 formula (the kernel runs it in double-double):
+        # coefficients of Q (n <= 5: 21 fma), kmax steps of the coefficient recursion
+        # (6 x 3), J Horner evaluations (6 fma) and accumulations
+        kmax = kmin + J - 1
+        return setup + 10 + 2 * 21 + kmax * 18 + J * (12 + 2)
     if op == OP_GCOUL:
         # d, 1/d, p, q, prefactor, exp argument; Boys head and the full downward
         # recursion to F_0; kmax applications of v_i <- p v_i + q v_{i+1} over a
@@ -62,7 +68,7 @@ def _radial_flops(op, J, kmin):
 
 def _radial_special(op):
     """Special-function calls per primitive pair (rsqrt, exp)."""
-    return {OP_OVERLAP: 2, OP_GAUSS: 3, OP_COULOMB: 1, OP_ERF: 2, OP_ERFC: 2, OP_GCOUL: 3}[op]
+    return {OP_OVERLAP: 2, OP_GAUSS: 3, OP_COULOMB: 1, OP_ERF: 2, OP_ERFC: 2, OP_GCOUL: 3, OP_RA2N: 3}[op]
 
 
 def pair_flops(la, lb, ka, kb, op):

@@ -118,6 +118,15 @@ void fill_consts(Consts &k)
         k.dfact[n] = (double)df;                 // (2n-1)!!
         df *= (2 * n + 1);
     }
+    // (a|r_a^{2n}|b): C(n, j) and the coefficients 2^{d-m} (2m+1)!! C(m,d) / (2d+1)!!
+    // of Eqs. sra2ms and I_jab
+    auto odd_fact = [](int n) { long double f = 1; for (int i = n; i > 1; i -= 2) f *= i; return f; };
+    for (int n = 0; n <= kRa2nMax; ++n)
+        for (int j = 0; j <= n; ++j) {
+            k.binom[n][j] = (double)(lfact(n) / (lfact(j) * lfact(n - j)));
+            k.ra2n_k[n][j] = (double)(std::ldexp(1.0L, j - n) * odd_fact(2 * n + 1) * (lfact(n) / (lfact(j) * lfact(n - j))) /
+                                      odd_fact(2 * j + 1));
+        }
 }
 
 // Boys table, computed in long double: F_N(T) from its power series
@@ -545,9 +554,14 @@ static int current_device_matches(int dev)
 
 int check_op(int op, double omega, int precision)
 {
-    if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS_COULOMB) return fail(SHG_EINVAL, "bad operator %d", op);
-    if (op != SHG_OP_OVERLAP && op != SHG_OP_COULOMB && !(omega > 0 && std::isfinite(omega)))
+    if (op < SHG_OP_OVERLAP || op > SHG_OP_RA2N) return fail(SHG_EINVAL, "bad operator %d", op);
+    if (op == SHG_OP_RA2N) {
+        if (!(omega >= 0 && omega <= kRa2nMax && omega == std::floor(omega)))
+            return fail(SHG_EINVAL, "SHG_OP_RA2N takes n = 0..%d in omega (got %g)", kRa2nMax, omega);
+        if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "SHG_OP_RA2N is available in FP64 only");
+    } else if (op != SHG_OP_OVERLAP && op != SHG_OP_COULOMB && !(omega > 0 && std::isfinite(omega))) {
         return fail(SHG_EINVAL, "operator %d needs omega > 0 (got %g)", op, omega);
+    }
     if (precision != SHG_PREC_FP64 && precision != SHG_PREC_MIXED)
         return fail(SHG_EINVAL, "precision %d not available", precision);
     return SHG_OK;

@@ -13,7 +13,7 @@ constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
 constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
 constexpr double kPi = 3.141592653589793238462643383279502884;        // pi
 
-enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5 };
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5, OP_RA2N = 6 };
 
 // ------------------------------------------------------------------------- //
 // Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //
@@ -180,12 +180,66 @@ __device__ __forceinline__ void w_row(const double *Rc, const double *Rs, int l,
 
 
 // ------------------------------------------------------------------------- //
+// Double-double arithmetic (unevaluated sums h + l of two FP64 numbers) from //
+// the error-free transformations TwoSum (Knuth), FastTwoSum (Dekker) and the //
+// FMA TwoProd; about 2^-104 relative per operation.  Used where a formula    //
+// cancels although the quantity it computes is well conditioned.            //
+// ------------------------------------------------------------------------- //
+struct ddv {
+    double h, l;
+};
+__device__ __forceinline__ ddv dd_fast(double a, double b)
+{
+    const double s = a + b;
+    return ddv{s, b - (s - a)};
+}
+__device__ __forceinline__ ddv dd_sum(double a, double b)
+{
+    const double s = a + b, bb = s - a;
+    return ddv{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ddv dd_prod(double a, double b)
+{
+    const double p = a * b;
+    return ddv{p, fma(a, b, -p)};
+}
+__device__ __forceinline__ ddv dd_add(ddv a, ddv b)
+{
+    ddv s = dd_sum(a.h, b.h);
+    const ddv t = dd_sum(a.l, b.l);
+    s = dd_fast(s.h, s.l + t.h);
+    return dd_fast(s.h, s.l + t.l);
+}
+__device__ __forceinline__ ddv dd_mul(ddv a, ddv b)
+{
+    const double p = a.h * b.h;
+    double e = fma(a.h, b.h, -p);
+    e = fma(a.h, b.l, e);
+    e = fma(a.l, b.h, e);
+    return dd_fast(p, e);
+}
+__device__ __forceinline__ ddv dd_mul_d(ddv a, double b)
+{
+    const double p = a.h * b;
+    const double e = fma(a.l, b, fma(a.h, b, -p));
+    return dd_fast(p, e);
+}
+// 1/a: FP64 reciprocal and one Newton step r + r (1 - a r) carried in double-double
+__device__ __forceinline__ ddv dd_inv(ddv a)
+{
+    const double r = 1.0 / a.h;
+    const ddv ar = dd_mul_d(a, r);
+    const ddv e = dd_add(ddv{1.0, 0.0}, ddv{-ar.h, -ar.l});
+    return dd_add(ddv{r, 0.0}, dd_mul_d(e, r));
+}
+
+// ------------------------------------------------------------------------- //
 // Radial terms of one primitive pair, accumulated into the contracted        //
 // O[j] = O^{(kmax-j)}, j = 0..J-1 (Table S1 and Eq. O_rab2_deriv).          //
 //   w = w_alpha w_beta = N_a N_b c_alpha c_beta / ((2alpha)^la (2beta)^lb)  //
 // ------------------------------------------------------------------------- //
 template <int OP, int J>
-__device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec &pb, double R2, int kmax,
+__device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec &pb, double R2, int kmax, int la,
                                                 const Args2c &g, double (&O)[J])
 {
     const int kmin = kmax - J + 1;
@@ -213,6 +267,65 @@ __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec
         for (int j = J - 1; j >= 0; --j) {
             O[j] += q;
             q *= f;
+        }
+    } else if (OP == OP_RA2N) {
+        // (a|r_a^{2n}|b), Eq. T_rab2_deriv with Eqs. sra2ms and I_jab.  Per primitive
+        // pair T(x) = w pi^{3/2} c^{-3/2} e^{-rho x} Q(x), x = R^2, with Q of degree n:
+        //   Q(x) = sum_d (beta^2 x / c)^d sum_{m=d}^{n} C(n, n-m) (la)_{n-m} alpha^{m-n} c^{-m} k_{m,d},
+        //   k_{m,d} = 2^{d-m} (2m+1)!! C(m,d) / (2d+1)!!  (an integer times a power of 2),
+        // (la)_j the rising factorial ((0)_0 = 1, (0)_j = 0).  Derivatives:
+        // T^{(k)} = w pi^{3/2} c^{-3/2} e^{-rho x} Q_k(x), Q_{k+1}[d] = (d+1) Q_k[d+1] - rho Q_k[d].
+        // For beta >> alpha the terms of Q_k are all of order alpha^{k-n} with
+        // alternating signs (T^{(k)} itself is well conditioned), so Q and its
+        // recursion run in double-double; the common factor stays in FP64.
+        const int n = __double2int_rn(g.omega);
+        const ddv cc = dd_sum(pa.alpha, pb.alpha);
+        const ddv icd = dd_inv(cc);
+        const ddv rhod = dd_mul(dd_prod(pa.alpha, pb.alpha), icd);
+        const ddv bcd = dd_mul(dd_prod(pb.alpha, pb.alpha), icd);
+        const ddv iad = dd_inv(ddv{pa.alpha, 0.0});
+        ddv tm[kRa2nMax + 1];
+#pragma unroll
+        for (int m = 0; m <= kRa2nMax; ++m) {
+            tm[m] = ddv{0.0, 0.0};
+            if (m <= n) {
+                const int j = n - m;
+                double rf = g.k.binom[n][j];                 // C(n, j) (la)_j: exact integer
+                for (int i = 0; i < j; ++i) rf *= (double)(la + i);
+                ddv t = ddv{rf, 0.0};
+                for (int i = 0; i < j; ++i) t = dd_mul(t, iad);
+                for (int i = 0; i < m; ++i) t = dd_mul(t, icd);
+                tm[m] = t;
+            }
+        }
+        ddv q[kRa2nMax + 2];
+        ddv bd = ddv{1.0, 0.0};
+#pragma unroll
+        for (int d = 0; d <= kRa2nMax; ++d) {
+            ddv sum = ddv{0.0, 0.0};
+#pragma unroll
+            for (int m = d; m <= kRa2nMax; ++m) sum = dd_add(sum, dd_mul_d(tm[m], g.k.ra2n_k[m][d]));
+            q[d] = dd_mul(bd, sum);
+            bd = dd_mul(bd, bcd);
+        }
+        q[kRa2nMax + 1] = ddv{0.0, 0.0};
+        const ddv mrho = ddv{-rhod.h, -rhod.l};
+        for (int k = 0; k < kmin; ++k) {
+#pragma unroll
+            for (int d = 0; d <= kRa2nMax; ++d) q[d] = dd_add(dd_mul_d(q[d + 1], (double)(d + 1)), dd_mul(mrho, q[d]));
+        }
+        const double we = w * kPi32 * ic * rc * exp(-T);
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+            ddv val = q[kRa2nMax];
+#pragma unroll
+            for (int d = kRa2nMax - 1; d >= 0; --d) val = dd_add(dd_mul_d(val, R2), q[d]);
+            O[J - 1 - t] += we * (val.h + val.l);
+            if (t + 1 < J) {
+#pragma unroll
+                for (int d = 0; d <= kRa2nMax; ++d)
+                    q[d] = dd_add(dd_mul_d(q[d + 1], (double)(d + 1)), dd_mul(mrho, q[d]));
+            }
         }
     } else if (OP == OP_GCOUL) {
         // exp(-w r^2)/r: (pi/c)^{3/2} (2 pi/d) exp(-w T/d) sum_i C(k,i) p^{k-i} q^i F_i(T rho/d),

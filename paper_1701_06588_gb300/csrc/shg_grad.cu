@@ -65,7 +65,7 @@ __device__ void pair_grad_fp64(const Args2c &g, int p)
     const int Kb = sb.nprim, npp = sa.nprim * Kb;
     for (int q = 0; q < npp; ++q) {
         const int ia = q / Kb, ib = q - ia * Kb;
-        radial_acc_fp64<OP, J + 1>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax + 1, g, Ox);
+        radial_acc_fp64<OP, J + 1>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax + 1, la, g, Ox);
     }
     // f0[e]: factor of Q~_j with O^{(kmax-j)}, f1[e]: with O^{(kmax-j+1)}
     double f0[J * J], f1[J * J];
@@ -199,6 +199,7 @@ cudaError_t launch_2c_grad(const Args2c &a, int op, int precision, int grid, cud
     case OP_ERF: k_2c_grad_fp64_persistent<OP_ERF><<<grid, 128, 0, s>>>(a); break;
     case OP_GAUSS: k_2c_grad_fp64_persistent<OP_GAUSS><<<grid, 128, 0, s>>>(a); break;
     case OP_GCOUL: k_2c_grad_fp64_persistent<OP_GCOUL><<<grid, 128, 0, s>>>(a); break;
+    case OP_RA2N: k_2c_grad_fp64_persistent<OP_RA2N><<<grid, 128, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -213,7 +214,8 @@ int persistent_grid_2c_grad(int op, int precision)
     case OP_ERFC: return grid_for<OP_ERFC>();
     case OP_ERF: return grid_for<OP_ERF>();
     case OP_GAUSS: return grid_for<OP_GAUSS>();
-    default: return grid_for<OP_GCOUL>();
+    case OP_GCOUL: return grid_for<OP_GCOUL>();
+    default: return grid_for<OP_RA2N>();
     }
 }
 

@@ -13,6 +13,7 @@ constexpr int kLmaxAabA = 10;     // largest la + la~ of an (aab) triple
 constexpr int kLmaxR = 10;        // largest l of the scaled solid harmonics table
 constexpr int kKmax = 32;         // largest contraction length
 constexpr int kJmax = 7;          // min(la, lb) + 1 <= 7
+constexpr int kRa2nMax = 5;                // largest n of the (a|r_a^{2n}|b) operator
 constexpr int kNClass = (kLmax2c + 1) * (kLmax2c + 1);
 constexpr int kTile = 32;         // pairs per warp tile
 
@@ -71,6 +72,8 @@ struct Consts {
     double dint[64];                       // (double) n
     double inv_int[192];                   // 1/n (0 for n = 0)
     double dfact[32];                      // (2n-1)!!, (-1)!! = 1
+    double binom[kRa2nMax + 1][kRa2nMax + 1];  // C(n, j)
+    double ra2n_k[kRa2nMax + 1][kRa2nMax + 1]; // 2^{d-m} (2m+1)!! C(m,d) / (2d+1)!!, [m][d], d <= m
 };
 
 void fill_consts(Consts &k);

@@ -52,7 +52,7 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
     const int Kb = sb.nprim, npp = sa.nprim * Kb;
     for (int q = 0; q < npp; ++q) {
         const int ia = q / Kb, ib = q - ia * Kb;
-        radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, g, O);
+        radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, la, g, O);
     }
 
     // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}, shared by z = c, s
@@ -123,7 +123,8 @@ __device__ __forceinline__ void run_tile_fp64(const Args2c &g, int op, const Til
     case OP_ERFC: pair_2c_fp64_dispatch<OP_ERFC>(g, p, J); break;
     case OP_ERF: pair_2c_fp64_dispatch<OP_ERF>(g, p, J); break;
     case OP_GAUSS: pair_2c_fp64_dispatch<OP_GAUSS>(g, p, J); break;
-    default: pair_2c_fp64_dispatch<OP_GCOUL>(g, p, J); break;
+    case OP_GCOUL: pair_2c_fp64_dispatch<OP_GCOUL>(g, p, J); break;
+    default: pair_2c_fp64_dispatch<OP_RA2N>(g, p, J); break;
     }
 }
 
@@ -377,6 +378,7 @@ cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persis
     case OP_ERF: return launch_2c_op<OP_ERF>(a, n, threads, persistent, s);
     case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, threads, persistent, s);
     case OP_GCOUL: return launch_2c_op<OP_GCOUL>(a, n, threads, persistent, s);
+    case OP_RA2N: return launch_2c_op<OP_RA2N>(a, n, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -394,7 +396,8 @@ int persistent_grid_2c(int op, int precision, int threads, int ctas_per_sm)
     case OP_ERFC: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERFC>, threads, 0); break;
     case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, threads, 0); break;
     case OP_GAUSS: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GCOUL>, threads, 0); break;
+    case OP_GCOUL: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GCOUL>, threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_RA2N>, threads, 0); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;

@@ -92,6 +92,15 @@ def reference_2c(shells, pair_a, pair_b, op, omega):
     return ref, _block_max(sc, off, sz)
 
 
+def reference_ra2n(shells, pair_a, pair_b, n):
+    """Oracle blocks (a|r_a^{2n}|b) and the per-element scale S_p (|N c| evaluation)."""
+    import oracle
+    shn, sha = normalised(shells)
+    ref, off, sz = oracle.eval_2c_ra2n(shn, pair_a, pair_b, n, normalize=False)
+    sc, _, _ = oracle.eval_2c_ra2n(sha, pair_a, pair_b, n, normalize=False)
+    return ref, _block_max(sc, off, sz)
+
+
 def reference_3c(shells, t_a, t_atilde, t_b):
     import oracle
     shn, sha = normalised(shells)

@@ -20,7 +20,7 @@ def test_table2_contracted_element_counts():
 
 
 def test_flop_model_monotone_and_positive():
-    for op in range(6):
+    for op in range(7):
         f = counts.pair_flops(np.array([0, 1, 2, 4, 6]), np.array([0, 1, 2, 4, 6]), np.ones(5), np.ones(5), op)
         assert np.all(f > 0) and np.all(np.diff(f) > 0)
         g = counts.pair_flops(np.full(4, 2), np.full(4, 3), np.array([1, 2, 4, 8]), np.array([1, 2, 4, 8]), op)
