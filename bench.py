@@ -477,8 +477,10 @@ def other_configs(args):
     from paper_1701_06588_gb300 import _lib as L
     st = torch.cuda.current_stream().cuda_stream
     ms = _events_ms(lambda: L.shg_eval_3c_aab(b.handle, b.handle, len(ta), d_ta, d_tt, d_tb, 0, 0.0, d_off, out, st), 3)
+    f3 = counts.workload_triple_flops(sh, ta, tt, tb)
     res["c4_aab_20k"] = {"triples": len(ta), "atom_pairs": len(ta) // per, "fp64": {
-        "ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3), "elements": total}}
+        "ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3), "elements": total,
+        "algorithmic_tflops": f3 / (ms * 1e-3) / 1e12}}
     w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
     ga = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
     gb = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
@@ -499,7 +501,8 @@ def other_configs(args):
     entry = {"pairs": len(pa)}
     for opn, op, om in [("coulomb", 1, 0.0), ("erfc", 2, 0.11)]:
         ms = _events_ms(lambda: L.shg_eval_2c_grad(b.handle, len(pa), d_pa, d_pb, op, om, 0, d_off, w, ga, gb, st), 3)
-        entry[opn] = {"ms_per_pass": ms, "pair_gradients_per_s": len(pa) / (ms * 1e-3)}
+        entry[opn] = {"ms_per_pass": ms, "pair_gradients_per_s": len(pa) / (ms * 1e-3),
+                      "algorithmic_tflops": counts.workload_grad_flops(sh, pa, pb, op) / (ms * 1e-3) / 1e12}
     res["c5_grad_500k_l5_k12"] = entry
     b.close()
     return res

@@ -103,3 +103,79 @@ def workload_flops(shells, pair_a, pair_b, op):
 def workload_elements(shells, pair_a, pair_b):
     l = np.asarray(shells["l"]).astype(np.int64)
     return int(np.sum((2 * l[pair_a] + 1) * (2 * l[pair_b] + 1)))
+
+
+def triple_flops(la, lt, lb, ka, kt, kb):
+    """Algorithmic FP64 flops of one contracted (a b a~) triple in the order the
+    (aab) formula is evaluated (Eqs. Pa_aba, sra2ms, devsra2ms, I_jab; Sec. II D),
+    numpy-vectorised.  The Gaunt sum counts 2 nL terms per (m_a, m_a~), an upper
+    estimate of the real Gaunt coefficients that are non-zero."""
+    la, lt, lb = (np.asarray(v, dtype=np.int64) for v in (la, lt, lb))
+    kk = np.asarray(ka, dtype=np.int64) * np.asarray(kt, dtype=np.int64) * np.asarray(kb, dtype=np.int64)
+    out = np.zeros(np.broadcast(la, lt, lb, kk).shape, dtype=np.float64)
+    it = np.nditer([la, lt, lb, kk], flags=["multi_index", "refs_ok"])
+    for a, t, b, k in it:
+        a, t, b, k = int(a), int(t), int(b), int(k)
+        Lmin, Lmax = abs(a - t), a + t
+        nL = (Lmax - Lmin) // 2 + 1
+        p = nL - 1
+        kmaxA = Lmax + b
+        kminA = max(Lmin, b)
+        prim = 20 + p * (p + 1) * (p + 2) // 3 + kmaxA + 3 * p
+        for m in range(p + 1):
+            for kd in range(kminA, kmaxA + 1):
+                prim += 4 * (min(m, kd) + 1) + 1
+        for iL in range(nL):
+            L = Lmin + 2 * iL
+            J = min(L, b) + 1
+            prim += J * (3 * (p - iL + 1) + 2) + 2
+        lmax = max(Lmax, b)
+        nb = 2 * b + 1
+        Jmax = min(Lmax, b) + 1
+        ang = 8 * (lmax + 1) * (lmax + 2) // 2 + nb * Jmax * Jmax
+        for iL in range(nL):
+            L = Lmin + 2 * iL
+            J = min(L, b) + 1
+            ang += J * J + (2 * L + 1) * (2 * J * J + nb * (2 * J * J + 2))
+        ang += (2 * a + 1) * (2 * t + 1) * 2 * nL * nb * 2
+        out[it.multi_index] = k * prim + ang
+    return out
+
+
+def workload_triple_flops(shells, t_a, t_t, t_b):
+    l = np.asarray(shells["l"])
+    k = np.asarray(shells["nprim"])
+    key = np.stack([l[t_a], l[t_t], l[t_b], k[t_a], k[t_t], k[t_b]], axis=1)
+    uniq, cnt = np.unique(key, axis=0, return_counts=True)
+    f = triple_flops(uniq[:, 0], uniq[:, 1], uniq[:, 2], uniq[:, 3], uniq[:, 4], uniq[:, 5])
+    return float(np.sum(f * cnt))
+
+
+def grad_pair_flops(la, lb, ka, kb, op):
+    """Algorithmic FP64 flops of one pair's vector-Jacobian product (Eq. dev_ab,
+    Eqs. cartesian_dev_x/y/z): the radial part with one more derivative order,
+    harmonics and their gradients, W and dW rows, the two contractions with the
+    upstream weights and the three gradient sums."""
+    la = np.asarray(la, dtype=np.int64)
+    lb = np.asarray(lb, dtype=np.int64)
+    kk = np.asarray(ka, dtype=np.int64) * np.asarray(kb, dtype=np.int64)
+    J = np.minimum(la, lb) + 1
+    kmin = np.maximum(la, lb)
+    lmax = np.maximum(la, lb)
+    na, nb = 2 * la + 1, 2 * lb + 1
+    rad = np.zeros(np.broadcast(la, lb, kk).shape, dtype=np.float64)
+    for j in range(1, 8):
+        for km in range(0, 7):
+            m = (J == j) & (kmin == km)
+            if np.any(m):
+                rad[m] = _radial_flops(op, j + 1, km)
+    nco = (lmax + 1) * (lmax + 2) / 2
+    JJ = J * J
+    ang = (3 * J * (J + 1) / 2 + 16 * nco + nb * JJ + na * 16 * JJ + na * nb * (4 * JJ + 3) + nb * 12 * JJ + 9)
+    return kk * rad + ang
+
+
+def workload_grad_flops(shells, pair_a, pair_b, op):
+    l = np.asarray(shells["l"])
+    k = np.asarray(shells["nprim"])
+    return float(np.sum(grad_pair_flops(l[pair_a], l[pair_b], k[pair_a], k[pair_b], op)))

@@ -29,3 +29,13 @@ def test_flop_model_monotone_and_positive():
     a = counts.pair_flops(3, 2, 5, 5, counts.OP_ERFC)
     assert a > counts.pair_flops(3, 2, 5, 5, counts.OP_COULOMB)
     assert a > counts.pair_flops(3, 2, 5, 5, counts.OP_ERF)
+
+
+def test_triple_and_gradient_flop_models():
+    # more primitives or higher l cost more; the gradient costs more than the forward pass
+    f = counts.triple_flops(np.array([0, 1, 2, 3]), np.array([0, 1, 2, 3]), np.array([1, 2, 3, 4]), 2, 2, 2)
+    assert np.all(f > 0) and np.all(np.diff(f) > 0)
+    g = counts.triple_flops(2, 2, 2, np.array([1, 2, 4]), 3, 2)
+    assert np.all(np.diff(g) > 0)
+    for op in range(7):
+        assert counts.grad_pair_flops(3, 2, 4, 4, op) > counts.pair_flops(3, 2, 4, 4, op)
