@@ -481,6 +481,9 @@ def other_configs(args):
     res["c4_aab_20k"] = {"triples": len(ta), "atom_pairs": len(ta) // per, "fp64": {
         "ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3), "elements": total,
         "algorithmic_tflops": f3 / (ms * 1e-3) / 1e12}}
+    ms = _events_ms(lambda: L.shg_eval_3c_aab(b.handle, b.handle, len(ta), d_ta, d_tt, d_tb, 1, 0.0, d_off, out, st), 3)
+    res["c4_aab_20k"]["mixed"] = {"ms_per_pass": ms, "triples_per_s": len(ta) / (ms * 1e-3),
+                                  "form": "radial sums FP64, angular part and Gaunt sum double-float"}
     w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
     ga = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
     gb = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")

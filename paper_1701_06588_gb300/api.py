@@ -184,6 +184,40 @@ class TwoCenterIntegrals(torch.autograd.Function):
         return g.to(ctx.device), None, None, None, None, None
 
 
+class ThreeIndexOverlap(torch.autograd.Function):
+    """Blocks (a b a~) as a differentiable function of the center coordinates.
+
+    forward(centers[n_centers, 3] float64, orb, aux, t_a, t_atilde, t_b): `orb`
+    and `aux` index one common list of centers (atoms), which is set on both;
+    returns the flat block tensor.  backward calls the library's (aab)
+    gradient kernel and scatters the per-triple gradients onto the centers of
+    a (= a~) and b with index_add_.
+    """
+
+    @staticmethod
+    def forward(ctx, centers, orb, aux, t_a, t_atilde, t_b):
+        c = centers.detach().cpu().numpy()
+        orb.set_centers(c)
+        if aux is not orb:
+            aux.set_centers(c)
+        out, off = eval_3c_aab(orb, aux, t_a, t_atilde, t_b)
+        ctx.orb, ctx.aux, ctx.t = orb, aux, (t_a, t_atilde, t_b)
+        ctx.off, ctx.n_centers, ctx.device = off, centers.shape[0], centers.device
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        t_a, t_atilde, t_b = ctx.t
+        ga, gb = eval_3c_aab_grad(ctx.orb, ctx.aux, t_a, t_atilde, t_b, grad_out.to("cuda", torch.float64),
+                                  offsets=ctx.off)
+        ca = torch.from_numpy(ctx.orb.center_of[np.asarray(t_a)].astype(np.int64)).cuda()
+        cb = torch.from_numpy(ctx.aux.center_of[np.asarray(t_b)].astype(np.int64)).cuda()
+        g = torch.zeros((ctx.n_centers, 3), dtype=torch.float64, device="cuda")
+        g.index_add_(0, ca, ga)
+        g.index_add_(0, cb, gb)
+        return g.to(ctx.device), None, None, None, None, None
+
+
 class Graph2c:
     """A CUDA graph replaying one plan for several operators (C ABI
     shg_graph_2c_create / shg_graph_launch)."""

@@ -12,17 +12,28 @@
 //
 // One thread per triple; a warp owns a class-pure tile (la, la~, lb).
 #include "shg_device.cuh"
+#include "shg_mix_angular.cuh"
 
 namespace shg {
 namespace {
 using namespace dev;
+using namespace dfm;
+using namespace mixa;
 
 constexpr int kPmax = 5;          // min(la, la~) <= 5 when la + la~ <= 10
 constexpr int kNL = kPmax + 1;    // number of L_a terms
 constexpr int kKmax3 = kLmaxAabA + kLmax2c;  // highest derivative order, 16
 constexpr int kLR = kLmaxAabA;    // scaled harmonics up to l = 10
 
-__device__ void triple_aab_fp64(const Args3c &g, int p)
+// Geometry of one triple and the L_a range of its product expansion.
+struct TripleGeom {
+    int la, lt, lb, Lmin, Lmax, nL;
+    double vx, vy, vz;
+};
+
+// Radial sums P[iL][j] = P_{L_a}^{(L_a+lb-j)} of one triple in FP64 (also in
+// the mixed form: the sum over i below alternates in sign).
+__device__ __forceinline__ TripleGeom aab_radial(const Args3c &g, int p, double (&P)[kNL][kJmax])
 {
     const ShellRec sa = g.orb_shells[g.t_a[p]];
     const ShellRec st = g.orb_shells[g.t_t[p]];
@@ -39,7 +50,6 @@ __device__ void triple_aab_fp64(const Args3c &g, int p)
     const int kmaxA = Lmax + lb;
     const int kminA = Lmin > lb ? Lmin : lb;
 
-    double P[kNL][kJmax];
     for (int i = 0; i < kNL; ++i)
         for (int j = 0; j < kJmax; ++j) P[i][j] = 0.0;
 
@@ -111,6 +121,15 @@ __device__ void triple_aab_fp64(const Args3c &g, int p)
             wL *= i2ap2;
         }
     }
+    return TripleGeom{la, lt, lb, Lmin, Lmax, nL, vx, vy, vz};
+}
+
+__device__ void triple_aab_fp64(const Args3c &g, int p)
+{
+    double P[kNL][kJmax];
+    const TripleGeom tg = aab_radial(g, p, P);
+    const int la = tg.la, lt = tg.lt, lb = tg.lb, Lmin = tg.Lmin, Lmax = tg.Lmax, nL = tg.nL;
+    const double vx = tg.vx, vy = tg.vy, vz = tg.vz;
 
     // angular part: R^{c/s}_{l,m}(R_a - R_b) up to max(L_a max, lb)
     double Rc[(kLR + 1) * (kLR + 2) / 2], Rs[(kLR + 1) * (kLR + 2) / 2];
@@ -173,6 +192,94 @@ __device__ void triple_aab_fp64(const Args3c &g, int p)
             }
             double *o = out + (ma * nt + mt) * nb;
             for (int mb = 0; mb < nb; ++mb) o[mb] = acc[mb];
+        }
+}
+
+// Mixed form: the radial sums in FP64 (aab_radial), the angular part and the
+// Gaunt sum in double-float on the FP32 pipes.  Per L_a the radial factors
+// are scaled by a power of two 2^e into FP32 range; the block is scaled back
+// by 2^e (in two exact steps) before the Gaunt sum.
+__device__ __forceinline__ df split_d(double v)
+{
+    const float hi = __double2float_rn(v);
+    return df{hi, __double2float_rn(v - (double)hi)};
+}
+
+__device__ void triple_aab_mixed(const Args3c &g, int p)
+{
+    double P[kNL][kJmax];
+    const TripleGeom tg = aab_radial(g, p, P);
+    const int la = tg.la, lt = tg.lt, lb = tg.lb, Lmin = tg.Lmin, Lmax = tg.Lmax, nL = tg.nL;
+
+    df Rc[(kLR + 1) * (kLR + 2) / 2], Rs[(kLR + 1) * (kLR + 2) / 2];
+    scaled_harmonics_mix(split_d(tg.vx), split_d(tg.vy), split_d(tg.vz), Lmax > lb ? Lmax : lb, g.km, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    const int Jmax = (Lmax < lb ? Lmax : lb) + 1;
+    df Wb[2 * kLmax2c + 1][kJmax * kJmax];
+    for (int mb = -lb; mb <= lb; ++mb) w_row_mix_rt(Rc, Rs, lb, mb, Jmax, Wb[mb + lb]);
+
+    df Bst[(1 + 5 + 9 + 13 + 17 + 21) * (2 * kLmax2c + 1)];
+    const double lam0 = 3.5449077018110320545963349666822903 / (g.k3.sqrt_int[2 * la + 1] * g.k3.sqrt_int[2 * lt + 1]);
+    int boff = 0;
+    for (int iL = 0; iL < nL; ++iL) {
+        const int L = Lmin + 2 * iL;
+        const int J = (L < lb ? L : lb) + 1;
+        const double lamK = lam0 * g.k3.sqrt_int[2 * L + 1];
+        double oj[kJmax];
+        double omax = 0.0;
+        for (int j = 0; j < J; ++j) {
+            oj[j] = P[iL][j] * lamK * g.k.pow2[L + lb - j];
+            omax = fmax(omax, fabs(oj[j]));
+        }
+        int ex = 0;
+        if (omax > 0.0) frexp(omax, &ex);
+        ex = ex > 250 ? 250 : (ex < -250 ? -250 : ex);
+        df ge[kJmax * kJmax];
+        for (int j = 0; j < J; ++j) {
+            const df oe = split_d(ldexp(oj[j], -ex));
+            for (int kp = 0; kp <= j; ++kp) {
+                const df v = mul(oe, ldf(g.km.jB[j][kp]));
+                const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+                ge[e0] = v;
+                if (kp) ge[e0 + 1] = v;
+            }
+        }
+        const float s1 = ldexpf(1.0f, ex / 2), s2 = ldexpf(1.0f, ex - ex / 2);
+        for (int M = -L; M <= L; ++M) {
+            df wa[kJmax * kJmax];
+            w_row_mix_rt(Rc, Rs, L, M, J, wa);
+            df Aa = ldf(g.km.A[L][M < 0 ? -M : M]);
+            if (lb & 1) Aa = neg(Aa);
+            for (int e = 0; e < J * J; ++e) wa[e] = mul(wa[e], ge[e]);
+            for (int mb = -lb; mb <= lb; ++mb) {
+                const df *wb = Wb[mb + lb];
+                df sum = mul(wa[0], wb[0]);
+                for (int e = 1; e < J * J; ++e) sum = add(sum, mul(wa[e], wb[e]));
+                const df blk = mul(Aa, mul(ldf(g.km.A[lb][mb < 0 ? -mb : mb]), sum));
+                Bst[boff + (M + L) * nb + (mb + lb)] = scale2(scale2(blk, s1), s2);
+            }
+        }
+        boff += (2 * L + 1) * nb;
+    }
+
+    const int nt = 2 * lt + 1;
+    const int rbase = g.gaunt_base[la * 7 + lt];
+    double *out = g.out + g.out_off[p];
+    for (int ma = 0; ma < 2 * la + 1; ++ma)
+        for (int mt = 0; mt < nt; ++mt) {
+            const int r = rbase + ma * nt + mt;
+            df acc[2 * kLmax2c + 1];
+            for (int mb = 0; mb < nb; ++mb) acc[mb] = df_f(0.0f);
+            for (int q = g.gaunt_row[r]; q < g.gaunt_row[r + 1]; ++q) {
+                const GauntEnt ge = g.gaunt[q];
+                const int iL = (ge.L - Lmin) / 2;
+                const int off_L = iL * (2 * Lmin + 1 + 2 * (iL - 1)) * nb;
+                const df *bl = Bst + off_L + (ge.M + ge.L) * nb;
+                const df gd = split_d(ge.g);
+                for (int mb = 0; mb < nb; ++mb) acc[mb] = add(acc[mb], mul(gd, bl[mb]));
+            }
+            double *o = out + (ma * nt + mt) * nb;
+            for (int mb = 0; mb < nb; ++mb) o[mb] = to_double(acc[mb]);
         }
 }
 
@@ -391,6 +498,20 @@ __global__ void __launch_bounds__(128) k_3c_grad_fp64_persistent(const Args3c g)
     }
 }
 
+__global__ void __launch_bounds__(128) k_3c_mixed_persistent(const Args3c g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        const Tile tl = g.tiles[t];
+        if (lane < tl.count) triple_aab_mixed(g, g.perm[tl.start + lane]);
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(128) k_3c_fp64_persistent(const Args3c g)
 {
     const int lane = threadIdx.x & 31;
@@ -409,9 +530,10 @@ __global__ void __launch_bounds__(128) k_3c_fp64_persistent(const Args3c g)
 
 cudaError_t launch_3c(const Args3c &a, int precision, int grid, cudaStream_t s)
 {
-    (void)precision;
     if (a.grad_a)
         k_3c_grad_fp64_persistent<<<grid, 128, 0, s>>>(a);
+    else if (precision == 1)
+        k_3c_mixed_persistent<<<grid, 128, 0, s>>>(a);
     else
         k_3c_fp64_persistent<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -419,12 +541,13 @@ cudaError_t launch_3c(const Args3c &a, int precision, int grid, cudaStream_t s)
 
 int persistent_grid_3c(int precision)
 {
-    (void)precision;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_grad_fp64_persistent, 128, 0) != cudaSuccess || per < 1)
-        per = 1;
+    cudaError_t e = precision == 1
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_mixed_persistent, 128, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_3c_grad_fp64_persistent, 128, 0);
+    if (e != cudaSuccess || per < 1) per = 1;
     return (sms > 0 ? sms : 1) * per;
 }
 

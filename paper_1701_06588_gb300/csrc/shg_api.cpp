@@ -175,7 +175,7 @@ static inline float2 split2d(double v)
 void fill_consts_mix(ConstsMix &k)
 {
     std::memset(&k, 0, sizeof k);
-    for (int l = 0; l <= kLmax2c; ++l)
+    for (int l = 0; l <= kLmaxR; ++l)
         for (int mu = 0; mu <= l; ++mu) {
             long double v = std::sqrt((long double)(mu == 0 ? 1 : 2) * lfact(l + mu) * lfact(l - mu));
             k.A[l][mu] = split2((mu & 1) ? -v : v);
@@ -185,7 +185,7 @@ void fill_consts_mix(ConstsMix &k)
         for (int i = 2 * j - 1; i > 1; i -= 2) df *= i;
         for (int kp = 0; kp <= j; ++kp) k.jB[j][kp] = split2(df / ((kp == 0 ? 1 : 2) * lfact(j + kp) * lfact(j - kp)));
     }
-    for (int i = 1; i < 64; ++i) k.inv_int[i] = split2(1.0L / i);
+    for (int i = 1; i < 128; ++i) k.inv_int[i] = split2(1.0L / i);
     for (int t = 0; t < 14; ++t) {
         k.inv_fact[t] = split2(1.0L / lfact(t));
         k.inv_fact_f[t] = (float)(1.0L / lfact(t));
@@ -1084,7 +1084,9 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
                           const double *w, double *grad_a, double *grad_b, void *stream)
 {
     if (!orb || !aux) return fail(SHG_EINVAL, "basis is NULL");
-    if (precision != SHG_PREC_FP64) return fail(SHG_EINVAL, "precision %d not available for (aab)", precision);
+    if (precision != SHG_PREC_FP64 && (precision != SHG_PREC_MIXED || grad_a))
+        return fail(SHG_EINVAL, "precision %d not available for the (aab) %s", precision,
+                    grad_a ? "gradient" : "integrals");
     if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_triples %lld out of range", (long long)n);
     if (n == 0) return SHG_OK;
     if (!ta || !tt || !tb || !off || (!out && !grad_a)) return fail(SHG_EINVAL, "NULL device pointer");
@@ -1161,6 +1163,7 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
     a.grad_b = grad_b;
     a.k = consts();
     a.k3 = consts3();
+    a.km = consts_mix();
     e = cudaMemsetAsync(d.counter, 0, sizeof(int), s);
     if (e == cudaSuccess && h[1] > 0) e = launch_3c(a, precision, persistent_grid_3c(precision), s);
     cudaFreeAsync(blk, s);

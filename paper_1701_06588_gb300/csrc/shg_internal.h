@@ -80,9 +80,9 @@ void fill_consts(Consts &k);
 
 // Double-float constants of the mixed-precision kernels.
 struct ConstsMix {
-    float2 A[kLmax2c + 1][kLmax2c + 1];    // A_{l,mu}
+    float2 A[kLmaxR + 1][kLmaxR + 1];      // A_{l,mu} (l <= 10: two-center and (aab) L_a)
     float2 jB[kJmax][kJmax];               // (2j-1)!! B_{j,kappa}
-    float2 inv_int[64];                    // 1/n
+    float2 inv_int[128];                   // 1/n
     float2 inv_fact[14];                   // 1/t!
     float inv_fact_f[14];
     float2 pi32, pi3, two_pi52, sqrt_pi_half, two_pi;
@@ -246,6 +246,7 @@ struct Args3c {
     double *grad_a, *grad_b;
     Consts k;
     Consts3 k3;
+    ConstsMix km;                 // mixed-precision angular part
 };
 
 // Kernel launchers (shg_kernels.cu, shg_3c.cu).

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from paper_1701_06588_gb300 import workloads as W
-from tests.parity import TOL_FP64, assert_parity, reference_3c
+from tests.parity import TOL_FP64, TOL_MIXED, assert_parity, reference_3c
 
 pytestmark = pytest.mark.gpu
 
@@ -17,10 +17,10 @@ def shg():
     return api
 
 
-def _run(api, shells, ta, tt, tb):
+def _run(api, shells, ta, tt, tb, precision="fp64"):
     import torch
     b = api.Basis(shells)
-    out, off = api.eval_3c_aab(b, b, ta, tt, tb)
+    out, off = api.eval_3c_aab(b, b, ta, tt, tb, precision=precision)
     torch.cuda.synchronize()
     res = out.cpu().numpy()
     b.close()
@@ -71,3 +71,38 @@ def test_aab_one_center_and_errors(shg):
         shg.eval_3c_aab(b, b, ta[:1], np.array([other], np.int32), tb[:1])
     assert e.value.code == L.SHG_EINVAL and "same center" in str(e.value)
     b.close()
+
+
+@pytest.mark.parametrize("layout", ["orbital_pairs_on_A", "aux_on_A"])
+def test_aab_mixed_subset(shg, layout):
+    """Mixed form (radial sums FP64, angular part and Gaunt sum in
+    double-float) against the oracle with the mixed bar, both layouts."""
+    sh, ta, tt, tb, per = W.aab_workload(12, seed=3, layout=layout)
+    got = _run(shg, sh, ta, tt, tb, precision="mixed")
+    ref, scale = reference_3c(sh, ta, tt, tb)
+    assert_parity(got, ref, TOL_MIXED, "aab mixed " + layout, scale)
+
+
+def test_aab_mixed_full_size_sampled_and_one_center(shg):
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    sh, ta, tt, tb, per = W.make("c4_aab_20k")
+    b = shg.Basis(sh)
+    out, off = shg.eval_3c_aab(b, b, ta, tt, tb, precision="mixed")
+    torch.cuda.synchronize()
+    l = sh["l"].astype(np.int64)
+    sizes = (2 * l[ta] + 1) * (2 * l[tt] + 1) * (2 * l[tb] + 1)
+    idx = np.sort(np.random.default_rng(78).choice(len(ta), 300, replace=False))
+    res = torch.cat([out[int(off[i]):int(off[i] + sizes[i])] for i in idx]).cpu().numpy()
+    ref, scale = reference_3c(sh, ta[idx], tt[idx], tb[idx])
+    assert_parity(res, ref, TOL_MIXED, "aab mixed full-size sampled", scale)
+    w = torch.ones(int(sizes.sum()), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.ShgError) as e:          # the (aab) gradient is FP64 only
+        shg.eval_3c_aab_grad(b, b, ta[:5], tt[:5], tb[:5], w[:int(sizes[:5].sum())], precision="mixed")
+    assert e.value.code == L.SHG_EINVAL
+    b.close()
+    sh2, ta2, tt2, tb2, _ = W.aab_workload(2, seed=5)
+    sh1 = dict(sh2, centers=np.zeros_like(sh2["centers"]))
+    got = _run(shg, sh1, ta2, tt2, tb2, precision="mixed")
+    ref, scale = reference_3c(sh1, ta2, tt2, tb2)
+    assert_parity(got, ref, TOL_MIXED, "aab mixed R=0", scale)

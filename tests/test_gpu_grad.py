@@ -179,3 +179,29 @@ def test_aab_grad_against_finite_differences_of_gpu_forward(shg):
     err = np.abs(ga - fd)[ok]
     assert np.all(err <= 1e-7 * np.maximum(1.0, np.abs(fd[ok]))), err.max()
     b.close()
+
+
+def test_aab_autograd_function_matches_finite_differences(shg):
+    """ThreeIndexOverlap through torch.autograd: d(sum W (a b a~))/dR of every
+    center against central differences of the GPU forward pass."""
+    import torch
+    sh, ta, tt, tb, per = W.aab_workload(4, seed=21)
+    b = shg.Basis(sh)
+    centers = torch.tensor(sh["centers"], dtype=torch.float64, requires_grad=True)
+    out = shg.ThreeIndexOverlap.apply(centers, b, b, ta, tt, tb)
+    wt = torch.from_numpy(np.random.default_rng(5).uniform(-1, 1, out.numel())).cuda()
+    (out * wt).sum().backward()
+    g = centers.grad.numpy()
+    used = sorted(set(sh["center_of"][ta].tolist()) | set(sh["center_of"][tb].tolist()))
+    h = 1e-5
+    for c_idx in used[:6]:
+        for d in range(3):
+            cp = sh["centers"].copy(); cp[c_idx, d] += h
+            cm = sh["centers"].copy(); cm[c_idx, d] -= h
+            b.set_centers(cp)
+            lp = float((shg.eval_3c_aab(b, b, ta, tt, tb)[0] * wt).sum())
+            b.set_centers(cm)
+            lm = float((shg.eval_3c_aab(b, b, ta, tt, tb)[0] * wt).sum())
+            fd = (lp - lm) / (2 * h)
+            assert abs(g[c_idx, d] - fd) <= 1e-7 * max(1.0, abs(fd)), (c_idx, d, g[c_idx, d], fd)
+    b.close()
