@@ -508,6 +508,34 @@ def other_configs(args):
                       "algorithmic_tflops": counts.workload_grad_flops(sh, pa, pb, op) / (ms * 1e-3) / 1e12}
     res["c5_grad_500k_l5_k12"] = entry
     b.close()
+    # molecular assembly: 300-atom molecule with family basis sets, all shell pairs a <= b
+    from paper_1701_06588_gb300 import molecule
+    coords, el, bs = W.molecule_workload(300, seed=7)
+    mol = molecule.Molecule(coords, el, bs)
+    pa, pb = mol.shell_pairs(True)
+    off, total = mol.basis.pair_offsets(pa, pb)
+    d_pa, d_pb, d_off = (torch.from_numpy(x).cuda() for x in (pa, pb, off))
+    blocks = torch.empty(total, dtype=torch.float64, device="cuda")
+    plan = api.Plan2c(mol.basis, d_pa, d_pb)
+    M = torch.zeros((mol.nao, mol.nao), dtype=torch.float64, device="cuda")
+    ms_eval = _events_ms(lambda: plan.exec("coulomb", d_off, blocks), 5)
+    ms_scat = _events_ms(lambda: L.shg_scatter_2c(mol.basis.handle, len(pa), d_pa, d_pb, d_off, blocks,
+                                                  mol.d_ao_off, mol.nao, 1, M, st), 5)
+    la = mol.shells["l"][pa].astype(np.int64)
+    n_el = (2 * la + 1) * (2 * mol.shells["l"][pb].astype(np.int64) + 1)
+    offdiag = (pa != pb)
+    scat_bytes = float(8 * n_el.sum() + 8 * (n_el * (1 + offdiag)).sum() + 24 * len(pa))
+    Wt = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, (mol.nao, mol.nao))).cuda()
+    Wt = 0.5 * (Wt + Wt.T)
+    ms_mat = _events_ms(lambda: mol.matrix("coulomb"), 3)
+    ms_frc = _events_ms(lambda: mol.forces("coulomb", Wt), 3)
+    res["molecule_300_atoms"] = {
+        "atoms": mol.n_atoms, "shells": len(mol.shells["l"]), "nao": mol.nao, "shell_pairs": len(pa),
+        "coulomb_eval_ms": ms_eval, "scatter_ms": ms_scat,
+        "scatter_gbs": scat_bytes / (ms_scat * 1e-3) / 1e9, "scatter_algorithmic_bytes": scat_bytes,
+        "matrix_ms_incl_planning": ms_mat, "forces_ms_incl_planning": ms_frc}
+    plan.close()
+    mol.close()
     return res
 
 

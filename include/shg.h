@@ -289,6 +289,40 @@ int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, const int32_t
                         const int64_t *d_out_offsets, double *d_out, void *stream);
 
 /*
+ * Molecular assembly (the caller-side use of the blocks; no paper formula).
+ * A basis whose shells carry AO offsets ao_off[s] (device int64[n_shells],
+ * the first row/column of shell s in an n_ao x n_ao matrix, functions of a
+ * shell consecutive in m = -l..l) maps a pair list onto a dense matrix.
+ *
+ * shg_scatter_2c - write every block (layout of shg_eval_2c) into the dense
+ *   row-major matrix d_matrix (leading dimension ld >= n_ao): rows
+ *   ao_off[a].., columns ao_off[b]..; with symmetric != 0 and a != b also
+ *   the transposed block at rows ao_off[b].., columns ao_off[a]...  Entries
+ *   no pair touches are left unchanged; the caller lists each unordered pair
+ *   once (pairs that write the same entries race).  HBM-bound.
+ * shg_gather_2c - the adjoint: d_blocks[p] = M[a rows, b columns], plus the
+ *   transpose of M[b rows, a columns] when symmetric != 0 and a != b.  With a
+ *   symmetric weight matrix W this gives the upstream weights of the
+ *   gradient call for sum_{mu,nu} W_{mu nu} M_{mu nu}.
+ * shg_reduce_centers - d_center_grad[c][i] += sum of d_grad_a[p][i] over the
+ *   pairs whose shell a sits on center c, and the same for d_grad_b with the
+ *   center of b (FP64 atomics: the order of the additions, hence the last
+ *   bits, may differ between runs).
+ * All pointers are device pointers owned by the caller; asynchronous on
+ * `stream`.  SHG_EINVAL for NULL pointers, n_pairs < 0 or ld < 1.  Shell
+ * indices are not checked (they come from a pair list already checked by the
+ * evaluation call).
+ */
+int shg_scatter_2c(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,
+                   const int64_t *d_block_off, const double *d_blocks, const int64_t *d_ao_off, int64_t ld,
+                   int symmetric, double *d_matrix, void *stream);
+int shg_gather_2c(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,
+                  const int64_t *d_block_off, const double *d_matrix, const int64_t *d_ao_off, int64_t ld,
+                  int symmetric, double *d_blocks, void *stream);
+int shg_reduce_centers(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,
+                       const double *d_grad_a, const double *d_grad_b, double *d_center_grad, void *stream);
+
+/*
  * shg_debug_boys - device Boys function F_n(T) = int_0^1 exp(-T t^2) t^{2n} dt
  * (SI Eq. 3) as used by the Coulomb-type radial terms: for every T in
  * d_T[n_T] writes F_n for n = 0..nmax (nmax <= 24) to d_F[i*(nmax+1) + n].

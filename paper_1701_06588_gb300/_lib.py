@@ -47,6 +47,9 @@ SIGNATURES = [
     ("shg_eval_2c_grad", _I, [_P, _L, _P, _P, _I, _D, _I, _P, _P, _P, _P, _P]),
     ("shg_eval_3c_aab_grad", _I, [_P, _P, _L, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
     ("shg_eval_2c_noalloc", _I, [_P, _L, _P, _P, _I, _D, _I, _P, _P, _P]),
+    ("shg_scatter_2c", _I, [_P, _L, _P, _P, _P, _P, _P, _L, _I, _P, _P]),
+    ("shg_gather_2c", _I, [_P, _L, _P, _P, _P, _P, _P, _L, _I, _P, _P]),
+    ("shg_reduce_centers", _I, [_P, _L, _P, _P, _P, _P, _P, _P]),
     ("shg_debug_boys", _I, [_L, _P, _I, _P, _P]),
     ("shg_measure_alu_peak", _I, [_I, _I, ctypes.POINTER(_D), _P]),
     ("shg_last_error", ctypes.c_char_p, []),
@@ -193,6 +196,21 @@ def shg_eval_3c_aab_grad(orb, aux, n, d_a, d_atilde, d_b, precision, d_w_offsets
 def shg_eval_2c_noalloc(basis, n_pairs, d_pair_a, d_pair_b, op, omega, precision, d_out_offsets, d_out, stream):
     return check(load().shg_eval_2c_noalloc(basis, n_pairs, _ptr(d_pair_a), _ptr(d_pair_b), op, omega, precision,
                                             _ptr(d_out_offsets), _ptr(d_out), stream))
+
+
+def shg_scatter_2c(basis, n, d_pa, d_pb, d_block_off, d_blocks, d_ao_off, ld, symmetric, d_matrix, stream):
+    return check(load().shg_scatter_2c(basis, n, _ptr(d_pa), _ptr(d_pb), _ptr(d_block_off), _ptr(d_blocks),
+                                       _ptr(d_ao_off), ld, int(symmetric), _ptr(d_matrix), stream))
+
+
+def shg_gather_2c(basis, n, d_pa, d_pb, d_block_off, d_matrix, d_ao_off, ld, symmetric, d_blocks, stream):
+    return check(load().shg_gather_2c(basis, n, _ptr(d_pa), _ptr(d_pb), _ptr(d_block_off), _ptr(d_matrix),
+                                      _ptr(d_ao_off), ld, int(symmetric), _ptr(d_blocks), stream))
+
+
+def shg_reduce_centers(basis, n, d_pa, d_pb, d_grad_a, d_grad_b, d_center_grad, stream):
+    return check(load().shg_reduce_centers(basis, n, _ptr(d_pa), _ptr(d_pb), _ptr(d_grad_a), _ptr(d_grad_b),
+                                           _ptr(d_center_grad), stream))
 
 
 def shg_debug_boys(n, d_T, nmax, d_F, stream):

@@ -1230,6 +1230,45 @@ int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t
     return eval_3c_common(orb, aux, n, ta, tt, tb, precision, w_off, nullptr, w, grad_a, grad_b, stream);
 }
 
+int shg_scatter_2c(const shg_basis_t *b, int64_t n, const int32_t *pa, const int32_t *pb, const int64_t *boff,
+                   const double *blocks, const int64_t *ao, int64_t ld, int symmetric, double *M, void *stream)
+{
+    g_err.clear();
+    if (!b || n < 0 || ld < 1) return fail(SHG_EINVAL, "bad argument");
+    if (n == 0) return SHG_OK;
+    if (!pa || !pb || !boff || !blocks || !ao || !M) return fail(SHG_EINVAL, "NULL device pointer");
+    int r = current_device_matches(b->d.device);
+    if (r) return r;
+    SHG_CUDA(launch_scatter_2c(b->d.shells, n, pa, pb, boff, blocks, ao, ld, symmetric, M, (cudaStream_t)stream));
+    return SHG_OK;
+}
+
+int shg_gather_2c(const shg_basis_t *b, int64_t n, const int32_t *pa, const int32_t *pb, const int64_t *boff,
+                  const double *M, const int64_t *ao, int64_t ld, int symmetric, double *blocks, void *stream)
+{
+    g_err.clear();
+    if (!b || n < 0 || ld < 1) return fail(SHG_EINVAL, "bad argument");
+    if (n == 0) return SHG_OK;
+    if (!pa || !pb || !boff || !blocks || !ao || !M) return fail(SHG_EINVAL, "NULL device pointer");
+    int r = current_device_matches(b->d.device);
+    if (r) return r;
+    SHG_CUDA(launch_gather_2c(b->d.shells, n, pa, pb, boff, M, ao, ld, symmetric, blocks, (cudaStream_t)stream));
+    return SHG_OK;
+}
+
+int shg_reduce_centers(const shg_basis_t *b, int64_t n, const int32_t *pa, const int32_t *pb, const double *ga,
+                       const double *gb, double *out, void *stream)
+{
+    g_err.clear();
+    if (!b || n < 0) return fail(SHG_EINVAL, "bad argument");
+    if (n == 0) return SHG_OK;
+    if (!pa || !pb || !ga || !gb || !out) return fail(SHG_EINVAL, "NULL device pointer");
+    int r = current_device_matches(b->d.device);
+    if (r) return r;
+    SHG_CUDA(launch_reduce_centers(b->d.shells, n, pa, pb, ga, gb, out, (cudaStream_t)stream));
+    return SHG_OK;
+}
+
 int shg_debug_boys(int64_t n, const double *T, int nmax, double *F, void *stream)
 {
     g_err.clear();

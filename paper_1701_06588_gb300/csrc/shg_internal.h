@@ -263,6 +263,14 @@ cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_
                       cudaStream_t s, int threads = 128);
 int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
 cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s);
+cudaError_t launch_scatter_2c(const ShellRec *shells, int64_t n, const int32_t *pa, const int32_t *pb,
+                              const int64_t *boff, const double *blocks, const int64_t *ao, int64_t ld, int sym,
+                              double *M, cudaStream_t s);
+cudaError_t launch_gather_2c(const ShellRec *shells, int64_t n, const int32_t *pa, const int32_t *pb,
+                             const int64_t *boff, const double *M, const int64_t *ao, int64_t ld, int sym,
+                             double *blocks, cudaStream_t s);
+cudaError_t launch_reduce_centers(const ShellRec *shells, int64_t n, const int32_t *pa, const int32_t *pb,
+                                  const double *ga, const double *gb, double *out, cudaStream_t s);
 cudaError_t launch_debug_boys(int64_t n, const double *T, int nmax, double *F, const DeviceTables &t,
                               cudaStream_t s);
 cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, double *sink, cudaStream_t s);

@@ -142,6 +142,28 @@ def aab_workload(n_atom_pairs, seed, n_clusters=21, n_atoms=32, box=12.0, dmin=1
     return shells, t_a, t_t, t_b, per_pair
 
 
+def molecule_workload(n_atoms, seed, box=None, dmin=1.8, exp_range=(0.05, 60.0), k_family=7):
+    """A random molecule with family basis sets (MOLOPT-like structure: all
+    shells of an element share one exponent set of k_family primitives).
+
+    Two element kinds alternate: a light one with shells (s, s, p) and a
+    heavy one with (s, s, p, p, d); exponents log-uniform in exp_range per
+    element, contraction coefficients uniform in [-1, 1] per shell.  Atoms are
+    placed by rejection sampling with minimum distance dmin in a cube of side
+    `box` (default: sized for ~0.1 atoms per bohr^3).  Returns
+    (coords[n_atoms, 3], elements[n_atoms], basis_sets)."""
+    rng = np.random.default_rng(seed)
+    if box is None:
+        box = (n_atoms / 0.1) ** (1.0 / 3.0)
+    coords = _cluster(rng, n_atoms, box, dmin)
+    elements = ["X" if i % 3 == 0 else "H" for i in range(n_atoms)]
+    basis_sets = {}
+    for el, ls in (("H", (0, 0, 1)), ("X", (0, 0, 1, 1, 2))):
+        e = np.sort(_log_uniform(rng, exp_range[0], exp_range[1], k_family))[::-1].copy()
+        basis_sets[el] = [(l, e, rng.uniform(-1.0, 1.0, size=k_family)) for l in ls]
+    return coords, elements, basis_sets
+
+
 def subset_pairs(shells, pair_a, pair_b, idx):
     """Pairs idx of a per-pair-geometry workload (both shells copied)."""
     idx = np.asarray(idx)
