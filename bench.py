@@ -519,6 +519,10 @@ def other_configs(args):
     plan = api.Plan2c(mol.basis, d_pa, d_pb)
     M = torch.zeros((mol.nao, mol.nao), dtype=torch.float64, device="cuda")
     ms_eval = _events_ms(lambda: plan.exec("coulomb", d_off, blocks), 5)
+    fplan = api.FamilyPlan(mol.basis, d_pa, d_pb)
+    ms_fam = _events_ms(lambda: fplan.exec("coulomb", d_off, blocks), 5)
+    n_groups = fplan.n_groups
+    fplan.close()
     ms_scat = _events_ms(lambda: L.shg_scatter_2c(mol.basis.handle, len(pa), d_pa, d_pb, d_off, blocks,
                                                   mol.d_ao_off, mol.nao, 1, M, st), 5)
     la = mol.shells["l"][pa].astype(np.int64)
@@ -531,7 +535,8 @@ def other_configs(args):
     ms_frc = _events_ms(lambda: mol.forces("coulomb", Wt), 3)
     res["molecule_300_atoms"] = {
         "atoms": mol.n_atoms, "shells": len(mol.shells["l"]), "nao": mol.nao, "shell_pairs": len(pa),
-        "coulomb_eval_ms": ms_eval, "scatter_ms": ms_scat,
+        "coulomb_eval_ms": ms_eval, "coulomb_eval_family_path_ms": ms_fam, "family_pair_groups": n_groups,
+        "scatter_ms": ms_scat,
         "scatter_gbs": scat_bytes / (ms_scat * 1e-3) / 1e9, "scatter_algorithmic_bytes": scat_bytes,
         "matrix_ms_incl_planning": ms_mat, "forces_ms_incl_planning": ms_frc}
     plan.close()

@@ -78,6 +78,7 @@ enum shg_schedule {
 
 typedef struct shg_basis shg_basis_t;
 typedef struct shg_plan shg_plan_t;
+typedef struct shg_family_plan shg_family_plan_t;
 
 /*
  * shg_basis_create - upload a shell set to the current device.
@@ -287,6 +288,35 @@ int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t
 int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a,
                         const int32_t *d_pair_b, int op, double omega, int precision,
                         const int64_t *d_out_offsets, double *d_out, void *stream);
+
+/*
+ * Family path (the structure of the bases the paper measures, Sec. III):
+ * when the shells of an element share one exponent set, the radial terms
+ * (0_a|O|0_b)^{(k)} of Table S1 depend only on the primitive pair and R_ab,
+ * so for all shell pairs of one pair of families they are computed once per
+ * primitive pair and contracted per shell pair with its weights
+ * N c (2 alpha)^{-l} (Eq. O_rab2_deriv); the angular part is the same
+ * class-tiled kernel as shg_eval_2c.  Families are found at
+ * shg_basis_create: shells on one center whose exponent lists are bitwise
+ * identical.
+ *
+ * shg_family_plan_create - group a device pair list (as shg_plan_2c_create;
+ *   copied to the host once, synchronously) by family pair.  Pairs whose two
+ *   families have K_a * K_b > 100 go to the regular path inside the plan.
+ * shg_family_plan_exec - blocks of every pair at d_out + d_out_offsets[p],
+ *   FP64, for op = OVERLAP, COULOMB, ERFC, ERF, GAUSS, GAUSS_COULOMB (not
+ *   RA2N: its radial term depends on la); equal to shg_eval_2c up to the
+ *   order of the contraction sums.  Asynchronous on `stream`.
+ * shg_family_plan_counts - total pairs (return value), pairs on the family
+ *   path and number of family-pair groups.
+ * Errors as shg_plan_2c_create / shg_plan_2c_exec.
+ */
+int shg_family_plan_create(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a,
+                           const int32_t *d_pair_b, void *stream, shg_family_plan_t **out);
+int shg_family_plan_exec(shg_family_plan_t *plan, int op, double omega, const int64_t *d_out_offsets,
+                         double *d_out, void *stream);
+int64_t shg_family_plan_counts(const shg_family_plan_t *plan, int64_t *n_family_pairs, int64_t *n_groups);
+void shg_family_plan_destroy(shg_family_plan_t *plan);
 
 /*
  * Molecular assembly (the caller-side use of the blocks; no paper formula).

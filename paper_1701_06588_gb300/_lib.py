@@ -39,6 +39,10 @@ SIGNATURES = [
     ("shg_plan_2c_exec", _I, [_P, _I, _D, _D, _I, _P, _P, _P]),
     ("shg_plan_launches", _I, [_P]),
     ("shg_plan_destroy", None, [_P]),
+    ("shg_family_plan_create", _I, [_P, _L, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("shg_family_plan_exec", _I, [_P, _I, _D, _P, _P, _P]),
+    ("shg_family_plan_counts", _L, [_P, ctypes.POINTER(_L), ctypes.POINTER(_L)]),
+    ("shg_family_plan_destroy", None, [_P]),
     ("shg_plan_2c_set_launch", _I, [_P, _I, _I]),
     ("shg_graph_2c_create", _I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
     ("shg_graph_launch", _I, [_P, _P]),
@@ -143,6 +147,26 @@ def shg_plan_2c_create(basis, n_pairs, d_pair_a, d_pair_b, schedule, stream):
 def shg_plan_2c_exec(plan, op, omega, screen_thresh, precision, d_out_offsets, d_out, stream):
     return check(load().shg_plan_2c_exec(plan, op, omega, screen_thresh, precision, _ptr(d_out_offsets),
                                          _ptr(d_out), stream))
+
+
+def shg_family_plan_create(basis, n_pairs, d_pair_a, d_pair_b, stream):
+    h = _P()
+    check(load().shg_family_plan_create(basis, n_pairs, _ptr(d_pair_a), _ptr(d_pair_b), stream, ctypes.byref(h)))
+    return h.value
+
+
+def shg_family_plan_exec(plan, op, omega, d_out_offsets, d_out, stream):
+    return check(load().shg_family_plan_exec(plan, op, omega, _ptr(d_out_offsets), _ptr(d_out), stream))
+
+
+def shg_family_plan_counts(plan):
+    nf, ng = _L(), _L()
+    n = load().shg_family_plan_counts(plan, ctypes.byref(nf), ctypes.byref(ng))
+    return int(n), int(nf.value), int(ng.value)
+
+
+def shg_family_plan_destroy(plan):
+    load().shg_family_plan_destroy(plan)
 
 
 def shg_plan_launches(plan):

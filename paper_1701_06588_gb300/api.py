@@ -119,6 +119,35 @@ class Plan2c:
             pass
 
 
+class FamilyPlan:
+    """Pair list grouped by family pair (shells on one center sharing one
+    exponent set): radial terms once per primitive pair of each family pair,
+    contracted per shell pair, then the class-tiled angular kernel.  FP64;
+    reusable for any operator but (a|r_a^{2n}|b) and any geometry."""
+
+    def __init__(self, basis, pair_a, pair_b, stream=None):
+        self.basis = basis
+        self.pair_a = _dev_i32(pair_a)
+        self.pair_b = _dev_i32(pair_b)
+        self.n = int(self.pair_a.numel())
+        self.handle = L.shg_family_plan_create(basis.handle, self.n, self.pair_a, self.pair_b, _stream(stream))
+        _, self.n_family_pairs, self.n_groups = L.shg_family_plan_counts(self.handle)
+
+    def exec(self, op, out_offsets, out, omega=0.0, stream=None):
+        L.shg_family_plan_exec(self.handle, _op(op), float(omega), out_offsets, out, _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.shg_family_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def eval_2c(basis, pair_a, pair_b, op, omega=0.0, precision="fp64", screen_thresh=0.0, stream=None):
     """All blocks (a|O|b) of a pair list as one flat float64 CUDA tensor plus
     the int64 offsets (numpy) of each block."""

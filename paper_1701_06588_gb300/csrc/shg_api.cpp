@@ -4,6 +4,8 @@
 #include "shg_internal.h"
 
 #include <algorithm>
+#include <string>
+#include <unordered_map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -659,6 +661,23 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         sh[s] = ShellRec{L, K, (int)off, center_of_shell[s]};
     }
     if (bad_shell >= 0) return fail(SHG_EINVAL, "shell %d: contracted function has zero norm", bad_shell);
+    // families: shells on one center whose exponent lists are bitwise identical
+    std::vector<int32_t> fam(n_shells), fam_prim, fam_k;
+    {
+        std::unordered_map<std::string, int> ids;
+        std::string key;
+        for (int s = 0; s < n_shells; ++s) {
+            key.assign(reinterpret_cast<const char *>(&center_of_shell[s]), sizeof(int32_t));
+            key.append(reinterpret_cast<const char *>(exps + first[s]), sizeof(double) * (size_t)nprim[s]);
+            auto it = ids.find(key);
+            if (it == ids.end()) {
+                it = ids.emplace(key, (int)fam_prim.size()).first;
+                fam_prim.push_back((int32_t)first[s]);
+                fam_k.push_back(nprim[s]);
+            }
+            fam[s] = it->second;
+        }
+    }
     std::vector<ScreenRec> scr(n_shells);
     for (int s = 0; s < n_shells; ++s) {
         double amin = exps[first[s]], sabs = 0;
@@ -700,6 +719,13 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
     std::memcpy(d.h_l, l, sizeof(int32_t) * n_shells);
     std::memcpy(d.h_nprim, nprim, sizeof(int32_t) * n_shells);
     std::memcpy(d.h_center, center_of_shell, sizeof(int32_t) * n_shells);
+    d.n_fams = (int)fam_prim.size();
+    d.h_fam = new int32_t[n_shells];
+    d.h_fam_prim = new int32_t[d.n_fams];
+    d.h_fam_k = new int32_t[d.n_fams];
+    std::memcpy(d.h_fam, fam.data(), sizeof(int32_t) * n_shells);
+    std::memcpy(d.h_fam_prim, fam_prim.data(), sizeof(int32_t) * d.n_fams);
+    std::memcpy(d.h_fam_k, fam_k.data(), sizeof(int32_t) * d.n_fams);
     if (cudaMalloc(&d.shells, sizeof(ShellRec) * n_shells) != cudaSuccess ||
         cudaMalloc(&d.prims, sizeof(PrimRec) * n_prims) != cudaSuccess ||
         cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess ||
@@ -780,6 +806,9 @@ void shg_basis_destroy(shg_basis_t *b)
     delete[] b->d.h_l;
     delete[] b->d.h_nprim;
     delete[] b->d.h_center;
+    delete[] b->d.h_fam;
+    delete[] b->d.h_fam_prim;
+    delete[] b->d.h_fam_k;
     delete b;
 }
 
@@ -978,6 +1007,9 @@ void shg_plan_destroy(shg_plan_t *p)
 }
 
 
+static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const int64_t *off, double *out,
+                     const double *o_pre, cudaStream_t s);
+
 int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int precision, const int64_t *off,
                      double *out, void *stream)
 {
@@ -1029,6 +1061,17 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         }
         return SHG_OK;
     }
+    return exec_fp64(p, op, omega, screen, off, out, nullptr, s);
+}
+
+// FP64 execution of a plan; o_pre != null runs the angular part on
+// precomputed contracted radial terms (op = OP_PRE, family path).
+static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const int64_t *off, double *out,
+                     const double *o_pre, cudaStream_t s)
+{
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    const int precision = SHG_PREC_FP64;
     Args2c a;
     a.shells = p->d.basis->shells;
     a.prims = p->d.basis->prims;
@@ -1044,6 +1087,7 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
     a.screen = p->d.basis->screen;
     a.boys = t->boys;
     a.boys_e = t->boys_e;
+    a.o_pre = o_pre;
     a.k = consts();
     if (p->d.schedule == SHG_SCHED_PERSISTENT) {
         SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
@@ -1194,8 +1238,7 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
     if (r) return r;
     const DeviceTables *t = device_tables();
     cudaStream_t s = (cudaStream_t)stream;
-    Args2c a;
-    std::memset(&a, 0, sizeof a);
+    Args2c a{};
     a.shells = basis->d.shells;
     a.prims = basis->d.prims;
     a.centers = basis->d.centers;
@@ -1228,6 +1271,183 @@ int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t
     g_err.clear();
     if (n > 0 && (!w || !w_off || !grad_a)) return fail(SHG_EINVAL, "NULL device pointer");
     return eval_3c_common(orb, aux, n, ta, tt, tb, precision, w_off, nullptr, w, grad_a, grad_b, stream);
+}
+
+// ------------------------------------------------------------------------- //
+// Family plans                                                               //
+// ------------------------------------------------------------------------- //
+void shg_family_plan_destroy(shg_family_plan_t *fp)
+{
+    if (!fp) return;
+    if (fp->plan_fam) shg_plan_destroy(fp->plan_fam);
+    if (fp->plan_rest) shg_plan_destroy(fp->plan_rest);
+    cudaFree(fp->block);
+    delete fp;
+}
+
+int shg_family_plan_create(const shg_basis_t *basis, int64_t n, const int32_t *d_pa, const int32_t *d_pb, void *stream,
+                           shg_family_plan_t **out)
+{
+    g_err.clear();
+    if (!basis || !out || n < 0 || (n > 0 && (!d_pa || !d_pb))) return fail(SHG_EINVAL, "bad argument");
+    if (n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_pairs %lld out of range", (long long)n);
+    *out = nullptr;
+    int r = current_device_matches(basis->d.device);
+    if (r) return r;
+    const BasisDev &bd = basis->d;
+    std::vector<int32_t> pa(n), pb(n);
+    if (n > 0) {
+        SHG_CUDA(cudaMemcpy(pa.data(), d_pa, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        SHG_CUDA(cudaMemcpy(pb.data(), d_pb, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (pa[i] < 0 || pa[i] >= bd.n_shells || pb[i] < 0 || pb[i] >= bd.n_shells)
+            return fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", bd.n_shells - 1);
+    // family subset, grouped by (family of a, family of b)
+    std::vector<std::pair<int64_t, int32_t>> keyed;
+    std::vector<int32_t> rest;
+    keyed.reserve(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int fa = bd.h_fam[pa[i]], fb = bd.h_fam[pb[i]];
+        if ((int64_t)bd.h_fam_k[fa] * bd.h_fam_k[fb] <= kFamPP)
+            keyed.emplace_back((int64_t)fa * bd.n_fams + fb, (int32_t)i);
+        else
+            rest.push_back((int32_t)i);
+    }
+    std::stable_sort(keyed.begin(), keyed.end(), [](const std::pair<int64_t, int32_t> &x,
+                                                    const std::pair<int64_t, int32_t> &y) { return x.first < y.first; });
+    const int64_t nf = (int64_t)keyed.size(), nr = (int64_t)rest.size();
+    std::vector<int32_t> idx_f(nf), pa_f(nf), pb_f(nf), pa_r(nr), pb_r(nr);
+    std::vector<FamGroup> groups;
+    for (int64_t i = 0; i < nf; ++i) {
+        const int32_t o = keyed[i].second;
+        idx_f[i] = o;
+        pa_f[i] = pa[o];
+        pb_f[i] = pb[o];
+        const int la = bd.h_l[pa[o]], lb = bd.h_l[pb[o]];
+        if (i == 0 || keyed[i].first != keyed[i - 1].first) {
+            const int fa = bd.h_fam[pa[o]], fb = bd.h_fam[pb[o]];
+            groups.push_back(FamGroup{bd.h_fam_prim[fa], bd.h_fam_k[fa], bd.h_fam_prim[fb], bd.h_fam_k[fb], (int)i, 0,
+                                      std::max(la, lb), la + lb, bd.h_center[pa[o]], bd.h_center[pb[o]], 0, 0});
+        }
+        FamGroup &g = groups.back();
+        g.count += 1;
+        g.kmin = std::min(g.kmin, std::max(la, lb));
+        g.kmax = std::max(g.kmax, la + lb);
+    }
+    for (int64_t i = 0; i < nr; ++i) {
+        pa_r[i] = pa[rest[i]];
+        pb_r[i] = pb[rest[i]];
+    }
+    shg_family_plan_t *fp = new (std::nothrow) shg_family_plan_t;
+    if (!fp) return fail(SHG_ENOMEM, "host allocation failed");
+    fp->basis = &bd;
+    fp->n = n;
+    fp->n_fam = nf;
+    fp->n_rest = nr;
+    fp->n_groups = (int)groups.size();
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_i32f = al(sizeof(int32_t) * (size_t)std::max<int64_t>(nf, 1));
+    const size_t b_i32r = al(sizeof(int32_t) * (size_t)std::max<int64_t>(nr, 1));
+    const size_t b_grp = al(sizeof(FamGroup) * (size_t)std::max(fp->n_groups, 1));
+    const size_t b_o = al(sizeof(double) * kJmax * (size_t)std::max<int64_t>(nf, 1));
+    const size_t b_offf = al(sizeof(int64_t) * (size_t)std::max<int64_t>(nf, 1));
+    const size_t b_offr = al(sizeof(int64_t) * (size_t)std::max<int64_t>(nr, 1));
+    const size_t total = 3 * b_i32f + 3 * b_i32r + b_grp + 256 + b_o + b_offf + b_offr;
+    if (cudaMalloc(&fp->block, total) != cudaSuccess) {
+        delete fp;
+        return fail(SHG_ENOMEM, "family plan: cudaMalloc of %zu bytes failed", total);
+    }
+    char *c = (char *)fp->block;
+    fp->d_idx_fam = (int32_t *)c; c += b_i32f;
+    fp->d_pa_fam = (int32_t *)c; c += b_i32f;
+    fp->d_pb_fam = (int32_t *)c; c += b_i32f;
+    fp->d_idx_rest = (int32_t *)c; c += b_i32r;
+    fp->d_pa_rest = (int32_t *)c; c += b_i32r;
+    fp->d_pb_rest = (int32_t *)c; c += b_i32r;
+    fp->d_groups = (FamGroup *)c; c += b_grp;
+    fp->d_counter = (int *)c; c += 256;
+    fp->d_o = (double *)c; c += b_o;
+    fp->d_off_fam = (int64_t *)c; c += b_offf;
+    fp->d_off_rest = (int64_t *)c;
+    bool ok = true;
+    if (nf > 0)
+        ok = cudaMemcpy(fp->d_idx_fam, idx_f.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(fp->d_pa_fam, pa_f.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(fp->d_pb_fam, pb_f.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(fp->d_groups, groups.data(), sizeof(FamGroup) * groups.size(), cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+    if (ok && nr > 0)
+        ok = cudaMemcpy(fp->d_idx_rest, rest.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(fp->d_pa_rest, pa_r.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(fp->d_pb_rest, pb_r.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        shg_family_plan_destroy(fp);
+        return fail(SHG_ECUDA, "family plan: upload failed");
+    }
+    if (nf > 0 && (r = shg_plan_2c_create(basis, nf, fp->d_pa_fam, fp->d_pb_fam, SHG_SCHED_PERSISTENT, stream,
+                                          &fp->plan_fam)) != SHG_OK) {
+        shg_family_plan_destroy(fp);
+        return r;
+    }
+    if (nr > 0 && (r = shg_plan_2c_create(basis, nr, fp->d_pa_rest, fp->d_pb_rest, SHG_SCHED_PERSISTENT, stream,
+                                          &fp->plan_rest)) != SHG_OK) {
+        shg_family_plan_destroy(fp);
+        return r;
+    }
+    *out = fp;
+    return SHG_OK;
+}
+
+int64_t shg_family_plan_counts(const shg_family_plan_t *fp, int64_t *n_family_pairs, int64_t *n_groups)
+{
+    if (!fp) return -1;
+    if (n_family_pairs) *n_family_pairs = fp->n_fam;
+    if (n_groups) *n_groups = fp->n_groups;
+    return fp->n;
+}
+
+int shg_family_plan_exec(shg_family_plan_t *fp, int op, double omega, const int64_t *off, double *out, void *stream)
+{
+    g_err.clear();
+    if (!fp) return fail(SHG_EINVAL, "plan is NULL");
+    int r = check_op(op, omega, SHG_PREC_FP64);
+    if (r) return r;
+    if (op == SHG_OP_RA2N) return fail(SHG_EINVAL, "SHG_OP_RA2N has no family path (its radial term depends on la)");
+    if (fp->n == 0) return SHG_OK;
+    if (!off || !out) return fail(SHG_EINVAL, "NULL output");
+    r = current_device_matches(fp->basis->device);
+    if (r) return r;
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (fp->n_fam > 0) {
+        SHG_CUDA(launch_gather_i64(off, fp->d_idx_fam, fp->n_fam, fp->d_off_fam, s));
+        ArgsFam a;
+        a.shells = fp->basis->shells;
+        a.prims = fp->basis->prims;
+        a.centers = fp->basis->centers;
+        a.pair_a = fp->d_pa_fam;
+        a.pair_b = fp->d_pb_fam;
+        a.groups = fp->d_groups;
+        a.n_groups = fp->n_groups;
+        a.counter = fp->d_counter;
+        a.o_pre = fp->d_o;
+        a.omega = omega;
+        a.boys = t->boys;
+        a.boys_e = t->boys_e;
+        a.k = consts();
+        SHG_CUDA(cudaMemsetAsync(fp->d_counter, 0, sizeof(int), s));
+        SHG_CUDA(launch_family_radial(a, op, s));
+        r = exec_fp64(fp->plan_fam, 7 /* OP_PRE */, omega, 0.0, fp->d_off_fam, out, fp->d_o, s);
+        if (r) return r;
+    }
+    if (fp->n_rest > 0) {
+        SHG_CUDA(launch_gather_i64(off, fp->d_idx_rest, fp->n_rest, fp->d_off_rest, s));
+        r = shg_plan_2c_exec(fp->plan_rest, op, omega, 0.0, SHG_PREC_FP64, fp->d_off_rest, out, stream);
+        if (r) return r;
+    }
+    return SHG_OK;
 }
 
 int shg_scatter_2c(const shg_basis_t *b, int64_t n, const int32_t *pa, const int32_t *pb, const int64_t *boff,

@@ -13,7 +13,8 @@ constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
 constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
 constexpr double kPi = 3.141592653589793238462643383279502884;        // pi
 
-enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5, OP_RA2N = 6 };
+enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP_GCOUL = 5, OP_RA2N = 6,
+       OP_PRE = 7 /* contracted radial terms precomputed (family path) */ };
 
 // ------------------------------------------------------------------------- //
 // Boys function F_k(T), k = kmax-J+1 .. kmax, into F[j] = F_{kmax-j}.       //

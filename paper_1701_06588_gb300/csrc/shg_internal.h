@@ -149,6 +149,10 @@ struct BasisDev {
     int *stage_bad = nullptr;
     // host copies used for validation and offsets
     int32_t *h_l = nullptr, *h_nprim = nullptr, *h_center = nullptr;
+    // families: shells on one center with bitwise-identical exponent lists
+    int32_t *h_fam = nullptr;                           // family of each shell
+    int32_t *h_fam_prim = nullptr, *h_fam_k = nullptr;  // per family: first primitive record, K
+    int n_fams = 0;
 };
 
 // A warp's unit of work: up to kTile consecutive entries of the sorted list,
@@ -203,6 +207,33 @@ struct Args2c {
     const long long *w_off;
     const double *w;
     double *grad_a, *grad_b;
+    // family path: contracted radial terms O[j] of pair p precomputed at
+    // o_pre[p * kJmax + j] (read by the OP_PRE instantiation only)
+    const double *o_pre = nullptr;
+    Consts k;
+};
+
+// Family basis sets: a group of shell pairs whose shells a share one
+// exponent set (family) on one center, and likewise for b.
+constexpr int kFamPP = 100;                // largest K_a * K_b of the family path
+constexpr int kFamOrd = 2 * kLmax2c + 1;   // derivative orders 0..la+lb
+struct FamGroup {
+    int fa_prim, fa_k, fb_prim, fb_k;   // first primitive record and K of each family
+    int start, count;                   // range of the group in the grouped pair order
+    int kmin, kmax;                     // derivative orders the group's pairs need
+    int ca, cb, pad0, pad1;             // centers
+};
+struct ArgsFam {
+    const ShellRec *shells;
+    const PrimRec *prims;
+    const Vec4 *centers;
+    const int32_t *pair_a, *pair_b;     // the family subset of the pair list, in group order
+    const FamGroup *groups;
+    int n_groups;
+    int *counter;
+    double *o_pre;                      // [n_subset][kJmax]
+    double omega;
+    const double *boys, *boys_e;
     Consts k;
 };
 
@@ -263,6 +294,8 @@ cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_
                       cudaStream_t s, int threads = 128);
 int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
 cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s);
+cudaError_t launch_family_radial(const ArgsFam &a, int op, cudaStream_t s);
+cudaError_t launch_gather_i64(const int64_t *src, const int32_t *idx, int64_t n, int64_t *dst, cudaStream_t s);
 cudaError_t launch_scatter_2c(const ShellRec *shells, int64_t n, const int32_t *pa, const int32_t *pb,
                               const int64_t *boff, const double *blocks, const int64_t *ao, int64_t ld, int sym,
                               double *M, cudaStream_t s);
@@ -285,5 +318,21 @@ struct shg_basis {
 struct shg_plan {
     shg::PlanDev d;
     int launches = 0;
+};
+
+// Family plan: the pairs whose shells both belong to families with
+// K_a * K_b <= kFamPP, grouped by family pair, plus the rest (regular path).
+struct shg_family_plan {
+    const shg::BasisDev *basis = nullptr;
+    int64_t n = 0, n_fam = 0, n_rest = 0;
+    int n_groups = 0;
+    int32_t *d_idx_fam = nullptr, *d_idx_rest = nullptr;   // original pair indices
+    int32_t *d_pa_fam = nullptr, *d_pb_fam = nullptr, *d_pa_rest = nullptr, *d_pb_rest = nullptr;
+    shg::FamGroup *d_groups = nullptr;
+    int *d_counter = nullptr;
+    double *d_o = nullptr;                                  // [n_fam][kJmax]
+    int64_t *d_off_fam = nullptr, *d_off_rest = nullptr;    // offsets gathered at execution
+    shg_plan *plan_fam = nullptr, *plan_rest = nullptr;
+    void *block = nullptr;
 };
 

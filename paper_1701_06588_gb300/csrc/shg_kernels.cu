@@ -47,12 +47,17 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
     double O[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) O[j] = 0.0;
-    // one flat loop over the Ka*Kb primitive pairs: tiles hold pairs of equal
-    // Ka*Kb, so every lane of a warp runs the same trip count
-    const int Kb = sb.nprim, npp = sa.nprim * Kb;
-    for (int q = 0; q < npp; ++q) {
-        const int ia = q / Kb, ib = q - ia * Kb;
-        radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, la, g, O);
+    if (OP == OP_PRE) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) O[j] = g.o_pre[(int64_t)p * kJmax + j];
+    } else {
+        // one flat loop over the Ka*Kb primitive pairs: tiles hold pairs of equal
+        // Ka*Kb, so every lane of a warp runs the same trip count
+        const int Kb = sb.nprim, npp = sa.nprim * Kb;
+        for (int q = 0; q < npp; ++q) {
+            const int ia = q / Kb, ib = q - ia * Kb;
+            radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, la, g, O);
+        }
     }
 
     // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}, shared by z = c, s
@@ -124,7 +129,8 @@ __device__ __forceinline__ void run_tile_fp64(const Args2c &g, int op, const Til
     case OP_ERF: pair_2c_fp64_dispatch<OP_ERF>(g, p, J); break;
     case OP_GAUSS: pair_2c_fp64_dispatch<OP_GAUSS>(g, p, J); break;
     case OP_GCOUL: pair_2c_fp64_dispatch<OP_GCOUL>(g, p, J); break;
-    default: pair_2c_fp64_dispatch<OP_RA2N>(g, p, J); break;
+    case OP_RA2N: pair_2c_fp64_dispatch<OP_RA2N>(g, p, J); break;
+    default: pair_2c_fp64_dispatch<OP_PRE>(g, p, J); break;
     }
 }
 
@@ -379,6 +385,7 @@ cudaError_t launch_2c(const Args2c &a, int op, int precision, int n, bool persis
     case OP_GAUSS: return launch_2c_op<OP_GAUSS>(a, n, threads, persistent, s);
     case OP_GCOUL: return launch_2c_op<OP_GCOUL>(a, n, threads, persistent, s);
     case OP_RA2N: return launch_2c_op<OP_RA2N>(a, n, threads, persistent, s);
+    case OP_PRE: return launch_2c_op<OP_PRE>(a, n, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -397,7 +404,8 @@ int persistent_grid_2c(int op, int precision, int threads, int ctas_per_sm)
     case OP_ERF: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_ERF>, threads, 0); break;
     case OP_GAUSS: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GAUSS>, threads, 0); break;
     case OP_GCOUL: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_GCOUL>, threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_RA2N>, threads, 0); break;
+    case OP_RA2N: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_RA2N>, threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_persistent<OP_PRE>, threads, 0); break;
     }
     if (e != cudaSuccess || per < 1) per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;

@@ -79,10 +79,11 @@ class Molecule:
     def _pairs(self, op, pairs):
         return self.shell_pairs(_is_symmetric(op)) if pairs is None else pairs
 
-    def matrix(self, op, omega=0.0, precision="fp64", pairs=None, out=None, stream=None):
+    def matrix(self, op, omega=0.0, precision="fp64", pairs=None, out=None, stream=None, path="pairs"):
         """Dense (nao, nao) float64 CUDA matrix of the operator; with a pair
         subset only the entries of those pairs are written (out defaults to
-        zeros)."""
+        zeros).  path="family" evaluates the blocks on the family path
+        (FP64; radial terms shared by the shell pairs of each atom pair)."""
         pa, pb = self._pairs(op, pairs)
         if out is None:
             out = torch.zeros((self.nao, self.nao), dtype=torch.float64, device="cuda")
@@ -92,8 +93,14 @@ class Molecule:
         d_pa, d_pb = torch.from_numpy(pa).cuda(), torch.from_numpy(pb).cuda()
         d_off = torch.from_numpy(off).cuda()
         blocks = torch.empty(total, dtype=torch.float64, device="cuda")
-        plan = api.Plan2c(self.basis, d_pa, d_pb, stream=stream)
-        plan.exec(op, d_off, blocks, omega=omega, precision=precision, stream=stream)
+        if path == "family":
+            if precision != "fp64":
+                raise ValueError("the family path is FP64")
+            plan = api.FamilyPlan(self.basis, d_pa, d_pb, stream=stream)
+            plan.exec(op, d_off, blocks, omega=omega, stream=stream)
+        else:
+            plan = api.Plan2c(self.basis, d_pa, d_pb, stream=stream)
+            plan.exec(op, d_off, blocks, omega=omega, precision=precision, stream=stream)
         L.shg_scatter_2c(self.basis.handle, len(pa), d_pa, d_pb, d_off, blocks, self.d_ao_off, self.nao,
                          _is_symmetric(op), out, api._stream(stream))
         plan.close()

@@ -50,6 +50,8 @@ def test_matrix_against_oracle(mol_mod, opname, op, omega):
     Sref = _dense(scale, mol.shells, mol.ao_off, mol.nao, pa, pb, True)
     assert_parity(M.ravel(), Mref.ravel(), TOL_FP64, "molecule " + opname, Sref.ravel())
     assert np.array_equal(M, M.T)
+    Mf = mol.matrix(opname, omega=omega, path="family").cpu().numpy()
+    assert_parity(Mf.ravel(), Mref.ravel(), TOL_FP64, "molecule family " + opname, Sref.ravel())
     if opname == "overlap":                      # normalised functions
         np.testing.assert_allclose(np.diag(M), 1.0, rtol=0, atol=1e-12)
     mol.close()
