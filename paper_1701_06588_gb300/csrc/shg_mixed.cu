@@ -234,8 +234,21 @@ __device__ __noinline__ void assemble_mix(const ArgsMix &g, int p, int la, int l
         if (lb & 1) Aa = neg(Aa);
         for (int mb = -lb; mb <= lb; ++mb) {
             const df *ub = Ub[mb + lb];
-            df s = mul(ua[0], ub[0]);
-            for (int e = 1; e < JJ; ++e) s = add(s, mul(ua[e], ub[e]));
+            // compensated dot product (Ogita, Rump and Oishi, "Dot2"): exact
+            // products of the high parts by FMA, their running sum by TwoSum,
+            // every rounding error and the cross terms summed in one FP32
+            // accumulator; as accurate as double-float accumulation
+            float sh = 0.0f, sl = 0.0f;
+            for (int e = 0; e < JJ; ++e) {
+                const float p = ua[e].hi * ub[e].hi;
+                float ep = fmaf(ua[e].hi, ub[e].hi, -p);
+                ep = fmaf(ua[e].hi, ub[e].lo, ep);
+                ep = fmaf(ua[e].lo, ub[e].hi, ep);
+                const df t = two_sum(sh, p);
+                sh = t.hi;
+                sl += t.lo + ep;
+            }
+            const df s = fast_two_sum(sh, sl);
             out[(ma + la) * nb + (mb + lb)] = to_double(mul(Aa, mul(ldf(g.km.A[lb][mb < 0 ? -mb : mb]), s)));
         }
     }
