@@ -224,8 +224,13 @@ void shg_plan_destroy(shg_plan_t *plan);
  *   aux            basis of b (may be the same handle as orb)
  *   d_a, d_atilde  device int32[n_triples] indices into orb
  *   d_b            device int32[n_triples] indices into aux
- *   precision      enum shg_precision
- *   screen_thresh  as in shg_eval_2c (overlap bound)
+ *   precision      enum shg_precision (FP64, or MIXED: radial sums FP64,
+ *                  angular part and Gaunt sum double-float)
+ *   screen_thresh  0 disables screening; > 0: a triple whose bound on every
+ *                  element magnitude is below it writes zeros.  The bound
+ *                  multiplies the single-shell bounds of a and a~ used by
+ *                  shg_eval_2c (one Gaussian of exponent (amin_a+amin_a~)/2
+ *                  on A) and takes the two-center overlap bound with b
  *   d_out_offsets  device int64[n_triples]; d_out device doubles
  * Limits: la + la~ <= SHG_LMAX_AAB_A, lb <= SHG_LMAX_2C.  Returns SHG_EINVAL
  * when a and a~ of a triple are not on the same center.

@@ -159,13 +159,13 @@ def eval_2c(basis, pair_a, pair_b, op, omega=0.0, precision="fp64", screen_thres
     return out[:total], off
 
 
-def eval_3c_aab(orb, aux, t_a, t_atilde, t_b, precision="fp64", stream=None):
+def eval_3c_aab(orb, aux, t_a, t_atilde, t_b, precision="fp64", screen_thresh=0.0, stream=None):
     """Three-index overlaps (a b a~) of a triple list (a, a~ in `orb` on one
     center, b in `aux`) as one flat float64 CUDA tensor plus block offsets."""
     off, total = orb.triple_offsets(aux, t_a, t_atilde, t_b)
     out = torch.empty(max(total, 1), dtype=torch.float64, device="cuda")
     L.shg_eval_3c_aab(orb.handle, aux.handle, len(off), _dev_i32(t_a), _dev_i32(t_atilde), _dev_i32(t_b),
-                      _prec(precision), 0.0, _dev_i64(off), out, _stream(stream))
+                      _prec(precision), float(screen_thresh), _dev_i64(off), out, _stream(stream))
     return out[:total], off
 
 

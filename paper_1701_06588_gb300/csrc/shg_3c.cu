@@ -124,8 +124,29 @@ __device__ __forceinline__ TripleGeom aab_radial(const Args3c &g, int p, double 
     return TripleGeom{la, lt, lb, Lmin, Lmax, nL, vx, vy, vz};
 }
 
+// Screening of one triple: |phi_a phi_a~| <= 2 sabs_a sabs_a~ lfac_a lfac_a~
+// exp(-(amin_a + amin_a~) r^2 / 2) (the single-shell bound of the two-center
+// screen, multiplied), so the two-center overlap bound of the combined record
+// and b bounds every element of the block.  Writes zeros and returns true
+// when that bound is below the threshold.
+__device__ __forceinline__ bool aab_screened(const Args3c &g, int p)
+{
+    if (!(g.screen_thresh > 0.0)) return false;
+    const ScreenRec ra = g.orb_screen[g.t_a[p]], rt = g.orb_screen[g.t_t[p]], rb = g.aux_screen[g.t_b[p]];
+    const ScreenRec at{ra.amin + rt.amin, ra.sabs * rt.sabs, 1.4142135623730950488 * ra.lfac * rt.lfac, 0.0};
+    const ShellRec sa = g.orb_shells[g.t_a[p]], st = g.orb_shells[g.t_t[p]], sb = g.aux_shells[g.t_b[p]];
+    const Vec4 A = g.orb_centers[sa.center], B = g.aux_centers[sb.center];
+    const double vx = A.x - B.x, vy = A.y - B.y, vz = A.z - B.z;
+    if (screen_bound(at, rb, vx * vx + vy * vy + vz * vz, OP_OVERLAP, 0.0) >= g.screen_thresh) return false;
+    double *o = g.out + g.out_off[p];
+    const int n = (2 * sa.l + 1) * (2 * st.l + 1) * (2 * sb.l + 1);
+    for (int i = 0; i < n; ++i) o[i] = 0.0;
+    return true;
+}
+
 __device__ void triple_aab_fp64(const Args3c &g, int p)
 {
+    if (aab_screened(g, p)) return;
     double P[kNL][kJmax];
     const TripleGeom tg = aab_radial(g, p, P);
     const int la = tg.la, lt = tg.lt, lb = tg.lb, Lmin = tg.Lmin, Lmax = tg.Lmax, nL = tg.nL;
@@ -207,6 +228,7 @@ __device__ __forceinline__ df split_d(double v)
 
 __device__ void triple_aab_mixed(const Args3c &g, int p)
 {
+    if (aab_screened(g, p)) return;
     double P[kNL][kJmax];
     const TripleGeom tg = aab_radial(g, p, P);
     const int la = tg.la, lt = tg.lt, lb = tg.lb, Lmin = tg.Lmin, Lmax = tg.Lmax, nL = tg.nL;

@@ -1125,7 +1125,7 @@ int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const in
 
 static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, const int32_t *ta,
                           const int32_t *tt, const int32_t *tb, int precision, const int64_t *off, double *out,
-                          const double *w, double *grad_a, double *grad_b, void *stream)
+                          const double *w, double *grad_a, double *grad_b, void *stream, double screen = 0.0)
 {
     if (!orb || !aux) return fail(SHG_EINVAL, "basis is NULL");
     if (precision != SHG_PREC_FP64 && (precision != SHG_PREC_MIXED || grad_a))
@@ -1205,6 +1205,9 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
     a.w = w;
     a.grad_a = grad_a;
     a.grad_b = grad_b;
+    a.screen_thresh = grad_a ? 0.0 : screen;
+    a.orb_screen = orb->d.screen;
+    a.aux_screen = aux->d.screen;
     a.k = consts();
     a.k3 = consts3();
     a.km = consts_mix();
@@ -1219,9 +1222,9 @@ int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n, c
                     const int32_t *tb, int precision, double screen, const int64_t *off, double *out, void *stream)
 {
     g_err.clear();
-    if (!(screen == 0.0)) return fail(SHG_EINVAL, "screening threshold must be 0 in this build");
+    if (!(screen >= 0.0) || !std::isfinite(screen)) return fail(SHG_EINVAL, "screening threshold must be >= 0");
     if (n > 0 && !out) return fail(SHG_EINVAL, "NULL output");
-    return eval_3c_common(orb, aux, n, ta, tt, tb, precision, off, out, nullptr, nullptr, nullptr, stream);
+    return eval_3c_common(orb, aux, n, ta, tt, tb, precision, off, out, nullptr, nullptr, nullptr, stream, screen);
 }
 
 int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,

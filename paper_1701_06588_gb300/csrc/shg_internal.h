@@ -275,6 +275,9 @@ struct Args3c {
     const long long *w_off;
     const double *w;
     double *grad_a, *grad_b;
+    // screening: > 0 writes zeros for a triple whose bound on every element is below it
+    double screen_thresh;
+    const ScreenRec *orb_screen, *aux_screen;
     Consts k;
     Consts3 k3;
     ConstsMix km;                 // mixed-precision angular part

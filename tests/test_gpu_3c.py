@@ -106,3 +106,33 @@ def test_aab_mixed_full_size_sampled_and_one_center(shg):
     got = _run(shg, sh1, ta2, tt2, tb2, precision="mixed")
     ref, scale = reference_3c(sh1, ta2, tt2, tb2)
     assert_parity(got, ref, TOL_MIXED, "aab mixed R=0", scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_aab_screening_bound(shg, precision):
+    """screen_thresh > 0 writes zeros only for triples whose bound is below
+    it: every element stays within the threshold of the unscreened result,
+    some blocks are screened at 1e-6, and the others are unchanged."""
+    import torch
+    sh, ta, tt, tb, per = W.aab_workload(60, seed=3)
+    b = shg.Basis(sh)
+    exact, off = shg.eval_3c_aab(b, b, ta, tt, tb, precision=precision)
+    e = exact.cpu().numpy()
+    l = sh["l"].astype(np.int64)
+    sizes = (2 * l[ta] + 1) * (2 * l[tt] + 1) * (2 * l[tb] + 1)
+    for thr in (1e-10, 1e-6):
+        scr, _ = shg.eval_3c_aab(b, b, ta, tt, tb, precision=precision, screen_thresh=thr)
+        torch.cuda.synchronize()
+        s_ = scr.cpu().numpy()
+        assert np.all(np.isfinite(s_))
+        assert np.max(np.abs(s_ - e)) <= thr, (precision, thr)
+        zero = np.array([not np.any(s_[o:o + z]) and np.any(e[o:o + z]) for o, z in zip(off, sizes)])
+        kept = ~np.array([not np.any(s_[o:o + z]) for o, z in zip(off, sizes)])
+        for o, z, k in zip(off, sizes, kept):
+            if k:
+                assert np.array_equal(s_[o:o + z], e[o:o + z])
+        if thr == 1e-6:
+            assert zero.mean() > 0.01, zero.mean()
+    with pytest.raises(Exception):
+        shg.eval_3c_aab(b, b, ta, tt, tb, precision=precision, screen_thresh=-1.0)
+    b.close()
