@@ -51,8 +51,9 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
 #pragma unroll
         for (int j = 0; j < J; ++j) O[j] = g.o_pre[(int64_t)p * kJmax + j];
     } else {
-        // one flat loop over the Ka*Kb primitive pairs: tiles hold pairs of equal
-        // Ka*Kb, so every lane of a warp runs the same trip count
+        // one flat loop over the Ka*Kb primitive pairs: a tile holds one class's
+        // pairs in descending Ka*Kb, so the lanes' trip counts differ only where
+        // a tile straddles two Ka*Kb values
         const int Kb = sb.nprim, npp = sa.nprim * Kb;
         for (int q = 0; q < npp; ++q) {
             const int ia = q / Kb, ib = q - ia * Kb;
@@ -207,38 +208,57 @@ __global__ void k_classify_3c(int64_t n, const int32_t *__restrict__ ta, const i
 }
 
 // single block: exclusive scans of hist and of ceil(hist/32); tile_start[n_bins] = total
-__global__ void k_scan_bins(int n_bins, const int *__restrict__ hist, int *__restrict__ bin_start,
+// Exclusive prefix sums over the bins in rank order: pair offsets bin_start
+// (and the scatter cursors) and tile offsets tile_start.  Tiles are cut per
+// chunk of `chunk` consecutive ranks: chunk = 1 cuts every bin on its own;
+// the two-center planner passes the bins of one class (a contiguous chunk in
+// both rank orders), so each class ends in one partial tile instead of each
+// of its (class, Ka*Kb) bins.  One block of 1024 threads.
+__global__ void k_scan_bins(int n_bins, int chunk, const int *__restrict__ hist, int *__restrict__ bin_start,
                             int *__restrict__ cursor, int *__restrict__ tile_start)
 {
     __shared__ long long s_cnt[1024], s_til[1024];
     const int per = (n_bins + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per;
-    long long c = 0, t = 0;
-    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
-        c += hist[i];
-        t += (hist[i] + kTile - 1) / kTile;
-    }
+    long long c = 0;
+    for (int i = b0; i < b0 + per && i < n_bins; ++i) c += hist[i];
     s_cnt[threadIdx.x] = c;
-    s_til[threadIdx.x] = t;
     __syncthreads();
     for (int off = 1; off < blockDim.x; off <<= 1) {
-        long long vc = 0, vt = 0;
-        if (threadIdx.x >= off) {
-            vc = s_cnt[threadIdx.x - off];
-            vt = s_til[threadIdx.x - off];
-        }
+        const long long vc = threadIdx.x >= off ? s_cnt[threadIdx.x - off] : 0;
         __syncthreads();
         s_cnt[threadIdx.x] += vc;
-        s_til[threadIdx.x] += vt;
         __syncthreads();
     }
-    long long rc = s_cnt[threadIdx.x] - c, rt = s_til[threadIdx.x] - t;
+    long long rc = s_cnt[threadIdx.x] - c;
+    const long long total = s_cnt[blockDim.x - 1];
     for (int i = b0; i < b0 + per && i < n_bins; ++i) {
         bin_start[i] = (int)rc;
         cursor[i] = (int)rc;
-        tile_start[i] = (int)rt;
         rc += hist[i];
-        rt += (hist[i] + kTile - 1) / kTile;
+    }
+    __syncthreads();
+    // tiles of each rank: its own bin (chunk = 1) or, at the first rank of a chunk, the chunk's pairs
+    auto tiles_of = [&](int i) -> long long {
+        if (chunk == 1) return (hist[i] + kTile - 1) / kTile;
+        if (i % chunk) return 0;
+        const long long end = i + chunk < n_bins ? bin_start[i + chunk] : total;
+        return (end - bin_start[i] + kTile - 1) / kTile;
+    };
+    long long t = 0;
+    for (int i = b0; i < b0 + per && i < n_bins; ++i) t += tiles_of(i);
+    s_til[threadIdx.x] = t;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        const long long vt = threadIdx.x >= off ? s_til[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_til[threadIdx.x] += vt;
+        __syncthreads();
+    }
+    long long rt = s_til[threadIdx.x] - t;
+    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
+        tile_start[i] = (int)rt;
+        rt += tiles_of(i);
     }
     if (threadIdx.x == blockDim.x - 1) tile_start[n_bins] = (int)s_til[blockDim.x - 1];
 }
@@ -251,20 +271,21 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ key, int *__restric
     }
 }
 
-__global__ void k_make_tiles(int n_bins, int bins_per_class, const int *__restrict__ hist,
+__global__ void k_make_tiles(int n_bins, int bins_per_class, int chunk, int n_pairs, const int *__restrict__ hist,
                              const int *__restrict__ bin_start, const int *__restrict__ tile_start,
                              const int *__restrict__ rank_to_bin, Tile *__restrict__ tiles)
 {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_bins; r += gridDim.x * blockDim.x) {
-        const int c = hist[r];
+        if (r % chunk) continue;
+        const int c = chunk == 1 ? hist[r] : (r + chunk < n_bins ? bin_start[r + chunk] : n_pairs) - bin_start[r];
         if (!c) continue;
-        const int bin = rank_to_bin[r];
+        const int cls = rank_to_bin[r] / bins_per_class;
         const int nt = (c + kTile - 1) / kTile;
         for (int t = 0; t < nt; ++t) {
             Tile tl;
             tl.start = bin_start[r] + t * kTile;
             tl.count = (c - t * kTile) < kTile ? (c - t * kTile) : kTile;
-            tl.cls = bin / bins_per_class;
+            tl.cls = cls;
             tl.pad = 0;
             tiles[tile_start[r] + t] = tl;
         }
@@ -353,10 +374,14 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
                                                  plan.basis->n_shells, plan.aux->shells, plan.aux->n_shells,
                                                  d_bin_rank, key, hist, d_err);
     }
-    k_scan_bins<<<1, 1024, 0, s>>>(n_bins, hist, bin_start, cursor, tile_start);
+    // two-center ranks are class-major (each class a chunk of kKbins2c ranks): one tiling per class;
+    // three-index ranks follow the bin cost, so their tiles stay per bin
+    const int bpc = plan.kind == 2 ? kKbins2c : kKbins3c;
+    const int chunk = plan.kind == 2 ? kKbins2c : 1;
+    k_scan_bins<<<1, 1024, 0, s>>>(n_bins, chunk, hist, bin_start, cursor, tile_start);
     if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, key, cursor, plan.perm);
-    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, plan.kind == 2 ? kKbins2c : kKbins3c, hist,
-                                                       bin_start, tile_start, d_bin_rank + n_bins, plan.tiles);
+    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, bpc, chunk, (int)n, hist, bin_start, tile_start,
+                                                       d_bin_rank + n_bins, plan.tiles);
     return cudaGetLastError();
 }
 
