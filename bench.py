@@ -49,6 +49,9 @@ def parse():
                    help="precision of the headline path (the other forms are reported beside it)")
     p.add_argument("--no-extras", action="store_true", help="time only the headline path (profiling)")
     p.add_argument("--no-tune", action="store_true", help="default launch shape instead of the autotuner (profiling)")
+    p.add_argument("--profile-case", default=None, choices=["aab", "aab_grad", "grad", "family"],
+                   help="run one kernel of another workload at size --case-n (profiling captures only)")
+    p.add_argument("--case-n", type=int, default=None)
     p.add_argument("--configs", action="store_true",
                    help="also time the other workloads (2k, 2M high-l, (aab) 20k atom pairs, gradients) and add "
                         "them under other_configs")
@@ -443,6 +446,59 @@ def _events_ms(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def profile_case(args):
+    """One warm and one timed call of a single kernel at a moderate size, for
+    ncu captures of the kernels outside the headline step:
+      aab       (a b a~) FP64, n atom pairs of the 20,000-atom-pair recipe (150 triples each)
+      aab_grad  its vector-Jacobian product
+      grad      two-center Coulomb VJP, n pairs of the 500k-pair gradient recipe
+      family    family-path Coulomb blocks of an n-atom molecule
+    Prints one JSON line with the CUDA-event time of the timed call."""
+    import numpy as np
+    import torch
+    from paper_1701_06588_gb300 import _lib as L, api, build, molecule, workloads as W
+    build.build()
+    st = torch.cuda.current_stream().cuda_stream
+    case, n = args.profile_case, args.case_n
+    if case in ("aab", "aab_grad"):
+        sh, ta, tt, tb, _ = W.make("c4_aab_20k", n=n or 2000)
+        b = api.Basis(sh)
+        off, total = b.triple_offsets(b, ta, tt, tb)
+        d_off = torch.from_numpy(off).cuda()
+        d = [torch.from_numpy(x).cuda() for x in (ta, tt, tb)]
+        if case == "aab":
+            out = torch.empty(total, dtype=torch.float64, device="cuda")
+            fn = lambda: L.shg_eval_3c_aab(b.handle, b.handle, len(ta), *d, 0, 0.0, d_off, out, st)
+        else:
+            w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+            ga = torch.empty((len(ta), 3), dtype=torch.float64, device="cuda")
+            gb = torch.empty_like(ga)
+            fn = lambda: L.shg_eval_3c_aab_grad(b.handle, b.handle, len(ta), *d, 0, d_off, w, ga, gb, st)
+        units = len(ta)
+    elif case == "grad":
+        sh, pa, pb = W.make("c5_grad_500k_l5_k12", n=n or 100_000)
+        b = api.Basis(sh)
+        off, total = b.pair_offsets(pa, pb)
+        d_off, d_pa, d_pb = (torch.from_numpy(x).cuda() for x in (off, pa, pb))
+        w = torch.empty(total, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+        ga = torch.empty((len(pa), 3), dtype=torch.float64, device="cuda")
+        gb = torch.empty_like(ga)
+        fn = lambda: L.shg_eval_2c_grad(b.handle, len(pa), d_pa, d_pb, 1, 0.0, 0, d_off, w, ga, gb, st)
+        units = len(pa)
+    else:
+        coords, el, bs = W.molecule_workload(n or 300, seed=7)
+        mol = molecule.Molecule(coords, el, bs)
+        pa, pb = mol.shell_pairs(True)
+        off, total = mol.basis.pair_offsets(pa, pb)
+        d_off = torch.from_numpy(off).cuda()
+        out = torch.empty(total, dtype=torch.float64, device="cuda")
+        fp = api.FamilyPlan(mol.basis, pa, pb)
+        fn = lambda: fp.exec("coulomb", d_off, out)
+        units = len(pa)
+    ms = _events_ms(fn, 1)
+    print(json.dumps({"profile_case": case, "units": units, "ms": ms}))
+
+
 def other_configs(args):
     """Throughput of the other synthetic workloads (CUDA events, inputs resident)."""
     import numpy as np
@@ -553,6 +609,9 @@ def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

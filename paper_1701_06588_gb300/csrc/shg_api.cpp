@@ -451,14 +451,19 @@ const DeviceTables *device_tables_impl(int **ranks, int **rank3 = nullptr)
         // three-index bins ordered by estimated cost
         int *d_r3 = nullptr;
         if (ok) {
+            // class-major like the two-center ranks (each class one contiguous chunk
+            // of kKbins3c ranks, tiled as a whole): classes by decreasing cost of
+            // their heaviest bin, Ka*Ka~*Kb descending inside a class
             std::vector<int> order(kNBins3), rank3(2 * kNBins3);
-            std::vector<double> cost(kNBins3);
-            for (int b = 0; b < kNBins3; ++b) {
-                order[b] = b;
-                const int cls = b / kKbins3c, kk = b % kKbins3c + 1;
-                cost[b] = class_cost3(cls / 49, (cls / 7) % 7, cls % 7, kk);
-            }
-            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+            std::vector<double> ccost(kNClass3);
+            for (int cls = 0; cls < kNClass3; ++cls)
+                ccost[cls] = class_cost3(cls / 49, (cls / 7) % 7, cls % 7, kKbins3c);
+            for (int b = 0; b < kNBins3; ++b) order[b] = b;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                const int cx = x / kKbins3c, cy = y / kKbins3c;
+                if (cx != cy) return ccost[cx] > ccost[cy] || (ccost[cx] == ccost[cy] && cx < cy);
+                return (x % kKbins3c) > (y % kKbins3c);
+            });
             for (int r = 0; r < kNBins3; ++r) {
                 rank3[order[r]] = r;
                 rank3[kNBins3 + r] = order[r];

@@ -164,7 +164,7 @@ struct Tile {
 constexpr int kKbins2c = kKmax * kKmax;      // two-center bins per class: Ka*Kb - 1
 constexpr int kNBins2c = kNClass * kKbins2c;
 constexpr int kNClass3 = 7 * 7 * 7;          // (la, la~, lb) classes
-constexpr int kKbins3c = 64;                 // three-index bins per class: min(Ka*Ka~*Kb, 64) - 1
+constexpr int kKbins3c = 512;                // three-index bins per class: min(Ka*Ka~*Kb, 512) - 1
 
 
 struct PlanDev {

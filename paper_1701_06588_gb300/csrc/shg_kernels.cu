@@ -207,13 +207,12 @@ __global__ void k_classify_3c(int64_t n, const int32_t *__restrict__ ta, const i
     }
 }
 
-// single block: exclusive scans of hist and of ceil(hist/32); tile_start[n_bins] = total
 // Exclusive prefix sums over the bins in rank order: pair offsets bin_start
 // (and the scatter cursors) and tile offsets tile_start.  Tiles are cut per
 // chunk of `chunk` consecutive ranks: chunk = 1 cuts every bin on its own;
-// the two-center planner passes the bins of one class (a contiguous chunk in
-// both rank orders), so each class ends in one partial tile instead of each
-// of its (class, Ka*Kb) bins.  One block of 1024 threads.
+// the planners pass the bins of one class (a contiguous chunk in their
+// class-major rank orders), so each class ends in one partial tile instead of
+// each of its (class, K-product) bins.  One block of 1024 threads.
 __global__ void k_scan_bins(int n_bins, int chunk, const int *__restrict__ hist, int *__restrict__ bin_start,
                             int *__restrict__ cursor, int *__restrict__ tile_start)
 {
@@ -374,10 +373,9 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
                                                  plan.basis->n_shells, plan.aux->shells, plan.aux->n_shells,
                                                  d_bin_rank, key, hist, d_err);
     }
-    // two-center ranks are class-major (each class a chunk of kKbins2c ranks): one tiling per class;
-    // three-index ranks follow the bin cost, so their tiles stay per bin
+    // both rank orders are class-major (each class a chunk of bins_per_class ranks): one tiling per class
     const int bpc = plan.kind == 2 ? kKbins2c : kKbins3c;
-    const int chunk = plan.kind == 2 ? kKbins2c : 1;
+    const int chunk = bpc;
     k_scan_bins<<<1, 1024, 0, s>>>(n_bins, chunk, hist, bin_start, cursor, tile_start);
     if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, key, cursor, plan.perm);
     k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, bpc, chunk, (int)n, hist, bin_start, tile_start,
