@@ -287,3 +287,31 @@ def test_screening_bound(shg, precision):
                 assert zero_blocks.mean() > 0.01, (opname, zero_blocks.mean())
     plan.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_c3_sampled(shg, precision):
+    """The full 2,000,000-pair workload (l up to 6, K up to 20) in one
+    persistent launch per operator; 300 sampled pairs against the oracle."""
+    import torch
+    from tests.parity import TOL_MIXED
+    sh, pa, pb = W.make("c3_2m_l6_k20")
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    plan = shg.Plan2c(b, pa, pb, schedule="persistent")
+    d_off = torch.from_numpy(off).cuda()
+    idx = np.sort(np.random.default_rng(321).choice(len(pa), 300, replace=False))
+    sub, spa, spb = W.subset_pairs(sh, pa, pb, idx)
+    l = sh["l"]
+    for opname, op, omega in [("coulomb", 1, 0.0), ("erfc", 2, 0.11)]:
+        out = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+        plan.exec(opname, d_off, out, omega=omega, precision=precision)
+        torch.cuda.synchronize()
+        got = torch.cat([out[int(off[p]):int(off[p]) + (2 * int(l[pa[p]]) + 1) * (2 * int(l[pb[p]]) + 1)]
+                         for p in idx]).cpu().numpy()
+        ref, scale = reference_2c(sub, spa, spb, op, omega)
+        assert_parity(got, ref, TOL_FP64 if precision == "fp64" else TOL_MIXED,
+                      "c3 full-size sampled %s %s" % (precision, opname), scale)
+        del out
+    plan.close()
+    b.close()

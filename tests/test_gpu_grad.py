@@ -205,3 +205,28 @@ def test_aab_autograd_function_matches_finite_differences(shg):
             fd = (lp - lm) / (2 * h)
             assert abs(g[c_idx, d] - fd) <= 1e-7 * max(1.0, abs(fd)), (c_idx, d, g[c_idx, d], fd)
     b.close()
+
+
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
+def test_grad_full_size_c5_sampled(shg, opname, op, omega):
+    """The full 500,000-pair gradient workload (l up to 5, K up to 12) in one
+    call; 200 sampled pair gradients against the oracle's vector-Jacobian
+    products with the gradient bar."""
+    import torch
+    sh, pa, pb = W.make("c5_grad_500k_l5_k12")
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = np.random.default_rng(44).uniform(-1, 1, total)
+    ga, gb = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega)
+    torch.cuda.synchronize()
+    ga = ga.cpu().numpy()
+    idx = np.sort(np.random.default_rng(45).choice(len(pa), 200, replace=False))
+    sub, spa, spb = W.subset_pairs(sh, pa, pb, idx)
+    l = sh["l"].astype(np.int64)
+    sizes = (2 * l[pa] + 1) * (2 * l[pb] + 1)
+    ws = np.concatenate([w[off[p]:off[p] + sizes[p]] for p in idx])
+    ref, scale = _oracle_vjp(sub, spa, spb, op, omega, ws)
+    bar = 1e-10 * np.abs(ref) + 1e-12 + 1e-15 * scale
+    ex = np.abs(ga[idx] - ref) / bar
+    assert ex.max() <= 1.0, (opname, ex.max())
+    b.close()

@@ -105,3 +105,46 @@ def test_mixed_error_table_c2(shg):
         with open(path, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
     assert worst <= 1.0, worst
+
+
+def test_mixed_error_table_c3_classes_up_to_l6(shg):
+    """Per-(la, lb, operator) error of the compensated variant on the 2M-pair
+    recipe's classes (l up to 6, K up to 20; 1/r and erfc(0.11)): a stratified
+    sample of up to 20 pairs per class, checked against the oracle with the
+    mixed bar; SHG_ERROR_TABLE_C3=<path> writes the table."""
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=200_000)
+    l = sh["l"]
+    rng = np.random.default_rng(6)
+    idx = []
+    for la in range(7):
+        for lb in range(7):
+            sel = np.where((l[pa] == la) & (l[pb] == lb))[0]
+            if len(sel):
+                idx.append(rng.choice(sel, min(20, len(sel)), replace=False))
+    idx = np.sort(np.concatenate(idx))
+    sub, spa, spb = W.subset_pairs(sh, pa, pb, idx)
+    sl = sub["l"]
+    table, worst = {}, 0.0
+    for opname, op, omega in [("coulomb", 1, 0.0), ("erfc", 2, 0.11)]:
+        got, off = _run(shg, sub, spa, spb, opname, omega)
+        ref, scale = reference_2c(sub, spa, spb, op, omega)
+        bar = TOL_MIXED[0] * np.abs(ref) + TOL_MIXED[1] + TOL_MIXED[2] * scale
+        sizes = (2 * sl[spa].astype(np.int64) + 1) * (2 * sl[spb].astype(np.int64) + 1)
+        for la in range(7):
+            for lb in range(7):
+                sel = np.where((sl[spa] == la) & (sl[spb] == lb))[0]
+                if not len(sel):
+                    continue
+                e = np.concatenate([np.arange(off[p], off[p] + sizes[p]) for p in sel])
+                r, g, bb, sc = ref[e], got[e], bar[e], scale[e]
+                big = np.abs(r) > np.maximum(1e-8 * sc, 1e-12)
+                rel = float(np.max(np.abs(g[big] - r[big]) / np.abs(r[big]))) if big.any() else 0.0
+                ex = float(np.max(np.abs(g - r) / bb))
+                table["%s l%d%d" % (opname, la, lb)] = {"max_rel": rel, "max_excess": ex, "pairs": int(len(sel))}
+                worst = max(worst, ex)
+    path = os.environ.get("SHG_ERROR_TABLE_C3")
+    if path:
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    assert len(table) == 2 * 49
+    assert worst <= 1.0, worst
