@@ -122,17 +122,23 @@ __device__ void pair_grad_fp64(const Args2c &g, int p)
         }
 #pragma unroll
         for (int e = 0; e < J * J; ++e) G1 = fma(f1[e] * wa[e], z[e], G1);
+        // compact (runtime-J) dW rows: six unrolled copies per J cost more in
+        // instruction fetch than the loops do
+#pragma unroll 1
         for (int d = 0; d < 3; ++d) {
-            double dw[J * J];
-            w_row<J>(dRc[d], dRs[d], la, ma, dw);
+            double dw[kJmax * kJmax];
+            w_row_rt(dRc[d], dRs[d], la, ma, J, dw);
 #pragma unroll
             for (int e = 0; e < J * J; ++e) G2[d] = fma(f0[e] * dw[e], z[e], G2[d]);
         }
     }
     for (int mb = -lb; mb <= lb; ++mb)
+        // compact (runtime-J) dW rows: six unrolled copies per J cost more in
+        // instruction fetch than the loops do
+#pragma unroll 1
         for (int d = 0; d < 3; ++d) {
-            double dw[J * J];
-            w_row<J>(dRc[d], dRs[d], lb, mb, dw);
+            double dw[kJmax * kJmax];
+            w_row_rt(dRc[d], dRs[d], lb, mb, J, dw);
 #pragma unroll
             for (int e = 0; e < J * J; ++e) G2[d] = fma(f0[e] * dw[e], Y[mb + lb][e], G2[d]);
         }
