@@ -7,8 +7,9 @@
 //   O^{(k)}_{ab} = sum_{i,j} w_a[i] w_b[j] G^{(k)}[i][j],
 //   w = N c (2 alpha)^{-l}                               (Eq. O_rab2_deriv),
 // instead of recomputing the radial terms per shell pair.  One warp per
-// group: G in shared memory, lanes over primitive pairs, then over shell
-// pairs.  The angular part follows in the class-tiled kernel (OP_PRE).
+// group: G in shared memory, lanes over primitive pairs, then over (shell
+// pair, order) items.  The angular part follows in the class-tiled kernel
+// (OP_PRE).
 #include "shg_device.cuh"
 
 namespace shg {
@@ -85,6 +86,7 @@ template <int OP>
 __global__ void __launch_bounds__(32 * kFamWarps) k_family_radial(const ArgsFam g)
 {
     __shared__ double Gs[kFamWarps][kFamOrd * kFamPP];
+    __shared__ int Js[kFamWarps][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double *gs = Gs[w];
     for (;;) {
@@ -105,11 +107,35 @@ __global__ void __launch_bounds__(32 * kFamWarps) k_family_radial(const ArgsFam 
             for (int k = gr.kmin; k <= gr.kmax; ++k) gs[(k - gr.kmin) * kFamPP + ij] = G[k];
         }
         __syncwarp();
-        for (int q = lane; q < gr.count; q += 32) {
-            const int p = gr.start + q;      // the subset is stored in group order
-            const ShellRec sa = g.shells[g.pair_a[p]], sb = g.shells[g.pair_b[p]];
-            const int J = (sa.l < sb.l ? sa.l : sb.l) + 1, kmax = sa.l + sb.l;
-            for (int tj = 0; tj < J; ++tj) {
+        // contraction: lanes over (shell pair, order) items, 32 shell pairs at a
+        // time; item it belongs to the pair r with js[r] <= it < js[r + 1]
+        int *js = Js[w];
+        for (int q0 = 0; q0 < gr.count; q0 += 32) {
+            int Jq = 0;
+            if (q0 + lane < gr.count) {
+                const int p = gr.start + q0 + lane;
+                const int la = g.shells[g.pair_a[p]].l, lb = g.shells[g.pair_b[p]].l;
+                Jq = (la < lb ? la : lb) + 1;
+            }
+            int inc = Jq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            js[lane + 1] = inc;
+            if (lane == 0) js[0] = 0;
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            __syncwarp();
+            for (int it = lane; it < total; it += 32) {
+                int r = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (js[r + step] <= it) r += step;
+                const int tj = it - js[r];
+                const int p = gr.start + q0 + r;      // the subset is stored in group order
+                const ShellRec sa = g.shells[g.pair_a[p]], sb = g.shells[g.pair_b[p]];
+                const int kmax = sa.l + sb.l;
                 const double *gk = gs + (kmax - tj - gr.kmin) * kFamPP;
                 double s = 0.0;
                 for (int i = 0; i < gr.fa_k; ++i) {
@@ -119,8 +145,8 @@ __global__ void __launch_bounds__(32 * kFamWarps) k_family_radial(const ArgsFam 
                 }
                 g.o_pre[(int64_t)p * kJmax + tj] = s;
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 

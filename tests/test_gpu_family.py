@@ -74,6 +74,26 @@ def test_family_mixed_with_regular_pairs(shg, opname, op, omega):
     assert_parity(fam, ref, TOL_FP64, "family c3 " + opname, scale)
 
 
+@pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("gauss", 4, 1.0)])
+def test_family_groups_of_more_than_32_pairs(shg, opname, op, omega):
+    """Ten shells (l up to 3) on one family per atom: 100 shell pairs per atom
+    pair and 55 on the diagonal, so a group's contraction runs over several
+    chunks of 32 shell pairs with up to 4 orders each."""
+    from paper_1701_06588_gb300 import molecule
+    rng = np.random.default_rng(43)
+    ls = (0, 0, 1, 1, 2, 2, 3, 3, 1, 0)
+    e = np.sort(np.exp(rng.uniform(np.log(0.08), np.log(40.0), 6)))[::-1].copy()
+    bs = {"Z": [(l, e, rng.uniform(-1.0, 1.0, 6)) for l in ls]}
+    coords = np.array([[0.0, 0.0, 0.0], [2.1, 0.3, -0.4], [-0.5, 2.6, 1.2]])
+    shells, _, _ = molecule.molecule_shells(coords, ["Z"] * 3, bs)
+    pa, pb = molecule.shell_pairs(len(shells["l"]), True)
+    fam, reg, (nf, ng) = _both(shg, shells, pa, pb, opname, omega)
+    assert nf == len(pa) == 465 and ng == 6
+    ref, scale = reference_2c(shells, pa, pb, op, omega)
+    assert_parity(fam, ref, TOL_FP64, "family big groups " + opname, scale)
+    assert np.all(np.abs(fam - reg) <= 1e-14 * scale + 1e-13 * np.abs(reg)), opname
+
+
 def test_family_errors(shg):
     import torch
     from paper_1701_06588_gb300 import _lib as L
