@@ -32,7 +32,8 @@ WORKLOAD = "c2_200k_l4_k8"
 OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
 DF_FMA_FP32_INSTR = 18.0       # FP32 instructions of one double-float multiply-add
 FP64_NOMINAL_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, context)
-PROFILES = {"fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt"),
+PROFILES = {"fp64_fused": os.path.join(ROOT, "profiles", "k_2c_fp64_fused_persistent_c2_200k.txt"),
+            "fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt"),
             "mixed": os.path.join(ROOT, "profiles", "k_2c_mixed_persistent_c2_200k.txt")}
 
 
@@ -47,6 +48,8 @@ def parse():
     p.add_argument("--n-pairs", type=int, default=None, help="smaller case of the same recipe (profiling only)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the headline path (the other forms are reported beside it)")
+    p.add_argument("--separate", action="store_true",
+                   help="FP64 headline as one pass per operator instead of the fused multi-operator pass")
     p.add_argument("--no-extras", action="store_true", help="time only the headline path (profiling)")
     p.add_argument("--no-tune", action="store_true", help="default launch shape instead of the autotuner (profiling)")
     p.add_argument("--profile-case", default=None, choices=["aab", "aab_grad", "grad", "family"],
@@ -252,6 +255,14 @@ def run_ours(args, rank, world):
                 e1.record(stream)
         return fn
 
+    def fused_step(plan):
+        def fn(evs):
+            e0, e1 = evs[0]
+            e0.record(stream)
+            plan.exec_fused(names, d_off, outs, omegas=omegas)
+            e1.record(stream)
+        return fn
+
     def graph_step(graph):
         def fn(evs):
             e0, e1 = evs[0]
@@ -260,22 +271,27 @@ def run_ours(args, rank, world):
             e1.record(stream)
         return fn
 
-    # autotuned launch shape for each precision (cached per GPU and workload)
+    # headline form: FP64 as the fused multi-operator pass (one kernel per step)
+    # unless --separate; mixed as one pass per operator
+    fused = args.precision == "fp64" and not args.separate
+    form = "fp64_fused" if fused else args.precision
+    # autotuned launch shape for each form (cached per GPU and workload)
     tuned = {}
-    for prec in ("fp64", "mixed"):
-        if args.no_extras and prec != args.precision:
+    for f in ("fp64_fused", "fp64", "mixed"):
+        if args.no_extras and f != form:
             continue
         if args.no_tune:
-            tuned[prec] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0}
+            tuned[f] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0}
         else:
-            tuned[prec] = autotune.tune_2c(basis, pa, pb, names, omegas, d_off, outs, precision=prec)
+            tuned[f] = autotune.tune_2c(basis, pa, pb, names, omegas, d_off, outs, precision=f)
 
-    # headline: the autotuned plan of the requested precision, replayed as one CUDA graph per step
-    plan = autotune.tuned_plan(basis, pa, pb, tuned[args.precision])
-    graph = api.Graph2c(plan, names, omegas, d_off, outs, precision=args.precision)
+    # headline: the autotuned plan of the headline form, replayed as one CUDA graph per step
+    plan = autotune.tuned_plan(basis, pa, pb, tuned[form])
+    graph = api.Graph2c(plan, names, omegas, d_off, outs, precision=args.precision, fused=fused)
+    kern_step = fused_step(plan) if fused else plan_step(plan, args.precision)
     for _ in range(max(args.warmup, 0)):
         graph.launch()
-        plan_step(plan, args.precision)([(torch.cuda.Event(enable_timing=True),) * 2 for _ in OPS])
+        kern_step([(torch.cuda.Event(enable_timing=True),) * 2 for _ in OPS])
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -290,22 +306,24 @@ def run_ours(args, rank, world):
         dist.barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    # kernel time per operator of the same plan (same kernels, launched one by one)
-    kern_ms, per_op_ms = time_steps(plan_step(plan, args.precision), args.steps, per_op=True)
+    # kernel time of the same plan (same kernels, launched outside the graph; per operator
+    # for the separate passes)
+    kern_ms, per_op_ms = time_steps(kern_step, args.steps, per_op=not fused)
     if dist:
         t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     value = world * units_per_step / (ms_step * 1e-3)
 
-    flops = [counts.workload_flops(shells, pa, pb, op) for _, op, _ in OPS]
-    flops_step = sum(flops)
+    flops_separate = sum(counts.workload_flops(shells, pa, pb, op) for _, op, _ in OPS)
+    flops_step = (counts.workload_fused_flops(shells, pa, pb, [(op, om) for _, op, om in OPS]) if fused
+                  else flops_separate)
     achieved = flops_step / (kern_ms * 1e-3) / 1e12
     # double-float: one multiply-add of the FP64 formula costs 18 FP32 instructions
     # (TwoProd 4, FastTwoSum 3, TwoSum 6, 2 adds, FastTwoSum 3), so the FP32 FMA rate
     # (2 flops per instruction) bounds FP64-formula flops at fp32_peak / 18
     peak = (fp64_peak if args.precision == "fp64" else fp32_peak / DF_FMA_FP32_INSTR) / 1e12
-    traffic = read_profile_traffic(args.precision)
+    traffic = read_profile_traffic(form)
 
     forms = {}
     if not args.no_extras:
@@ -320,24 +338,27 @@ def run_ours(args, rank, world):
         ms_pp, _ = time_steps(plan_step(pp, "fp64"), args.steps, per_op=True)
         forms["fp64_persistent"] = {"ms_per_step": ms_pp, "value": units_per_step / (ms_pp * 1e-3)}
         pp.close()
-        other = "mixed" if args.precision == "fp64" else "fp64"
-        po = autotune.tuned_plan(basis, pa, pb, tuned[other])
-        go = api.Graph2c(po, names, omegas, d_off, outs, precision=other)
-        go.launch()
-        torch.cuda.synchronize()
-        ms_o, _ = time_steps(graph_step(go), args.steps)
-        forms[other + "_tuned_graph"] = {"ms_per_step": ms_o, "value": units_per_step / (ms_o * 1e-3),
-                                         "launch": {k: tuned[other][k] for k in ("schedule", "threads_per_cta",
-                                                                                  "ctas_per_sm")}}
-        go.close()
-        po.close()
-        forms[args.precision + "_tuned_graph"] = {"ms_per_step": ms_step, "value": units_per_step / (ms_step * 1e-3),
-                                                  "launch": {k: tuned[args.precision][k] for k in
-                                                             ("schedule", "threads_per_cta", "ctas_per_sm")}}
-        if "mixed_tuned_graph" in forms:
-            forms["mixed_speedup_vs_fp64_per_class"] = ms_pc / forms["mixed_tuned_graph"]["ms_per_step"]
-            forms["mixed_speedup_vs_fp64_tuned_graph"] = (forms["fp64_tuned_graph"]["ms_per_step"] /
-                                                          forms["mixed_tuned_graph"]["ms_per_step"])
+        for other in ("fp64_fused", "fp64", "mixed"):
+            if other == form:
+                continue
+            po = autotune.tuned_plan(basis, pa, pb, tuned[other])
+            go = api.Graph2c(po, names, omegas, d_off, outs, precision="mixed" if other == "mixed" else "fp64",
+                             fused=other == "fp64_fused")
+            go.launch()
+            torch.cuda.synchronize()
+            ms_o, _ = time_steps(graph_step(go), args.steps)
+            forms[other + "_tuned_graph"] = {"ms_per_step": ms_o, "value": units_per_step / (ms_o * 1e-3),
+                                             "launch": {k: tuned[other][k] for k in ("schedule", "threads_per_cta",
+                                                                                      "ctas_per_sm")}}
+            go.close()
+            po.close()
+        forms[form + "_tuned_graph"] = {"ms_per_step": ms_step, "value": units_per_step / (ms_step * 1e-3),
+                                        "launch": {k: tuned[form][k] for k in
+                                                   ("schedule", "threads_per_cta", "ctas_per_sm")}}
+        for f in ("fp64_fused", "mixed"):
+            forms[f + "_speedup_vs_fp64_per_class"] = ms_pc / forms[f + "_tuned_graph"]["ms_per_step"]
+            forms[f + "_speedup_vs_fp64_tuned_graph"] = (forms["fp64_tuned_graph"]["ms_per_step"] /
+                                                         forms[f + "_tuned_graph"]["ms_per_step"])
         torch.cuda.synchronize()
 
     # end to end through the public API with host buffers
@@ -360,9 +381,13 @@ def run_ours(args, rank, world):
         d_off2.copy_(off_h, non_blocking=True)
         basis.set_centers(cent_h.numpy())
         t2 = time.perf_counter()
-        p2 = autotune.tuned_plan(basis, d_pa, d_pb, tuned[args.precision])
+        p2 = autotune.tuned_plan(basis, d_pa, d_pb, tuned[form])
         t3 = time.perf_counter()
-        for (name, _, om), o, oh in zip(OPS, outs, outs_h):
+        if fused:
+            p2.exec_fused(names, d_off2, outs, omegas=omegas)
+            for o, oh in zip(outs, outs_h):
+                oh.copy_(o, non_blocking=True)
+        for (name, _, om), o, oh in ([] if fused else zip(OPS, outs, outs_h)):
             p2.exec(name, d_off2, o, omega=om, precision=args.precision)
             # read each operator's blocks back on a copy stream while the next operator computes
             done = torch.cuda.Event()
@@ -392,12 +417,15 @@ def run_ours(args, rank, world):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": workload_description(n_pairs), "pairs": n_pairs, "operators": names,
-                   "precision": args.precision, "form": "autotuned launch shape, one CUDA graph per step",
-                   "launch": {k: tuned[args.precision][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
+                   "precision": args.precision,
+                   "form": ("fused multi-operator FP64 pass (one kernel per step, geometry-only Q_j shared by the "
+                            "five operators), autotuned launch shape, one CUDA graph per step" if fused else
+                            "one pass per operator, autotuned launch shape, one CUDA graph per step"),
+                   "launch": {k: tuned[form][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
                    "units_per_step": units_per_step, "elements_per_step": total * len(OPS),
                    "l2": "flushed between steps by a 512 MB device write outside the timed events",
                    "wall_s_timed_loop": wall},
-        "per_operator_kernel_ms": {n: m for n, m in zip(names, per_op_ms)},
+        "per_operator_kernel_ms": {n: m for n, m in zip(names, per_op_ms)} if per_op_ms else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "peak_source": ("measured FP64 FMA-chain probe (shg_measure_alu_peak) in this run; nominal %.2f "
@@ -407,16 +435,21 @@ def run_ours(args, rank, world):
                      "in this run: FP32 rate / 18 (FP32 instructions of one double-float multiply-add); "
                      "algorithmic flops are the FP64 formula count",
                      "algorithmic_flops_per_step": flops_step, "kernel_ms_per_step": kern_ms,
-                     "kernel": "k_2c_%s_persistent<op> / static (5 operators per step)" %
-                               ("fp64" if args.precision == "fp64" else "mixed")},
+                     "separate_passes_flops_per_step": flops_separate,
+                     "kernel": ("k_2c_fp64_fused_persistent (5 operators in one pass)" if fused else
+                                "k_2c_%s_persistent<op> / static (5 operators per step)" %
+                                ("fp64" if args.precision == "fp64" else "mixed"))},
         "forms": forms,
         "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "what": "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
-                        "shg_plan_2c_create, 5 x shg_plan_2c_exec, D2H of all blocks to pinned memory (operator k's "
-                        "copy on a second stream overlaps operator k+1's kernel)",
+                "what": ("per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
+                         "shg_plan_2c_create, shg_plan_2c_exec_fused (5 operators), D2H of all blocks to pinned "
+                         "memory" if fused else
+                         "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
+                         "shg_plan_2c_create, 5 x shg_plan_2c_exec, D2H of all blocks to pinned memory (operator "
+                         "k's copy on a second stream overlaps operator k+1's kernel)"),
                 "ms_parts": {k: 1e3 * statistics.mean(v) for k, v in parts.items() if v}},
-        "gpu_launches": args.steps * len(OPS) * plan.launches,
+        "gpu_launches": args.steps * (1 if fused else len(OPS)) * plan.launches,
         "clocks": clk,
         "measured_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12},
     }
@@ -524,6 +557,15 @@ def other_configs(args):
                                 else 50) for n, w in ops)
             entry[prec] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),
                            "algorithmic_tflops": flops / (ms * 1e-3) / 1e12}
+        if len(ops) > 1:
+            # the same operators in one fused FP64 pass
+            outs = [out] + [torch.empty(total, dtype=torch.float64, device="cuda") for _ in ops[1:]]
+            names, oms = [n for n, _ in ops], [w for _, w in ops]
+            ms = _events_ms(lambda: plan.exec_fused(names, d_off, outs, omegas=oms), 3 if len(pa) > 1e5 else 50)
+            ff = counts.workload_fused_flops(sh, pa, pb, [(api.L.OPERATORS[n], w) for n, w in ops])
+            entry["fp64_fused"] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),
+                                   "algorithmic_tflops": ff / (ms * 1e-3) / 1e12}
+            del outs
         res[key] = entry
         plan.close()
         b.close()

@@ -45,6 +45,8 @@ SIGNATURES = [
     ("shg_family_plan_destroy", None, [_P]),
     ("shg_plan_2c_set_launch", _I, [_P, _I, _I]),
     ("shg_graph_2c_create", _I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
+    ("shg_plan_2c_exec_fused", _I, [_P, _I, _P, _P, _P, _P, _P]),
+    ("shg_graph_2c_create_fused", _I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     ("shg_graph_launch", _I, [_P, _P]),
     ("shg_graph_destroy", None, [_P]),
     ("shg_eval_3c_aab", _I, [_P, _P, _L, _P, _P, _P, _I, _D, _P, _P, _P]),
@@ -190,6 +192,29 @@ def shg_graph_2c_create(plan, ops, omegas, precision, d_out_offsets, d_outs):
     h = _P()
     check(load().shg_graph_2c_create(plan, n, _ptr(ops_a), _ptr(om_a), precision, _ptr(d_out_offsets),
                                      ctypes.cast(outs_a, ctypes.c_void_p), ctypes.byref(h)))
+    return h.value
+
+
+def _op_arrays(ops, omegas, d_outs):
+    import numpy as _np
+    n = len(ops)
+    ops_a = _np.ascontiguousarray(ops, dtype=_np.int32)
+    om_a = _np.ascontiguousarray(omegas, dtype=_np.float64)
+    outs_a = (ctypes.c_void_p * n)(*[_ptr(o) for o in d_outs])
+    return n, ops_a, om_a, outs_a
+
+
+def shg_plan_2c_exec_fused(plan, ops, omegas, d_out_offsets, d_outs, stream):
+    n, ops_a, om_a, outs_a = _op_arrays(ops, omegas, d_outs)
+    return check(load().shg_plan_2c_exec_fused(plan, n, _ptr(ops_a), _ptr(om_a), _ptr(d_out_offsets),
+                                               ctypes.cast(outs_a, ctypes.c_void_p), stream))
+
+
+def shg_graph_2c_create_fused(plan, ops, omegas, d_out_offsets, d_outs):
+    n, ops_a, om_a, outs_a = _op_arrays(ops, omegas, d_outs)
+    h = _P()
+    check(load().shg_graph_2c_create_fused(plan, n, _ptr(ops_a), _ptr(om_a), _ptr(d_out_offsets),
+                                           ctypes.cast(outs_a, ctypes.c_void_p), ctypes.byref(h)))
     return h.value
 
 

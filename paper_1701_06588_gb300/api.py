@@ -107,6 +107,15 @@ class Plan2c:
                            out_offsets, out, _stream(stream))
         return out
 
+    def exec_fused(self, ops, out_offsets, outs, omegas=None, stream=None):
+        """Several operators (overlap, coulomb, erfc, erf, gauss; each at most
+        once) in one FP64 pass sharing the geometry-only angular part;
+        outs[i] receives operator ops[i] in the layout of exec."""
+        omegas = [0.0] * len(ops) if omegas is None else [float(w) for w in omegas]
+        L.shg_plan_2c_exec_fused(self.handle, [_op(o) for o in ops], omegas, out_offsets, list(outs),
+                                 _stream(stream))
+        return outs
+
     def close(self):
         if getattr(self, "handle", None):
             L.shg_plan_destroy(self.handle)
@@ -249,14 +258,21 @@ class ThreeIndexOverlap(torch.autograd.Function):
 
 class Graph2c:
     """A CUDA graph replaying one plan for several operators (C ABI
-    shg_graph_2c_create / shg_graph_launch)."""
+    shg_graph_2c_create / shg_graph_launch; fused=True captures one
+    shg_plan_2c_exec_fused pass instead of one pass per operator)."""
 
-    def __init__(self, plan, ops, omegas, out_offsets, outs, precision="fp64"):
+    def __init__(self, plan, ops, omegas, out_offsets, outs, precision="fp64", fused=False):
         self.plan = plan
         self.outs = list(outs)
         self.out_offsets = out_offsets
-        self.handle = L.shg_graph_2c_create(plan.handle, [_op(o) for o in ops], [float(w) for w in omegas],
-                                            _prec(precision), out_offsets, self.outs)
+        if fused:
+            if _prec(precision) != L.SHG_PREC_FP64:
+                raise ValueError("the fused pass is FP64 only")
+            self.handle = L.shg_graph_2c_create_fused(plan.handle, [_op(o) for o in ops],
+                                                      [float(w) for w in omegas], out_offsets, self.outs)
+        else:
+            self.handle = L.shg_graph_2c_create(plan.handle, [_op(o) for o in ops], [float(w) for w in omegas],
+                                                _prec(precision), out_offsets, self.outs)
 
     def launch(self, stream=None):
         L.shg_graph_launch(self.handle, _stream(stream))

@@ -52,7 +52,17 @@ def _save(db):
 
 
 def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp64", reps=3, force=False):
-    """Best (schedule, threads_per_cta, ctas_per_sm) for this workload; times in ms per pass over `ops`."""
+    """Best (schedule, threads_per_cta, ctas_per_sm) for this workload; times in ms per pass over `ops`.
+    precision "fp64_fused" tunes the fused multi-operator FP64 pass (one exec_fused per pass)."""
+    fused = precision == "fp64_fused"
+
+    def one_pass(plan):
+        if fused:
+            plan.exec_fused(ops, out_offsets, outs, omegas=omegas)
+        else:
+            for op, om, o in zip(ops, omegas, outs):
+                plan.exec(op, out_offsets, o, omega=om, precision=precision)
+
     key = "|".join([torch.cuda.get_device_name(), precision, ",".join(map(str, ops)),
                     workload_signature(basis, pair_a, pair_b)])
     db = _load()
@@ -65,14 +75,12 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
             plans[sched] = api.Plan2c(basis, pair_a, pair_b, schedule=sched)
         plan = plans[sched]
         api.set_launch(plan, threads, ctas)
-        for op, om, o in zip(ops, omegas, outs):
-            plan.exec(op, out_offsets, o, omega=om, precision=precision)
+        one_pass(plan)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            for op, om, o in zip(ops, omegas, outs):
-                plan.exec(op, out_offsets, o, omega=om, precision=precision)
+            one_pass(plan)
         e1.record()
         torch.cuda.synchronize()
         results.append((e0.elapsed_time(e1) / reps, sched, threads, ctas))

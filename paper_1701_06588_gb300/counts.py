@@ -94,6 +94,65 @@ def pair_flops(la, lb, ka, kb, op):
     return radial + harmonics + w_rows + scale + assembly
 
 
+def _fused_radial_flops(ops, J, kmin):
+    """Per primitive pair of the fused pass (shg_plan_2c_exec_fused), with the
+    per-term counts of _radial_flops: shared setup and (-rho)^kmin, one Boys
+    sum for 1/r and erfc, one attenuated sum per distinct omega of erf/erfc."""
+    ops = dict(ops)                     # op id -> omega
+    setup = 1 + 1 + 2 + 1 + 1
+    powk = 2 * max(int(np.ceil(np.log2(kmin + 1))), 0)
+    f = setup
+    if OP_OVERLAP in ops or OP_COULOMB in ops or OP_ERFC in ops:
+        f += powk
+    if OP_OVERLAP in ops:
+        f += 4 + J * 2
+    if OP_GAUSS in ops:
+        f += 10 + powk + J * 2
+    boys_sums = (OP_COULOMB in ops or OP_ERFC in ops)
+    atts = {ops[o] for o in (OP_ERF, OP_ERFC) if o in ops}
+    if boys_sums or atts:
+        f += 4                          # 2 pi^{5/2} w / (alpha beta sqrt(c))
+    if boys_sums:
+        f += _BOYS + 3 * (J - 1) + J * (2 + 1)
+    f += len(atts) * (6 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1))
+    return f
+
+
+def fused_pair_flops(la, lb, ka, kb, ops):
+    """Algorithmic FP64 flops of one contracted shell pair in the fused pass
+    over `ops` ((op id, omega) pairs; numpy-vectorised over la, lb, ka, kb):
+    radial sums as _fused_radial_flops, then per pair the harmonics, both W
+    sides, the (2j-1)!! B weights on W_a, Q_j (J^2 fma per element) and per
+    operator its J orders (fma) and the A_a A_b factor."""
+    ops = list(ops)
+    la = np.asarray(la, dtype=np.int64)
+    lb = np.asarray(lb, dtype=np.int64)
+    kk = np.asarray(ka, dtype=np.int64) * np.asarray(kb, dtype=np.int64)
+    J = np.minimum(la, lb) + 1
+    kmin = np.maximum(la, lb)
+    lmax = np.maximum(la, lb)
+    na, nb = 2 * la + 1, 2 * lb + 1
+    nop = len(ops)
+    rad = np.zeros(np.broadcast(la, lb, kk).shape, dtype=np.float64)
+    for j in range(1, 8):
+        for km in range(0, 7):
+            m = (J == j) & (kmin == km)
+            if np.any(m):
+                rad[m] = _fused_radial_flops(ops, j, km)
+    post = J * (nop + (1 if any(o == OP_ERFC for o, _ in ops) else 0))   # 2^{kmax-j} scaling, erfc = 1/r - erf
+    harmonics = 8.0 * (lmax + 1) * (lmax + 2) / 2
+    w_rows = (na + nb) * J * J
+    scale = na * J * J                                                    # (2j-1)!! B weights on W_a
+    assembly = na * nb * (2 * J * J + 1 + nop * (2 * J + 1))
+    return kk * rad + post + harmonics + w_rows + scale + assembly
+
+
+def workload_fused_flops(shells, pair_a, pair_b, ops):
+    l = np.asarray(shells["l"])
+    k = np.asarray(shells["nprim"])
+    return float(np.sum(fused_pair_flops(l[pair_a], l[pair_b], k[pair_a], k[pair_b], ops)))
+
+
 def workload_flops(shells, pair_a, pair_b, op):
     l = np.asarray(shells["l"])
     k = np.asarray(shells["nprim"])

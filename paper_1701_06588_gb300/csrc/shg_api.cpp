@@ -941,17 +941,11 @@ struct shg_graph {
     cudaGraphExec_t exec = nullptr;
 };
 
-int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
-                        const int64_t *off, double *const *outs, shg_graph_t **out)
+// Capture the launches `issue` makes on a private stream into an instantiated graph.
+extern "C++" {
+template <class F>
+static int capture_graph(F issue, shg_graph_t **out)
 {
-    g_err.clear();
-    if (!out) return fail(SHG_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!p || n_ops < 1 || !ops || !omegas || !outs) return fail(SHG_EINVAL, "bad argument");
-    for (int i = 0; i < n_ops; ++i) {
-        int r = check_op(ops[i], omegas[i], precision);
-        if (r) return r;
-    }
     cudaStream_t s = nullptr;
     SHG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -959,8 +953,7 @@ int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *
         cudaStreamDestroy(s);
         return fail(SHG_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
     }
-    int rc = SHG_OK;
-    for (int i = 0; i < n_ops && rc == SHG_OK; ++i) rc = shg_plan_2c_exec(p, ops[i], omegas[i], 0.0, precision, off, outs[i], s);
+    const int rc = issue(s);
     std::string msg = g_err;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s, &graph);
@@ -986,6 +979,28 @@ int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *
     g->exec = exec;
     *out = g;
     return SHG_OK;
+}
+}  // extern "C++"
+
+int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
+                        const int64_t *off, double *const *outs, shg_graph_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(SHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p || n_ops < 1 || !ops || !omegas || !outs) return fail(SHG_EINVAL, "bad argument");
+    for (int i = 0; i < n_ops; ++i) {
+        int r = check_op(ops[i], omegas[i], precision);
+        if (r) return r;
+    }
+    return capture_graph(
+        [&](cudaStream_t s) {
+            int rc = SHG_OK;
+            for (int i = 0; i < n_ops && rc == SHG_OK; ++i)
+                rc = shg_plan_2c_exec(p, ops[i], omegas[i], 0.0, precision, off, outs[i], s);
+            return rc;
+        },
+        out);
 }
 
 int shg_graph_launch(shg_graph_t *g, void *stream)
@@ -1111,6 +1126,90 @@ static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const i
         }
     }
     return SHG_OK;
+}
+
+// Arguments of a fused pass: the operators are checked (each of overlap,
+// 1/r, erfc, erf and the Gaussian at most once, FP64), outputs placed by
+// operator id.
+static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
+                      double *const *outs, ArgsFused &a)
+{
+    if (!p) return fail(SHG_EINVAL, "plan is NULL");
+    if (n_ops < 1 || n_ops > 5) return fail(SHG_EINVAL, "n_ops must be 1..5 (got %d)", n_ops);
+    if (!ops || !omegas || !outs) return fail(SHG_EINVAL, "NULL operator, omega or output array");
+    for (int i = 0; i < 5; ++i) a.out[i] = nullptr;
+    a.w_erf = a.w_erfc = a.w_gauss = 0.0;
+    for (int i = 0; i < n_ops; ++i) {
+        const int op = ops[i];
+        if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS)
+            return fail(SHG_EINVAL, "the fused pass takes overlap, 1/r, erfc, erf and the Gaussian only (got %d)", op);
+        int r = check_op(op, omegas[i], SHG_PREC_FP64);
+        if (r) return r;
+        if (a.out[op]) return fail(SHG_EINVAL, "operator %d listed twice", op);
+        if (!outs[i]) return fail(SHG_EINVAL, "NULL output for operator %d", op);
+        a.out[op] = outs[i];
+        if (op == SHG_OP_ERF) a.w_erf = omegas[i];
+        if (op == SHG_OP_ERFC) a.w_erfc = omegas[i];
+        if (op == SHG_OP_GAUSS) a.w_gauss = omegas[i];
+    }
+    if (!off) return fail(SHG_EINVAL, "NULL output offsets");
+    a.share_att = (a.out[SHG_OP_ERF] && a.out[SHG_OP_ERFC] && a.w_erf == a.w_erfc) ? 1 : 0;
+    return SHG_OK;
+}
+
+int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
+                           double *const *outs, void *stream)
+{
+    g_err.clear();
+    ArgsFused a;
+    int r = fused_args(p, n_ops, ops, omegas, off, outs, a);
+    if (r) return r;
+    if (p->d.n_pairs == 0 || p->d.n_tiles == 0) return SHG_OK;
+    r = current_device_matches(p->d.basis->device);
+    if (r) return r;
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    a.shells = p->d.basis->shells;
+    a.prims = p->d.basis->prims;
+    a.centers = p->d.basis->centers;
+    a.pair_a = p->d.pair_a;
+    a.pair_b = p->d.pair_b;
+    a.perm = p->d.perm;
+    a.tiles = p->d.tiles;
+    a.out_off = reinterpret_cast<const long long *>(off);
+    a.boys = t->boys;
+    a.boys_e = t->boys_e;
+    a.k = consts();
+    if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+        a.tile_begin = 0;
+        a.tile_end = p->d.n_tiles;
+        a.counter = p->d.counter;
+        SHG_CUDA(launch_2c_fused(a, persistent_grid_2c_fused(p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
+    } else {
+        a.counter = nullptr;
+        for (int cls = 0; cls < kNClass; ++cls) {
+            a.tile_begin = p->d.class_tile_begin[cls];
+            a.tile_end = p->d.class_tile_begin[cls + 1];
+            if (a.tile_end <= a.tile_begin) continue;
+            SHG_CUDA(launch_2c_fused(a, 0, false, s, p->d.threads));
+        }
+    }
+    return SHG_OK;
+}
+
+int shg_graph_2c_create_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
+                              double *const *outs, shg_graph_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(SHG_EINVAL, "out is NULL");
+    *out = nullptr;
+    ArgsFused chk;
+    int r = fused_args(p, n_ops, ops, omegas, off, outs, chk);
+    if (r) return r;
+    return capture_graph([&](cudaStream_t s) { return shg_plan_2c_exec_fused(p, n_ops, ops, omegas, off, outs, s); },
+                         out);
 }
 
 int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,

@@ -1,0 +1,245 @@
+// Several operators of one pair list in one pass (FP64): the two-center
+// formula of Sec. II B of arXiv:1701.06588 with the operators of Table S1,
+// rearranged so that everything that depends on the geometry only is built
+// once per shell pair and shared by the operators:
+//
+//   (a|O|b)[ma][mb] = (-1)^lb A_{la,ma} A_{lb,mb} sum_j 2^{la+lb-j} O^{(la+lb-j)} Q_j[ma][mb],
+//   Q_j[ma][mb]     = (2j-1)!! sum_kappa B_{j,kappa} sum_z W_a[ma][j,kappa,z] W_b[mb][j,kappa,z],
+//
+// Q_j is the operator-independent part (Eq. Q_matrix with the B weights of
+// Eq. B); per element it costs J^2 multiply-adds once, and each operator then
+// needs only its J radial orders (J multiply-adds).  The radial sums share the
+// primitive-pair setup (c, rho, T, the prefactors), erfc(wr)/r is formed as
+// 1/r - erf(wr)/r from the Coulomb and attenuated Boys sums (Table S1), and
+// when erf and erfc are both requested with the same omega the attenuated
+// sum is computed once.
+//
+// Work mapping as the single-operator kernel: one thread per shell pair, a
+// warp per class-pure tile of up to 32 pairs, tiles from the same plan.
+#include "shg_device.cuh"
+
+namespace shg {
+namespace {
+using namespace dev;
+
+// attenuated radial sum (the erf(omega r)/r part of Table S1) of one primitive pair
+template <int J>
+__device__ __forceinline__ void att_acc(double om, double rho, double T, int kmax, int kmin, double pre,
+                                        const ArgsFused &g, double (&O)[J])
+{
+    const double w2 = om * om;
+    const double rw = rsqrt(w2 + rho);
+    const double s = w2 * rw * rw;
+    const double f = -rho * s;
+    double F[J];
+    boys_top<J>(s * T, kmax, g.boys, g.boys_e, g.k, F);
+    double q = pre * om * rw * powi(f, kmin);
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+        O[j] = fma(q, F[j], O[j]);
+        q *= f;
+    }
+}
+
+template <int J>
+__device__ void pair_2c_fused(const ArgsFused &g, int p)
+{
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l;
+    const Vec4 A = g.centers[sa.center];
+    const Vec4 B = g.centers[sb.center];
+    const double vx = A.x - B.x, vy = A.y - B.y, vz = A.z - B.z;
+    const double R2 = vx * vx + vy * vy + vz * vz;
+    const int kmax = la + lb, kmin = kmax - J + 1;
+
+    // which sums the requested operators need (uniform over the launch)
+    const bool f_ov = g.out[OP_OVERLAP] != nullptr;
+    const bool f_ga = g.out[OP_GAUSS] != nullptr;
+    const bool f_co = g.out[OP_COULOMB] != nullptr || g.out[OP_ERFC] != nullptr;
+    const bool f_er = g.out[OP_ERF] != nullptr;
+    const bool f_x = g.out[OP_ERFC] != nullptr && !(f_er && g.share_att);
+
+    double Oov[J], Oco[J], Oer[J], Ox[J], Oga[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) Oov[j] = Oco[j] = Oer[j] = Ox[j] = Oga[j] = 0.0;
+
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        const PrimRec pa = g.prims[sa.prim_off + ia], pb = g.prims[sb.prim_off + ib];
+        const double w = pa.w2c * pb.w2c;
+        const double c = pa.alpha + pb.alpha;
+        const double rc = rsqrt(c);
+        const double ic = rc * rc;
+        const double rho = pa.alpha * pb.alpha * ic;
+        const double T = rho * R2;
+        const double mrk = powi(-rho, kmin);
+        if (f_ov) {
+            // (pi/c)^{3/2} exp(-T) (-rho)^k
+            double t = w * kPi32 * ic * rc * exp(-T) * mrk;
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                Oov[j] += t;
+                t *= -rho;
+            }
+        }
+        if (f_ga) {
+            // (pi^2/(c (rho+w)))^{3/2} exp(-w T/(rho+w)) (-w rho/(rho+w))^k
+            const double rd = rsqrt(rho + g.w_gauss);
+            const double id = rd * rd;
+            const double f = -g.w_gauss * rho * id;
+            double t = w * kPi3 * ic * rc * id * rd * exp(-g.w_gauss * T * id) * powi(f, kmin);
+#pragma unroll
+            for (int j = J - 1; j >= 0; --j) {
+                Oga[j] += t;
+                t *= f;
+            }
+        }
+        if (f_co || f_er || f_x) {
+            // 2 pi^{5/2} / (alpha beta sqrt(c)) times the Boys sums
+            const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
+            if (f_co) {
+                double F[J];
+                boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, F);
+                double t = pre * mrk;
+#pragma unroll
+                for (int j = J - 1; j >= 0; --j) {
+                    Oco[j] = fma(t, F[j], Oco[j]);
+                    t *= -rho;
+                }
+            }
+            if (f_er) att_acc<J>(g.w_erf, rho, T, kmax, kmin, pre, g, Oer);
+            if (f_x) att_acc<J>(g.w_erfc, rho, T, kmax, kmin, pre, g, Ox);
+        }
+    }
+    // erfc = coulomb - attenuated; then every operator's orders scaled by 2^{kmax-j}
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const double p2 = g.k.pow2[kmax - j];
+        Ox[j] = (Oco[j] - (f_x ? Ox[j] : Oer[j])) * p2;
+        Oov[j] *= p2;
+        Oco[j] *= p2;
+        Oer[j] *= p2;
+        Oga[j] *= p2;
+    }
+
+    double Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics(vx, vy, vz, la > lb ? la : lb, g.k, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    double Wb[2 * kLmax2c + 1][J * J];
+    for (int mb = -lb; mb <= lb; ++mb) {
+        double w[J * J];
+        w_row<J>(Rc, Rs, lb, mb, w);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) Wb[mb + lb][e] = w[e];
+    }
+    const double sgn_b = (lb & 1) ? -1.0 : 1.0;
+    const long long o = g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        double ua[J * J];
+        w_row<J>(Rc, Rs, la, ma, ua);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+#pragma unroll
+            for (int kp = 0; kp <= j; ++kp) {
+                const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+                ua[e0] *= g.k.jB[j][kp];
+                if (kp) ua[e0 + 1] *= g.k.jB[j][kp];
+            }
+        }
+        const double Aa = g.k.A[la][ma < 0 ? -ma : ma] * sgn_b;
+        for (int mb = -lb; mb <= lb; ++mb) {
+            // Q_j[ma][mb] for j = 0..J-1 (block j holds the 2j+1 entries e = j^2 .. j^2+2j)
+            double Q[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int e = j * j; e < (j + 1) * (j + 1); ++e) s = fma(ua[e], Wb[mb + lb][e], s);
+                Q[j] = s;
+            }
+            const double aa = Aa * g.k.A[lb][mb < 0 ? -mb : mb];
+            const long long idx = o + (ma + la) * nb + (mb + lb);
+#define SHG_FUSED_STORE(OPID, ARR)                                          \
+    if (g.out[OPID]) {                                                      \
+        double s = 0.0;                                                     \
+        _Pragma("unroll") for (int j = 0; j < J; ++j) s = fma(ARR[j], Q[j], s); \
+        g.out[OPID][idx] = aa * s;                                          \
+    }
+            SHG_FUSED_STORE(OP_OVERLAP, Oov)
+            SHG_FUSED_STORE(OP_COULOMB, Oco)
+            SHG_FUSED_STORE(OP_ERFC, Ox)
+            SHG_FUSED_STORE(OP_ERF, Oer)
+            SHG_FUSED_STORE(OP_GAUSS, Oga)
+#undef SHG_FUSED_STORE
+        }
+    }
+}
+
+__device__ __forceinline__ void run_tile_fused(const ArgsFused &g, const Tile &t, int lane)
+{
+    if (lane >= t.count) return;
+    const int p = g.perm[t.start + lane];
+    const int la = t.cls / (kLmax2c + 1), lb = t.cls % (kLmax2c + 1);
+    switch ((la < lb ? la : lb) + 1) {
+    case 1: pair_2c_fused<1>(g, p); break;
+    case 2: pair_2c_fused<2>(g, p); break;
+    case 3: pair_2c_fused<3>(g, p); break;
+    case 4: pair_2c_fused<4>(g, p); break;
+    case 5: pair_2c_fused<5>(g, p); break;
+    case 6: pair_2c_fused<6>(g, p); break;
+    default: pair_2c_fused<7>(g, p); break;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_2c_fp64_fused_persistent(const ArgsFused g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        run_tile_fused(g, g.tiles[t], lane);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(128) k_2c_fp64_fused_static(const ArgsFused g)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = g.tile_begin + warp;
+    if (t >= g.tile_end) return;
+    run_tile_fused(g, g.tiles[t], lane);
+}
+
+}  // namespace
+
+cudaError_t launch_2c_fused(const ArgsFused &a, int n_tiles_or_grid, bool persistent, cudaStream_t s, int threads)
+{
+    if (persistent) {
+        k_2c_fp64_fused_persistent<<<n_tiles_or_grid, threads, 0, s>>>(a);
+    } else {
+        const int tiles = a.tile_end - a.tile_begin;
+        if (tiles <= 0) return cudaSuccess;
+        const int wpb = threads / 32;
+        k_2c_fp64_fused_static<<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int persistent_grid_2c_fused(int threads, int ctas_per_sm)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_fused_persistent, threads, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
+    return (sms > 0 ? sms : 1) * per;
+}
+
+}  // namespace shg

@@ -213,6 +213,26 @@ struct Args2c {
     Consts k;
 };
 
+// Fused multi-operator FP64 pass (overlap, 1/r, erfc, erf, Gaussian): one
+// output per requested operator (null = not requested), all with the block
+// offsets out_off.
+struct ArgsFused {
+    const ShellRec *shells;
+    const PrimRec *prims;
+    const Vec4 *centers;
+    const int32_t *pair_a, *pair_b;
+    const int32_t *perm;
+    const Tile *tiles;
+    int tile_begin, tile_end;
+    int *counter;                 // persistent schedule (null: static)
+    const long long *out_off;
+    double *out[5];               // indexed by OP_OVERLAP .. OP_GAUSS
+    double w_erf, w_erfc, w_gauss;
+    int share_att;                // erf and erfc requested with the same omega
+    const double *boys, *boys_e;
+    Consts k;
+};
+
 // Family basis sets: a group of shell pairs whose shells a share one
 // exponent set (family) on one center, and likewise for b.
 constexpr int kFamPP = 100;                // largest K_a * K_b of the family path
@@ -296,6 +316,9 @@ int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
                       cudaStream_t s, int threads = 128);
 int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
+cudaError_t launch_2c_fused(const ArgsFused &args, int n_tiles_or_grid, bool persistent, cudaStream_t s,
+                            int threads);
+int persistent_grid_2c_fused(int threads = 128, int ctas_per_sm = 0);
 cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s);
 cudaError_t launch_family_radial(const ArgsFam &a, int op, cudaStream_t s);
 cudaError_t launch_gather_i64(const int64_t *src, const int32_t *idx, int64_t n, int64_t *dst, cudaStream_t s);

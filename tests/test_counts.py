@@ -39,3 +39,25 @@ def test_triple_and_gradient_flop_models():
     assert np.all(np.diff(g) > 0)
     for op in range(7):
         assert counts.grad_pair_flops(3, 2, 4, 4, op) > counts.pair_flops(3, 2, 4, 4, op)
+
+
+def test_fused_flop_model():
+    five = [(counts.OP_OVERLAP, 0.0), (counts.OP_COULOMB, 0.0), (counts.OP_ERFC, 0.11), (counts.OP_ERF, 0.11),
+            (counts.OP_GAUSS, 1.0)]
+    la, lb = np.array([0, 1, 2, 4, 4]), np.array([0, 2, 2, 3, 4])
+    k = np.array([1, 3, 5, 8, 8])
+    fused = counts.fused_pair_flops(la, lb, k, k, five)
+    separate = sum(counts.pair_flops(la, lb, k, k, op) for op, _ in five)
+    assert np.all(fused > 0) and np.all(fused < separate)
+    # erf and erfc with the same omega share one attenuated sum; different omegas need two
+    same = counts.fused_pair_flops(3, 3, 6, 6, [(counts.OP_ERF, 0.2), (counts.OP_ERFC, 0.2)])
+    diff = counts.fused_pair_flops(3, 3, 6, 6, [(counts.OP_ERF, 0.2), (counts.OP_ERFC, 0.3)])
+    assert diff > same
+    # erfc costs one Boys sum more than erf alone (the 1/r part)
+    assert (counts.fused_pair_flops(3, 3, 6, 6, [(counts.OP_ERFC, 0.2)]) >
+            counts.fused_pair_flops(3, 3, 6, 6, [(counts.OP_ERF, 0.2)]))
+    # adding an operator to the pass adds less than the operator costs on its own
+    for op, w in five:
+        rest = [o for o in five if o[0] != op]
+        extra = counts.fused_pair_flops(4, 4, 8, 8, five) - counts.fused_pair_flops(4, 4, 8, 8, rest)
+        assert 0 < extra < counts.pair_flops(4, 4, 8, 8, op)
