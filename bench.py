@@ -33,6 +33,7 @@ OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0
 DF_FMA_FP32_INSTR = 18.0       # FP32 instructions of one double-float multiply-add
 FP64_NOMINAL_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, context)
 PROFILES = {"fp64_fused": os.path.join(ROOT, "profiles", "k_2c_fp64_fused_persistent_c2_200k.txt"),
+            "mixed_fused": os.path.join(ROOT, "profiles", "k_2c_mixed_fused_persistent_c2_200k.txt"),
             "fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt"),
             "mixed": os.path.join(ROOT, "profiles", "k_2c_mixed_persistent_c2_200k.txt")}
 
@@ -49,7 +50,7 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the headline path (the other forms are reported beside it)")
     p.add_argument("--separate", action="store_true",
-                   help="FP64 headline as one pass per operator instead of the fused multi-operator pass")
+                   help="headline as one pass per operator instead of the fused multi-operator pass")
     p.add_argument("--no-extras", action="store_true", help="time only the headline path (profiling)")
     p.add_argument("--no-tune", action="store_true", help="default launch shape instead of the autotuner (profiling)")
     p.add_argument("--profile-case", default=None, choices=["aab", "aab_grad", "grad", "family"],
@@ -259,7 +260,7 @@ def run_ours(args, rank, world):
         def fn(evs):
             e0, e1 = evs[0]
             e0.record(stream)
-            plan.exec_fused(names, d_off, outs, omegas=omegas)
+            plan.exec_fused(names, d_off, outs, omegas=omegas, precision=args.precision)
             e1.record(stream)
         return fn
 
@@ -271,13 +272,12 @@ def run_ours(args, rank, world):
             e1.record(stream)
         return fn
 
-    # headline form: FP64 as the fused multi-operator pass (one kernel per step)
-    # unless --separate; mixed as one pass per operator
-    fused = args.precision == "fp64" and not args.separate
-    form = "fp64_fused" if fused else args.precision
+    # headline form: the fused multi-operator pass (one kernel per step) unless --separate
+    fused = not args.separate
+    form = args.precision + ("_fused" if fused else "")
     # autotuned launch shape for each form (cached per GPU and workload)
     tuned = {}
-    for f in ("fp64_fused", "fp64", "mixed"):
+    for f in ("fp64_fused", "fp64", "mixed_fused", "mixed"):
         if args.no_extras and f != form:
             continue
         if args.no_tune:
@@ -338,12 +338,12 @@ def run_ours(args, rank, world):
         ms_pp, _ = time_steps(plan_step(pp, "fp64"), args.steps, per_op=True)
         forms["fp64_persistent"] = {"ms_per_step": ms_pp, "value": units_per_step / (ms_pp * 1e-3)}
         pp.close()
-        for other in ("fp64_fused", "fp64", "mixed"):
+        for other in ("fp64_fused", "fp64", "mixed_fused", "mixed"):
             if other == form:
                 continue
             po = autotune.tuned_plan(basis, pa, pb, tuned[other])
-            go = api.Graph2c(po, names, omegas, d_off, outs, precision="mixed" if other == "mixed" else "fp64",
-                             fused=other == "fp64_fused")
+            go = api.Graph2c(po, names, omegas, d_off, outs, precision="mixed" if other.startswith("mixed") else "fp64",
+                             fused=other.endswith("_fused"))
             go.launch()
             torch.cuda.synchronize()
             ms_o, _ = time_steps(graph_step(go), args.steps)
@@ -355,7 +355,7 @@ def run_ours(args, rank, world):
         forms[form + "_tuned_graph"] = {"ms_per_step": ms_step, "value": units_per_step / (ms_step * 1e-3),
                                         "launch": {k: tuned[form][k] for k in
                                                    ("schedule", "threads_per_cta", "ctas_per_sm")}}
-        for f in ("fp64_fused", "mixed"):
+        for f in ("fp64_fused", "mixed_fused", "mixed"):
             forms[f + "_speedup_vs_fp64_per_class"] = ms_pc / forms[f + "_tuned_graph"]["ms_per_step"]
             forms[f + "_speedup_vs_fp64_tuned_graph"] = (forms["fp64_tuned_graph"]["ms_per_step"] /
                                                          forms[f + "_tuned_graph"]["ms_per_step"])
@@ -384,7 +384,7 @@ def run_ours(args, rank, world):
         p2 = autotune.tuned_plan(basis, d_pa, d_pb, tuned[form])
         t3 = time.perf_counter()
         if fused:
-            p2.exec_fused(names, d_off2, outs, omegas=omegas)
+            p2.exec_fused(names, d_off2, outs, omegas=omegas, precision=args.precision)
             for o, oh in zip(outs, outs_h):
                 oh.copy_(o, non_blocking=True)
         for (name, _, om), o, oh in ([] if fused else zip(OPS, outs, outs_h)):
@@ -418,7 +418,7 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "config": {"workload": workload_description(n_pairs), "pairs": n_pairs, "operators": names,
                    "precision": args.precision,
-                   "form": ("fused multi-operator FP64 pass (one kernel per step, geometry-only Q_j shared by the "
+                   "form": ("fused multi-operator pass (one kernel per step, geometry-only Q_j shared by the "
                             "five operators), autotuned launch shape, one CUDA graph per step" if fused else
                             "one pass per operator, autotuned launch shape, one CUDA graph per step"),
                    "launch": {k: tuned[form][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
@@ -436,7 +436,8 @@ def run_ours(args, rank, world):
                      "algorithmic flops are the FP64 formula count",
                      "algorithmic_flops_per_step": flops_step, "kernel_ms_per_step": kern_ms,
                      "separate_passes_flops_per_step": flops_separate,
-                     "kernel": ("k_2c_fp64_fused_persistent (5 operators in one pass)" if fused else
+                     "kernel": ("k_2c_%s_fused_persistent (5 operators in one pass)" %
+                                ("fp64" if args.precision == "fp64" else "mixed") if fused else
                                 "k_2c_%s_persistent<op> / static (5 operators per step)" %
                                 ("fp64" if args.precision == "fp64" else "mixed"))},
         "forms": forms,
@@ -558,13 +559,16 @@ def other_configs(args):
             entry[prec] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),
                            "algorithmic_tflops": flops / (ms * 1e-3) / 1e12}
         if len(ops) > 1:
-            # the same operators in one fused FP64 pass
+            # the same operators in one fused pass
             outs = [out] + [torch.empty(total, dtype=torch.float64, device="cuda") for _ in ops[1:]]
             names, oms = [n for n, _ in ops], [w for _, w in ops]
-            ms = _events_ms(lambda: plan.exec_fused(names, d_off, outs, omegas=oms), 3 if len(pa) > 1e5 else 50)
             ff = counts.workload_fused_flops(sh, pa, pb, [(api.L.OPERATORS[n], w) for n, w in ops])
-            entry["fp64_fused"] = {"ms_per_pass": ms, "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),
-                                   "algorithmic_tflops": ff / (ms * 1e-3) / 1e12}
+            for prec in precs:
+                ms = _events_ms(lambda: plan.exec_fused(names, d_off, outs, omegas=oms, precision=prec),
+                                3 if len(pa) > 1e5 else 50)
+                entry[prec + "_fused"] = {"ms_per_pass": ms,
+                                          "shell_pair_integrals_per_s": len(pa) * len(ops) / (ms * 1e-3),
+                                          "algorithmic_tflops": ff / (ms * 1e-3) / 1e12}
             del outs
         res[key] = entry
         plan.close()

@@ -211,8 +211,7 @@ int shg_graph_launch(shg_graph_t *graph, void *stream);
 void shg_graph_destroy(shg_graph_t *graph);
 
 /*
- * shg_plan_2c_exec_fused - several operators of one plan in a single FP64
- * pass.  The two-center formula of Sec. II B factors as
+ * shg_plan_2c_exec_fused - several operators of one plan in a single pass.  The two-center formula of Sec. II B factors as
  *   (a|O|b)[ma][mb] = (-1)^lb A_{la,ma} A_{lb,mb} sum_j 2^{la+lb-j} O^{(la+lb-j)} Q_j[ma][mb],
  * where Q_j (Eq. Q_matrix contracted with the weights (2j-1)!! B_{j,kappa} of
  * Eq. B) depends on the geometry only; the pass builds Q_j once per shell
@@ -220,23 +219,26 @@ void shg_graph_destroy(shg_graph_t *graph);
  * (Table S1).  The radial sums share their primitive-pair setup, erfc(wr)/r
  * is formed as 1/r - erf(wr)/r, and erf and erfc with the same omega share
  * one attenuated sum.  Results agree with shg_plan_2c_exec of each operator
- * up to the order of the floating-point sums.
+ * up to the order of the floating-point sums.  SHG_PREC_MIXED runs the same
+ * scheme in double-float (each block sum of Q_j a compensated dot product);
+ * its accuracy bar is that of the mixed single-operator pass.
  *   ops[n_ops], omegas[n_ops]  host arrays, 1 <= n_ops <= 5; each of
  *                  SHG_OP_OVERLAP, SHG_OP_COULOMB, SHG_OP_ERFC, SHG_OP_ERF,
  *                  SHG_OP_GAUSS at most once; omega rules of shg_eval_2c
+ *   precision      SHG_PREC_FP64 or SHG_PREC_MIXED
  *   d_out_offsets  device int64[n_pairs], block offsets shared by all outputs
  *   d_outs[n_ops]  host array of device output pointers (operator i writes
  *                  d_outs[i], layout of shg_eval_2c); owned by the caller
  * No screening threshold (every block is evaluated).  Asynchronous on
  * `stream`; issues a memset and kernel launches only (graph-capturable).
  * SHG_EINVAL for other operators, a repeated operator, n_ops outside 1..5,
- * a bad omega or a NULL array or output.
+ * a bad omega or precision, or a NULL array or output.
  * shg_graph_2c_create_fused - the CUDA-graph form of one fused pass (same
  * arguments; see shg_graph_2c_create for the graph's lifetime rules).
  */
-int shg_plan_2c_exec_fused(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas,
+int shg_plan_2c_exec_fused(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas, int precision,
                            const int64_t *d_out_offsets, double *const *d_outs, void *stream);
-int shg_graph_2c_create_fused(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas,
+int shg_graph_2c_create_fused(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas, int precision,
                               const int64_t *d_out_offsets, double *const *d_outs, shg_graph_t **out);
 
 /* shg_plan_destroy - free a plan (synchronises its stream first). NULL ok. */

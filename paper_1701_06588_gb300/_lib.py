@@ -45,8 +45,8 @@ SIGNATURES = [
     ("shg_family_plan_destroy", None, [_P]),
     ("shg_plan_2c_set_launch", _I, [_P, _I, _I]),
     ("shg_graph_2c_create", _I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
-    ("shg_plan_2c_exec_fused", _I, [_P, _I, _P, _P, _P, _P, _P]),
-    ("shg_graph_2c_create_fused", _I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("shg_plan_2c_exec_fused", _I, [_P, _I, _P, _P, _I, _P, _P, _P]),
+    ("shg_graph_2c_create_fused", _I, [_P, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
     ("shg_graph_launch", _I, [_P, _P]),
     ("shg_graph_destroy", None, [_P]),
     ("shg_eval_3c_aab", _I, [_P, _P, _L, _P, _P, _P, _I, _D, _P, _P, _P]),
@@ -204,16 +204,16 @@ def _op_arrays(ops, omegas, d_outs):
     return n, ops_a, om_a, outs_a
 
 
-def shg_plan_2c_exec_fused(plan, ops, omegas, d_out_offsets, d_outs, stream):
+def shg_plan_2c_exec_fused(plan, ops, omegas, precision, d_out_offsets, d_outs, stream):
     n, ops_a, om_a, outs_a = _op_arrays(ops, omegas, d_outs)
-    return check(load().shg_plan_2c_exec_fused(plan, n, _ptr(ops_a), _ptr(om_a), _ptr(d_out_offsets),
+    return check(load().shg_plan_2c_exec_fused(plan, n, _ptr(ops_a), _ptr(om_a), precision, _ptr(d_out_offsets),
                                                ctypes.cast(outs_a, ctypes.c_void_p), stream))
 
 
-def shg_graph_2c_create_fused(plan, ops, omegas, d_out_offsets, d_outs):
+def shg_graph_2c_create_fused(plan, ops, omegas, precision, d_out_offsets, d_outs):
     n, ops_a, om_a, outs_a = _op_arrays(ops, omegas, d_outs)
     h = _P()
-    check(load().shg_graph_2c_create_fused(plan, n, _ptr(ops_a), _ptr(om_a), _ptr(d_out_offsets),
+    check(load().shg_graph_2c_create_fused(plan, n, _ptr(ops_a), _ptr(om_a), precision, _ptr(d_out_offsets),
                                            ctypes.cast(outs_a, ctypes.c_void_p), ctypes.byref(h)))
     return h.value
 

@@ -107,13 +107,13 @@ class Plan2c:
                            out_offsets, out, _stream(stream))
         return out
 
-    def exec_fused(self, ops, out_offsets, outs, omegas=None, stream=None):
+    def exec_fused(self, ops, out_offsets, outs, omegas=None, precision="fp64", stream=None):
         """Several operators (overlap, coulomb, erfc, erf, gauss; each at most
-        once) in one FP64 pass sharing the geometry-only angular part;
-        outs[i] receives operator ops[i] in the layout of exec."""
+        once) in one pass sharing the geometry-only angular part; outs[i]
+        receives operator ops[i] in the layout of exec."""
         omegas = [0.0] * len(ops) if omegas is None else [float(w) for w in omegas]
-        L.shg_plan_2c_exec_fused(self.handle, [_op(o) for o in ops], omegas, out_offsets, list(outs),
-                                 _stream(stream))
+        L.shg_plan_2c_exec_fused(self.handle, [_op(o) for o in ops], omegas, _prec(precision), out_offsets,
+                                 list(outs), _stream(stream))
         return outs
 
     def close(self):
@@ -266,10 +266,9 @@ class Graph2c:
         self.outs = list(outs)
         self.out_offsets = out_offsets
         if fused:
-            if _prec(precision) != L.SHG_PREC_FP64:
-                raise ValueError("the fused pass is FP64 only")
             self.handle = L.shg_graph_2c_create_fused(plan.handle, [_op(o) for o in ops],
-                                                      [float(w) for w in omegas], out_offsets, self.outs)
+                                                      [float(w) for w in omegas], _prec(precision), out_offsets,
+                                                      self.outs)
         else:
             self.handle = L.shg_graph_2c_create(plan.handle, [_op(o) for o in ops], [float(w) for w in omegas],
                                                 _prec(precision), out_offsets, self.outs)

@@ -53,12 +53,12 @@ def _save(db):
 
 def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp64", reps=3, force=False):
     """Best (schedule, threads_per_cta, ctas_per_sm) for this workload; times in ms per pass over `ops`.
-    precision "fp64_fused" tunes the fused multi-operator FP64 pass (one exec_fused per pass)."""
-    fused = precision == "fp64_fused"
+    precision "fp64_fused" / "mixed_fused" tunes the fused multi-operator pass (one exec_fused per pass)."""
+    fused = precision.endswith("_fused")
 
     def one_pass(plan):
         if fused:
-            plan.exec_fused(ops, out_offsets, outs, omegas=omegas)
+            plan.exec_fused(ops, out_offsets, outs, omegas=omegas, precision=precision[:-len("_fused")])
         else:
             for op, om, o in zip(ops, omegas, outs):
                 plan.exec(op, out_offsets, o, omega=om, precision=precision)

@@ -1129,10 +1129,10 @@ static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const i
 }
 
 // Arguments of a fused pass: the operators are checked (each of overlap,
-// 1/r, erfc, erf and the Gaussian at most once, FP64), outputs placed by
-// operator id.
-static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
-                      double *const *outs, ArgsFused &a)
+// 1/r, erfc, erf and the Gaussian at most once, in the given precision),
+// outputs placed by operator id.
+static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
+                      const int64_t *off, double *const *outs, ArgsFused &a)
 {
     if (!p) return fail(SHG_EINVAL, "plan is NULL");
     if (n_ops < 1 || n_ops > 5) return fail(SHG_EINVAL, "n_ops must be 1..5 (got %d)", n_ops);
@@ -1143,7 +1143,7 @@ static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *om
         const int op = ops[i];
         if (op < SHG_OP_OVERLAP || op > SHG_OP_GAUSS)
             return fail(SHG_EINVAL, "the fused pass takes overlap, 1/r, erfc, erf and the Gaussian only (got %d)", op);
-        int r = check_op(op, omegas[i], SHG_PREC_FP64);
+        int r = check_op(op, omegas[i], precision);
         if (r) return r;
         if (a.out[op]) return fail(SHG_EINVAL, "operator %d listed twice", op);
         if (!outs[i]) return fail(SHG_EINVAL, "NULL output for operator %d", op);
@@ -1157,12 +1157,12 @@ static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *om
     return SHG_OK;
 }
 
-int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
-                           double *const *outs, void *stream)
+int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
+                           const int64_t *off, double *const *outs, void *stream)
 {
     g_err.clear();
     ArgsFused a;
-    int r = fused_args(p, n_ops, ops, omegas, off, outs, a);
+    int r = fused_args(p, n_ops, ops, omegas, precision, off, outs, a);
     if (r) return r;
     if (p->d.n_pairs == 0 || p->d.n_tiles == 0) return SHG_OK;
     r = current_device_matches(p->d.basis->device);
@@ -1170,6 +1170,44 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     const DeviceTables *t = device_tables();
     if (!t) return SHG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    if (precision == SHG_PREC_MIXED) {
+        ArgsMixFused m;
+        m.shells = p->d.basis->shells;
+        m.prims = p->d.basis->mprims;
+        m.centers = p->d.basis->mcenters;
+        m.pair_a = p->d.pair_a;
+        m.pair_b = p->d.pair_b;
+        m.perm = p->d.perm;
+        m.tiles = p->d.tiles;
+        m.out_off = reinterpret_cast<const long long *>(off);
+        for (int i = 0; i < 5; ++i) m.out[i] = a.out[i];
+        m.w_erf = split2(a.w_erf);
+        m.w_erf2 = split2((long double)a.w_erf * a.w_erf);
+        m.w_erfc = split2(a.w_erfc);
+        m.w_erfc2 = split2((long double)a.w_erfc * a.w_erfc);
+        m.w_gauss = split2(a.w_gauss);
+        m.share_att = a.share_att;
+        m.boys = t->boys_mix;
+        m.boys_e = t->boys_e_mix;
+        m.km = consts_mix();
+        if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+            m.tile_begin = 0;
+            m.tile_end = p->d.n_tiles;
+            m.counter = p->d.counter;
+            SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm), true, s,
+                                           p->d.threads));
+        } else {
+            m.counter = nullptr;
+            for (int cls = 0; cls < kNClass; ++cls) {
+                m.tile_begin = p->d.class_tile_begin[cls];
+                m.tile_end = p->d.class_tile_begin[cls + 1];
+                if (m.tile_end <= m.tile_begin) continue;
+                SHG_CUDA(launch_2c_mixed_fused(m, 0, false, s, p->d.threads));
+            }
+        }
+        return SHG_OK;
+    }
     a.shells = p->d.basis->shells;
     a.prims = p->d.basis->prims;
     a.centers = p->d.basis->centers;
@@ -1199,17 +1237,17 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     return SHG_OK;
 }
 
-int shg_graph_2c_create_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, const int64_t *off,
-                              double *const *outs, shg_graph_t **out)
+int shg_graph_2c_create_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
+                              const int64_t *off, double *const *outs, shg_graph_t **out)
 {
     g_err.clear();
     if (!out) return fail(SHG_EINVAL, "out is NULL");
     *out = nullptr;
     ArgsFused chk;
-    int r = fused_args(p, n_ops, ops, omegas, off, outs, chk);
+    int r = fused_args(p, n_ops, ops, omegas, precision, off, outs, chk);
     if (r) return r;
-    return capture_graph([&](cudaStream_t s) { return shg_plan_2c_exec_fused(p, n_ops, ops, omegas, off, outs, s); },
-                         out);
+    return capture_graph(
+        [&](cudaStream_t s) { return shg_plan_2c_exec_fused(p, n_ops, ops, omegas, precision, off, outs, s); }, out);
 }
 
 int shg_eval_2c(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int op, double omega,

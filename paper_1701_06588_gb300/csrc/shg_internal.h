@@ -277,6 +277,25 @@ struct ArgsMix {
     ConstsMix km;
 };
 
+// Fused multi-operator pass in double-float (outputs as ArgsFused).
+struct ArgsMixFused {
+    const ShellRec *shells;
+    const MixPrim *prims;
+    const MixCenter *centers;
+    const int32_t *pair_a, *pair_b;
+    const int32_t *perm;
+    const Tile *tiles;
+    int tile_begin, tile_end;
+    int *counter;
+    const long long *out_off;
+    double *out[5];                     // indexed by OP_OVERLAP .. OP_GAUSS
+    float2 w_erf, w_erf2, w_erfc, w_erfc2, w_gauss;   // omega (and omega^2) as double-float
+    int share_att;
+    const float4 *boys;
+    const float2 *boys_e;
+    ConstsMix km;
+};
+
 // Arguments of the three-index kernels (by value).
 struct Args3c {
     const ShellRec *orb_shells, *aux_shells;
@@ -311,6 +330,9 @@ cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, 
 cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s,
                             int threads = 128);
 int persistent_grid_2c_mixed(int op, int threads = 128, int ctas_per_sm = 0);
+cudaError_t launch_2c_mixed_fused(const ArgsMixFused &args, int grid, bool persistent, cudaStream_t s,
+                                  int threads);
+int persistent_grid_2c_mixed_fused(int threads = 128, int ctas_per_sm = 0);
 int persistent_grid_2c_grad(int op, int precision);
 int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,

@@ -123,41 +123,106 @@ __device__ __forceinline__ void boys_all_mix(df T, int kmax, const float4 *__res
     for (int n = kmax; n > 0; --n) F[n - 1] = mul(add(mul(twoT, F[n]), e), ldf(k.inv_int[2 * n - 1]));
 }
 
+// Common part of one primitive pair: c, 1/sqrt(c), 1/c, rho, T and the
+// order factors hp[j] = base (2 rho)^-j (-1)^{kmax-j}.
+struct MixPair {
+    df c, rc, ic, rho, T;
+};
+
+template <int J>
+__device__ __forceinline__ MixPair mix_setup(const MixPrim &pa, const MixPrim &pb, df R2, int la, int lb, df (&hp)[J])
+{
+    const int kmax = la + lb;
+    MixPair m;
+    const df a = ldf(pa.alpha), b = ldf(pb.alpha);
+    m.c = add(a, b);
+    m.rc = rsqrt_df(m.c);
+    m.ic = mul(m.rc, m.rc);
+    m.rho = mul(mul(a, b), m.ic);
+    m.T = mul(m.rho, R2);
+    df base = mul(ldf(pa.wN), powi_df(mul(b, m.ic), la));
+    base = mul(base, mul(ldf(pb.wN), powi_df(mul(a, m.ic), lb)));
+    const df h = scale2(mul(mul(m.c, ldf(pa.inv_alpha)), ldf(pb.inv_alpha)), 0.5f);   // 1/(2 rho)
+    hp[0] = (kmax & 1) ? neg(base) : base;
+#pragma unroll
+    for (int j = 1; j < J; ++j) hp[j] = neg(mul(hp[j - 1], h));
+    return m;
+}
+
+// the operator parts: S_j += hp[j] X_k
+template <int J>
+__device__ __forceinline__ void mix_overlap(const MixPair &m, const df (&hp)[J], const ConstsMix &km, df (&S)[J])
+{
+    const df X = mul(mul(ldf(km.pi32), mul(m.ic, m.rc)), exp_neg_df(m.T, km));
+#pragma unroll
+    for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(hp[j], X));
+}
+
+template <int J>
+__device__ __forceinline__ void mix_gauss(const MixPair &m, const df (&hp)[J], df omega, int kmax, const ConstsMix &km,
+                                          df (&S)[J])
+{
+    const df d = add(m.rho, omega);
+    const df rd = rsqrt_df(d);
+    const df id = mul(rd, rd);
+    const df wd = mul(omega, id);                                            // omega / (rho + omega)
+    df X = mul(mul(ldf(km.pi3), mul(mul(m.ic, m.rc), mul(id, rd))), exp_neg_df(mul(m.T, wd), km));
+    X = mul(X, powi_df(wd, kmax - J + 1));                                  // X_k at k = kmax - J + 1
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+        S[j] = add(S[j], mul(hp[j], X));
+        X = mul(X, wd);
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void mix_coulomb(const MixPair &m, const df (&hp)[J], df pre, int kmax, const float4 *boys,
+                                            const float2 *boys_e, const ConstsMix &km, df (&S)[J])
+{
+    df F[J];
+    boys_top_mix<J>(m.T, kmax, boys, boys_e, km, F);
+#pragma unroll
+    for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(mul(hp[j], pre), F[j]));
+}
+
+// attenuated part omega/sqrt(omega^2+rho) (-omega^2 rho/(omega^2+rho))^k F_k(omega^2 T/(omega^2+rho)),
+// subtracted when negate (the erfc share of a single-operator pass)
+template <int J>
+__device__ __forceinline__ void mix_attenuated(const MixPair &m, const df (&hp)[J], df pre, df omega, df omega2,
+                                               bool negate, int kmax, const float4 *boys, const float2 *boys_e,
+                                               const ConstsMix &km, df (&S)[J])
+{
+    const df rw = rsqrt_df(add(omega2, m.rho));
+    const df s = mul(omega2, mul(rw, rw));                                   // omega^2 / (omega^2 + rho)
+    df F[J];
+    boys_top_mix<J>(mul(s, m.T), kmax, boys, boys_e, km, F);
+    df X = mul(mul(pre, mul(omega, rw)), powi_df(s, kmax - J + 1));
+    if (negate) X = neg(X);
+#pragma unroll
+    for (int j = J - 1; j >= 0; --j) {
+        S[j] = add(S[j], mul(mul(hp[j], X), F[j]));
+        X = mul(X, s);
+    }
+}
+
+__device__ __forceinline__ df mix_boys_prefactor(const MixPair &m, const MixPrim &pa, const MixPrim &pb,
+                                                 const ConstsMix &km)
+{
+    return mul(mul(ldf(km.two_pi52), m.rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
+}
+
 // S_j += (-1)^k base (2 rho)^-j X_k for one primitive pair, k = la+lb-j.
 template <int OP, int J>
 __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim &pb, df R2, int la, int lb,
                                                const ArgsMix &g, df (&S)[J])
 {
     const int kmax = la + lb;
-    const df a = ldf(pa.alpha), b = ldf(pb.alpha);
-    const df c = add(a, b);
-    const df rc = rsqrt_df(c);
-    const df ic = mul(rc, rc);
-    const df rho = mul(mul(a, b), ic);
-    const df T = mul(rho, R2);
-    df base = mul(ldf(pa.wN), powi_df(mul(b, ic), la));
-    base = mul(base, mul(ldf(pb.wN), powi_df(mul(a, ic), lb)));
-    const df h = scale2(mul(mul(c, ldf(pa.inv_alpha)), ldf(pb.inv_alpha)), 0.5f);   // 1/(2 rho)
     df hp[J];                       // base (2 rho)^-j (-1)^{kmax-j}
-    hp[0] = (kmax & 1) ? neg(base) : base;
-#pragma unroll
-    for (int j = 1; j < J; ++j) hp[j] = neg(mul(hp[j - 1], h));
+    const MixPair m = mix_setup<J>(pa, pb, R2, la, lb, hp);
     if (OP == OP_OVERLAP) {
-        const df X = mul(mul(ldf(g.km.pi32), mul(ic, rc)), exp_neg_df(T, g.km));
-#pragma unroll
-        for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(hp[j], X));
+        mix_overlap<J>(m, hp, g.km, S);
     } else if (OP == OP_GAUSS) {
-        const df d = add(rho, ldf(g.omega));
-        const df rd = rsqrt_df(d);
-        const df id = mul(rd, rd);
-        const df wd = mul(ldf(g.omega), id);                               // omega / (rho + omega)
-        df X = mul(mul(ldf(g.km.pi3), mul(mul(ic, rc), mul(id, rd))), exp_neg_df(mul(T, wd), g.km));
-        X = mul(X, powi_df(wd, kmax - J + 1));                            // X_k at k = kmax - J + 1
-#pragma unroll
-        for (int j = J - 1; j >= 0; --j) {
-            S[j] = add(S[j], mul(hp[j], X));
-            X = mul(X, wd);
-        }
+        mix_gauss<J>(m, hp, ldf(g.omega), kmax, g.km, S);
     } else if (OP == OP_GCOUL) {
         // exp(-w r^2)/r without the (-rho)^k carried by hp:
         //   X_k = (pi/c)^{3/2} (2 pi/d) exp(-w T/d) sum_i C(k,i) (w/d)^{k-i} (rho/d)^i F_i(T rho/d),
@@ -165,14 +230,15 @@ __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim 
         // v_i <- (w/d) v_i + (rho/d) v_{i+1} (kmin times over F_0..F_kmax, then
         // over a J-wide register window)
         const int kmin = kmax - J + 1;
-        const df rd = rsqrt_df(add(rho, ldf(g.omega)));
+        const df rd = rsqrt_df(add(m.rho, ldf(g.omega)));
         const df id = mul(rd, rd);
-        const df sw = mul(ldf(g.omega), id), sr = mul(rho, id);
-        const df pre = mul(mul(ldf(g.km.pi32), mul(ic, rc)), mul(mul(ldf(g.km.two_pi), id), exp_neg_df(mul(T, sw), g.km)));
+        const df sw = mul(ldf(g.omega), id), sr = mul(m.rho, id);
+        const df pre = mul(mul(ldf(g.km.pi32), mul(m.ic, m.rc)),
+                           mul(mul(ldf(g.km.two_pi), id), exp_neg_df(mul(m.T, sw), g.km)));
         df F[kBoysN];
-        boys_all_mix(mul(T, sr), kmax, g.boys, g.boys_e, g.km, F);
-        for (int m = 1; m <= kmin; ++m)
-            for (int i = 0; i <= kmax - m; ++i) F[i] = add(mul(sw, F[i]), mul(sr, F[i + 1]));
+        boys_all_mix(mul(m.T, sr), kmax, g.boys, g.boys_e, g.km, F);
+        for (int mm = 1; mm <= kmin; ++mm)
+            for (int i = 0; i <= kmax - mm; ++i) F[i] = add(mul(sw, F[i]), mul(sr, F[i + 1]));
         df v[J];
 #pragma unroll
         for (int i = 0; i < J; ++i) v[i] = F[i];
@@ -184,26 +250,10 @@ __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim 
             S[J - 1 - t] = add(S[J - 1 - t], mul(hp[J - 1 - t], mul(pre, v[0])));
         }
     } else {
-        const df pre = mul(mul(ldf(g.km.two_pi52), rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
-        if (OP == OP_COULOMB || OP == OP_ERFC) {
-            df F[J];
-            boys_top_mix<J>(T, kmax, g.boys, g.boys_e, g.km, F);
-#pragma unroll
-            for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(mul(hp[j], pre), F[j]));
-        }
-        if (OP == OP_ERF || OP == OP_ERFC) {
-            const df rw = rsqrt_df(add(ldf(g.omega2), rho));
-            const df s = mul(ldf(g.omega2), mul(rw, rw));                  // omega^2 / (omega^2 + rho)
-            df F[J];
-            boys_top_mix<J>(mul(s, T), kmax, g.boys, g.boys_e, g.km, F);
-            df X = mul(mul(pre, mul(ldf(g.omega), rw)), powi_df(s, kmax - J + 1));
-            if (OP == OP_ERFC) X = neg(X);
-#pragma unroll
-            for (int j = J - 1; j >= 0; --j) {
-                S[j] = add(S[j], mul(mul(hp[j], X), F[j]));
-                X = mul(X, s);
-            }
-        }
+        const df pre = mix_boys_prefactor(m, pa, pb, g.km);
+        if (OP == OP_COULOMB || OP == OP_ERFC) mix_coulomb<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, S);
+        if (OP == OP_ERF || OP == OP_ERFC)
+            mix_attenuated<J>(m, hp, pre, ldf(g.omega), ldf(g.omega2), OP == OP_ERFC, kmax, g.boys, g.boys_e, g.km, S);
     }
 }
 
@@ -283,6 +333,154 @@ __device__ void pair_2c_mix(const ArgsMix &g, int p)
 #pragma unroll
     for (int j = 0; j < J; ++j) Sr[j] = S[j];
     assemble_mix(g, p, la, lb, vx, vy, vz, Sr, J);
+}
+
+// ------------------------------------------------------------------------- //
+// Fused multi-operator pass in double-float (the FP64 fused pass of          //
+// shg_fused.cu with this file's arithmetic): per primitive pair the common   //
+// setup once and one sum per requested operator (erfc = 1/r - attenuated),   //
+// then Q_j = sum_{e in block j} A_a (2j-1)!! B_{j,kappa} W_a[e] A_b W_b[e]    //
+// by a compensated dot product per block, read once for all operators.      //
+// ------------------------------------------------------------------------- //
+__device__ __noinline__ void assemble_mix_fused(const ArgsMixFused &g, int p, int la, int lb, df vx, df vy, df vz,
+                                                const df (*S)[kJmax], int J)
+{
+    df Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics_mix(vx, vy, vz, la > lb ? la : lb, g.km, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    const int JJ = J * J;
+    df Ub[2 * kLmax2c + 1][kJmax * kJmax];
+    for (int mb = -lb; mb <= lb; ++mb) {
+        df *ub = Ub[mb + lb];
+        w_row_mix_rt(Rc, Rs, lb, mb, J, ub);
+        const df Ab = ldf(g.km.A[lb][mb < 0 ? -mb : mb]);
+        for (int e = 0; e < JJ; ++e) ub[e] = mul(ub[e], Ab);
+    }
+    const long long o = g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        df ua[kJmax * kJmax];
+        w_row_mix_rt(Rc, Rs, la, ma, J, ua);
+        df Aa = ldf(g.km.A[la][ma < 0 ? -ma : ma]);
+        if (lb & 1) Aa = neg(Aa);
+        for (int j = 0; j < J; ++j)
+            for (int kp = 0; kp <= j; ++kp) {
+                const df gv = mul(Aa, ldf(g.km.jB[j][kp]));
+                const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+                ua[e0] = mul(ua[e0], gv);
+                if (kp) ua[e0 + 1] = mul(ua[e0 + 1], gv);
+            }
+        for (int mb = -lb; mb <= lb; ++mb) {
+            const df *ub = Ub[mb + lb];
+            df Q[kJmax];
+            for (int j = 0; j < J; ++j) {
+                // compensated dot product over block j (Dot2 of Ogita, Rump and Oishi)
+                float sh = 0.0f, sl = 0.0f;
+                for (int e = j * j; e < (j + 1) * (j + 1); ++e) {
+                    const float pr = ua[e].hi * ub[e].hi;
+                    float ep = fmaf(ua[e].hi, ub[e].hi, -pr);
+                    ep = fmaf(ua[e].hi, ub[e].lo, ep);
+                    ep = fmaf(ua[e].lo, ub[e].hi, ep);
+                    const df t = two_sum(sh, pr);
+                    sh = t.hi;
+                    sl += t.lo + ep;
+                }
+                Q[j] = fast_two_sum(sh, sl);
+            }
+            const long long idx = o + (ma + la) * nb + (mb + lb);
+            for (int op = 0; op < 5; ++op) {
+                if (!g.out[op]) continue;
+                df s = mul(S[op][0], Q[0]);
+                for (int j = 1; j < J; ++j) s = add(s, mul(S[op][j], Q[j]));
+                g.out[op][idx] = to_double(s);
+            }
+        }
+    }
+}
+
+template <int J>
+__device__ void pair_2c_mix_fused(const ArgsMixFused &g, int p)
+{
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l, kmax = la + lb;
+    const MixCenter A = g.centers[sa.center];
+    const MixCenter B = g.centers[sb.center];
+    const df vx = sub(ldf(A.x), ldf(B.x)), vy = sub(ldf(A.y), ldf(B.y)), vz = sub(ldf(A.z), ldf(B.z));
+    const df R2 = add(add(mul(vx, vx), mul(vy, vy)), mul(vz, vz));
+    const bool f_ov = g.out[OP_OVERLAP] != nullptr;
+    const bool f_ga = g.out[OP_GAUSS] != nullptr;
+    const bool f_co = g.out[OP_COULOMB] != nullptr || g.out[OP_ERFC] != nullptr;
+    const bool f_er = g.out[OP_ERF] != nullptr;
+    const bool f_x = g.out[OP_ERFC] != nullptr && !(f_er && g.share_att);
+
+    df Sov[J], Sco[J], Sx[J], Ser[J], Sga[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) Sov[j] = Sco[j] = Sx[j] = Ser[j] = Sga[j] = df_f(0.0f);
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        const MixPrim pa = g.prims[sa.prim_off + ia], pb = g.prims[sb.prim_off + ib];
+        df hp[J];
+        const MixPair m = mix_setup<J>(pa, pb, R2, la, lb, hp);
+        if (f_ov) mix_overlap<J>(m, hp, g.km, Sov);
+        if (f_ga) mix_gauss<J>(m, hp, ldf(g.w_gauss), kmax, g.km, Sga);
+        if (f_co || f_er || f_x) {
+            const df pre = mix_boys_prefactor(m, pa, pb, g.km);
+            if (f_co) mix_coulomb<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, Sco);
+            if (f_er)
+                mix_attenuated<J>(m, hp, pre, ldf(g.w_erf), ldf(g.w_erf2), false, kmax, g.boys, g.boys_e, g.km, Ser);
+            if (f_x)
+                mix_attenuated<J>(m, hp, pre, ldf(g.w_erfc), ldf(g.w_erfc2), false, kmax, g.boys, g.boys_e, g.km, Sx);
+        }
+    }
+    df Sr[5][kJmax];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        Sr[OP_OVERLAP][j] = Sov[j];
+        Sr[OP_COULOMB][j] = Sco[j];
+        Sr[OP_ERFC][j] = sub(Sco[j], f_x ? Sx[j] : Ser[j]);
+        Sr[OP_ERF][j] = Ser[j];
+        Sr[OP_GAUSS][j] = Sga[j];
+    }
+    assemble_mix_fused(g, p, la, lb, vx, vy, vz, Sr, J);
+}
+
+__device__ __forceinline__ void run_tile_mix_fused(const ArgsMixFused &g, const Tile &tl, int lane)
+{
+    if (lane >= tl.count) return;
+    const int p = g.perm[tl.start + lane];
+    const int la = tl.cls / (kLmax2c + 1), lb = tl.cls % (kLmax2c + 1);
+    switch ((la < lb ? la : lb) + 1) {
+    case 1: pair_2c_mix_fused<1>(g, p); break;
+    case 2: pair_2c_mix_fused<2>(g, p); break;
+    case 3: pair_2c_mix_fused<3>(g, p); break;
+    case 4: pair_2c_mix_fused<4>(g, p); break;
+    case 5: pair_2c_mix_fused<5>(g, p); break;
+    case 6: pair_2c_mix_fused<6>(g, p); break;
+    default: pair_2c_mix_fused<7>(g, p); break;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_2c_mixed_fused_persistent(const ArgsMixFused g)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(g.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (t >= g.tile_end) break;
+        run_tile_mix_fused(g, g.tiles[t], lane);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(128) k_2c_mixed_fused_static(const ArgsMixFused g)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int t = g.tile_begin + warp;
+    if (t >= g.tile_end) return;
+    run_tile_mix_fused(g, g.tiles[t], lane);
 }
 
 template <int OP>
@@ -371,6 +569,31 @@ cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent,
     case OP_GCOUL: return launch_mix_op<OP_GCOUL>(a, grid, threads, persistent, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_2c_mixed_fused(const ArgsMixFused &a, int grid, bool persistent, cudaStream_t s, int threads)
+{
+    if (persistent) {
+        k_2c_mixed_fused_persistent<<<grid, threads, 0, s>>>(a);
+    } else {
+        const int tiles = a.tile_end - a.tile_begin;
+        if (tiles <= 0) return cudaSuccess;
+        const int wpb = threads / 32;
+        k_2c_mixed_fused_static<<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int persistent_grid_2c_mixed_fused(int threads, int ctas_per_sm)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent, threads, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
+    return (sms > 0 ? sms : 1) * per;
 }
 
 int persistent_grid_2c_mixed(int op, int threads, int ctas_per_sm)

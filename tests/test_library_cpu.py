@@ -71,10 +71,10 @@ def test_null_and_range_arguments(lib):
     assert lib.shg_pair_offsets(None, 1, None, None, None) == L.SHG_EINVAL
     ops = (ctypes.c_int * 2)(1, 2)
     om = (ctypes.c_double * 2)(0.0, 0.1)
-    assert lib.shg_plan_2c_exec_fused(None, 2, ops, om, None, None, None) == L.SHG_EINVAL
+    assert lib.shg_plan_2c_exec_fused(None, 2, ops, om, 0, None, None, None) == L.SHG_EINVAL
     assert "plan is NULL" in L.shg_last_error()
-    assert lib.shg_graph_2c_create_fused(None, 2, ops, om, None, None, ctypes.byref(ctypes.c_void_p())) == L.SHG_EINVAL
-    assert lib.shg_graph_2c_create_fused(None, 2, ops, om, None, None, None) == L.SHG_EINVAL
+    assert lib.shg_graph_2c_create_fused(None, 2, ops, om, 1, None, None, ctypes.byref(ctypes.c_void_p())) == L.SHG_EINVAL
+    assert lib.shg_graph_2c_create_fused(None, 2, ops, om, 0, None, None, None) == L.SHG_EINVAL
     assert lib.shg_debug_boys(10, None, 99, None, None) == L.SHG_EINVAL
     assert "nmax" in L.shg_last_error()
     lib.shg_basis_destroy(None)
