@@ -378,16 +378,24 @@ static void make_ranks(int schedule, std::vector<int> &rank, std::vector<int> &i
             return (x % kKbins2c) > (y % kKbins2c);
         });
     } else {
-        // class-major, classes by decreasing estimated cost of their heaviest
-        // pairs, Ka*Kb descending inside a class: longest tiles first, and the
-        // warps resident on one SM mostly run one class's code at a time
-        // (instruction-cache locality)
+        // class-major; classes grouped by J = min(la, lb) + 1 (descending), then by
+        // decreasing estimated cost of their heaviest pairs; Ka*Kb descending
+        // inside a class.  Longest tiles come first (J-major is close to cost
+        // order), and the warps resident on one SM mostly run one J
+        // instantiation at a time (instruction-cache locality)
         std::vector<double> ccost(kNClass);
-        for (int cls = 0; cls < kNClass; ++cls)
-            ccost[cls] = class_cost(cls / (kLmax2c + 1), cls % (kLmax2c + 1), 64);
+        std::vector<int> cJ(kNClass);
+        for (int cls = 0; cls < kNClass; ++cls) {
+            const int la = cls / (kLmax2c + 1), lb = cls % (kLmax2c + 1);
+            ccost[cls] = class_cost(la, lb, 64);
+            cJ[cls] = std::min(la, lb) + 1;
+        }
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
             const int cx = x / kKbins2c, cy = y / kKbins2c;
-            if (cx != cy) return ccost[cx] > ccost[cy] || (ccost[cx] == ccost[cy] && cx < cy);
+            if (cx != cy) {
+                if (cJ[cx] != cJ[cy]) return cJ[cx] > cJ[cy];
+                return ccost[cx] > ccost[cy] || (ccost[cx] == ccost[cy] && cx < cy);
+            }
             return (x % kKbins2c) > (y % kKbins2c);
         });
     }
