@@ -4,9 +4,11 @@
 One step = every two-center block of the 200,000-pair workload (l <= 4,
 K = 1..8, exponents 0.05..500, separations 0..10 bohr, seed 1) for all five
 operators (overlap, 1/r, erfc(0.11 r)/r, erf(0.11 r)/r, exp(-r^2)), i.e.
-1,000,000 shell-pair integrals, FP64, one persistent launch per operator.
+1,000,000 shell-pair integrals, FP64: one fused persistent launch for the
+five operators (--separate: one persistent launch per operator).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|mixed] [--separate] [--configs]
 
 N > 1 runs under torch.distributed.run, one rank per GPU: every rank owns an
 independent copy of the workload (weak scaling, no data-path collective).
