@@ -62,11 +62,12 @@ __device__ __forceinline__ void boys_head(double T, int kmax, const double *__re
     }
 }
 
+// e returns exp(-T) as the head computes it (0 for T >= kBoysTmax, where exp(-T) < 1e-52).
 template <int J>
 __device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
-                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+                                         const double *__restrict__ etab, const Consts &k, double (&F)[J], double &e)
 {
-    double f, e;
+    double f;
     boys_head(T, kmax, tab, etab, k, f, e);
     // downward recursion F_{k-1} = (2T F_k + exp(-T)) / (2k-1), shared by both branches
     F[0] = f;
@@ -76,6 +77,14 @@ __device__ __forceinline__ void boys_top(double T, int kmax, const double *__res
         const int kk = kmax - j + 1;
         F[j] = fma(twoT, F[j - 1], e) * k.inv_int[2 * kk - 1];
     }
+}
+
+template <int J>
+__device__ __forceinline__ void boys_top(double T, int kmax, const double *__restrict__ tab,
+                                         const double *__restrict__ etab, const Consts &k, double (&F)[J])
+{
+    double e;
+    boys_top<J>(T, kmax, tab, etab, k, F, e);
 }
 
 // All of F_0 .. F_kmax (F[n] = F_n, runtime kmax <= kBoysN - 1): the same head

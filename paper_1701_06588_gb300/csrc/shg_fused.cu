@@ -75,9 +75,13 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
         const double rho = pa.alpha * pb.alpha * ic;
         const double T = rho * R2;
         const double mrk = powi(-rho, kmin);
+        // Boys head of the 1/r sum first: it also yields exp(-T) for the overlap
+        // (0 for T >= kBoysTmax, where the overlap term is below e^-120 of its prefactor)
+        double Fc[J], eT = 0.0;
+        if (f_co) boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, Fc, eT);
         if (f_ov) {
             // (pi/c)^{3/2} exp(-T) (-rho)^k
-            double t = w * kPi32 * ic * rc * exp(-T) * mrk;
+            double t = w * kPi32 * ic * rc * (f_co ? eT : exp(-T)) * mrk;
 #pragma unroll
             for (int j = J - 1; j >= 0; --j) {
                 Oov[j] += t;
@@ -100,12 +104,10 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
             // 2 pi^{5/2} / (alpha beta sqrt(c)) times the Boys sums
             const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
             if (f_co) {
-                double F[J];
-                boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, F);
                 double t = pre * mrk;
 #pragma unroll
                 for (int j = J - 1; j >= 0; --j) {
-                    Oco[j] = fma(t, F[j], Oco[j]);
+                    Oco[j] = fma(t, Fc[j], Oco[j]);
                     t *= -rho;
                 }
             }
