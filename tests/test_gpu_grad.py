@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1701_06588_gb300 import workloads as W
-from tests.parity import normalised
+from tests.parity import normalised, vjp_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -24,8 +24,9 @@ def shg():
 
 
 def _oracle_vjp(shells, pa, pb, op, omega, w):
-    """sum_e W_e dI_e/dR_a from the oracle Jacobian, and the bar scale
-    sum_e |W_e| |dI_e/dR_a| evaluated with |N c| (conditioning of the sum)."""
+    """sum_e W_e dI_e/dR_a from the oracle Jacobian, and the element-wise bar
+    scale sum_e |W_e| |dI_e/dR_a| with the |N c| Jacobian (conditioning of the
+    dot product and of the contractions in it)."""
     shn, sha = normalised(shells)
     J, off, sz = oracle.eval_2c_grad(shn, pa, pb, op, omega, center="A", normalize=False)
     if op == oracle.OP_ERFC:
@@ -34,16 +35,7 @@ def _oracle_vjp(shells, pa, pb, op, omega, w):
         Ja = np.abs(J1) + np.abs(J2)
     else:
         Ja, _, _ = oracle.eval_2c_grad(sha, pa, pb, op, omega, center="A", normalize=False)
-        Ja = np.abs(Ja)
-    g = np.zeros((len(pa), 3))
-    s = np.zeros((len(pa), 3))
-    for p in range(len(pa)):
-        blk = J[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
-        ablk = Ja[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
-        wp = w[off[p]: off[p] + sz[p]]
-        g[p] = blk @ wp
-        s[p] = (ablk.max(axis=1, keepdims=True) * np.ones_like(ablk)) @ np.abs(wp)
-    return g, s
+    return vjp_reference(J, Ja, off, sz, w)
 
 
 @pytest.mark.parametrize("name,n", [("c5_grad_500k_l5_k12", 1200), ("c2_200k_l4_k8", 800)])
@@ -119,19 +111,10 @@ def test_autograd_function_matches_finite_differences(shg):
 
 
 def _oracle_vjp_3c(shells, ta, tt, tb, w):
-    from tests.parity import normalised
     shn, sha = normalised(shells)
     J, off, sz = oracle.eval_3c_aab_grad(shn, ta, tt, tb, center="A", normalize=False)
     Ja, _, _ = oracle.eval_3c_aab_grad(sha, ta, tt, tb, center="A", normalize=False)
-    g = np.zeros((len(ta), 3))
-    s = np.zeros((len(ta), 3))
-    for p in range(len(ta)):
-        blk = J[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p])
-        ablk = np.abs(Ja[3 * off[p]: 3 * (off[p] + sz[p])].reshape(3, sz[p]))
-        wp = w[off[p]: off[p] + sz[p]]
-        g[p] = blk @ wp
-        s[p] = ablk.max(axis=1) * np.abs(wp).sum()
-    return g, s
+    return vjp_reference(J, Ja, off, sz, w)
 
 
 @pytest.mark.parametrize("layout", ["orbital_pairs_on_A", "aux_on_A"])

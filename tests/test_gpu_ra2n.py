@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1701_06588_gb300 import workloads as W
-from tests.parity import TOL_FP64, assert_parity, normalised, reference_ra2n
+from tests.parity import TOL_FP64, assert_parity, normalised, reference_ra2n, vjp_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -86,14 +86,7 @@ def test_ra2n_gradient_against_oracle(shg, n):
     shn, sha = normalised(sh)
     J, o, z = oracle.eval_2c_ra2n_grad(shn, pa, pb, n, center="A", normalize=False)
     Ja, _, _ = oracle.eval_2c_ra2n_grad(sha, pa, pb, n, center="A", normalize=False)
-    ref = np.zeros((len(pa), 3))
-    scale = np.zeros((len(pa), 3))
-    for p in range(len(pa)):
-        blk = J[3 * o[p]: 3 * (o[p] + z[p])].reshape(3, z[p])
-        ablk = np.abs(Ja[3 * o[p]: 3 * (o[p] + z[p])].reshape(3, z[p]))
-        wp = w[o[p]: o[p] + z[p]]
-        ref[p] = blk @ wp
-        scale[p] = ablk.max(axis=1) * np.abs(wp).sum()
+    ref, scale = vjp_reference(J, Ja, o, z, w)
     bar = 1e-10 * np.abs(ref) + 1e-12 + 1e-15 * scale
     ex = np.abs(ga - ref) / bar
     assert ex.max() <= 1.0, (n, ex.max(), np.unravel_index(ex.argmax(), ex.shape))
