@@ -1,18 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark: contracted SHG two-center integrals on GB300.
 
-One step = every two-center block of the 200,000-pair workload (l <= 4,
-K = 1..8, exponents 0.05..500, separations 0..10 bohr, seed 1) for all five
-operators (overlap, 1/r, erfc(0.11 r)/r, erf(0.11 r)/r, exp(-r^2)), i.e.
-1,000,000 shell-pair integrals, FP64: one fused persistent launch for the
-five operators (--separate: one persistent launch per operator).
+One step = every two-center block of the 2,000,000-pair high-l workload
+(la, lb in 0..6 with P(l) ~ 2^-l, contraction lengths 1..20 with 30% of the
+shells at 12..20 primitives, exponents 0.03..5000, separations 0..10 bohr,
+seed 2) for 1/r and erfc(0.11 r)/r, i.e. 4,000,000 shell-pair integrals:
+one fused persistent launch for both operators in FP64 (--precision mixed:
+double-float; --separate: one persistent launch per operator).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp64|mixed] [--separate] [--configs]
 
-N > 1 runs under torch.distributed.run, one rank per GPU: every rank owns an
-independent copy of the workload (weak scaling, no data-path collective).
-Prints one JSON line on rank 0.
+N > 1 runs under torch.distributed.run, one rank per GPU: the one pair list
+is split into cost-balanced contiguous slices, one per rank (shard.py; strong
+scaling, no data-path collective: each rank writes its own blocks), and the
+step time is the maximum over the ranks (--replicas: every rank evaluates the
+whole workload, weak scaling).  Prints one JSON line on rank 0.
 """
 import argparse
 import hashlib
@@ -30,14 +33,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "shell-pair integrals/s on 1 GB300 at 1e-12 rel (FP64) vs mixed; % of roofline"
 UNIT = "shell-pair integrals/s"
-WORKLOAD = "c2_200k_l4_k8"
-OPS = [("overlap", 0, 0.0), ("coulomb", 1, 0.0), ("erfc", 2, 0.11), ("erf", 3, 0.11), ("gauss", 4, 1.0)]
+WORKLOAD = "c3_2m_l6_k20"
+OPS = [("coulomb", 1, 0.0), ("erfc", 2, 0.11)]
 DF_FMA_FP32_INSTR = 18.0       # FP32 instructions of one double-float multiply-add
 FP64_NOMINAL_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal, context)
-PROFILES = {"fp64_fused": os.path.join(ROOT, "profiles", "k_2c_fp64_fused_persistent_c2_200k.txt"),
-            "mixed_fused": os.path.join(ROOT, "profiles", "k_2c_mixed_fused_persistent_c2_200k.txt"),
-            "fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c2_200k.txt"),
-            "mixed": os.path.join(ROOT, "profiles", "k_2c_mixed_persistent_c2_200k.txt")}
+PROFILES = {"fp64_fused": os.path.join(ROOT, "profiles", "k_2c_fp64_fused_persistent_c3_2m.txt"),
+            "mixed_fused": os.path.join(ROOT, "profiles", "k_2c_mixed_fused_persistent_c3_2m.txt"),
+            "fp64": os.path.join(ROOT, "profiles", "k_2c_fp64_persistent_c3_2m.txt"),
+            "mixed": os.path.join(ROOT, "profiles", "k_2c_mixed_persistent_c3_2m.txt")}
 
 
 def parse():
@@ -47,7 +50,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--replicas", action="store_true",
+                   help="N > 1: every rank evaluates the whole workload (weak scaling) instead of its "
+                        "cost-balanced slice of the one pair list (strong scaling, the default)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-chunks", type=int, default=4,
+                   help="contiguous chunks of the end-to-end pipeline (read-back of chunk k overlaps chunk k+1)")
     p.add_argument("--n-pairs", type=int, default=None, help="smaller case of the same recipe (profiling only)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the headline path (the other forms are reported beside it)")
@@ -65,9 +73,10 @@ def parse():
 
 
 def workload_description(n):
-    return ("%s: %d shell pairs (la, lb uniform 0..4, K uniform 1..8, exponents log-uniform 0.05..500, "
-            "coefficients uniform -1..1 shell-normalised, separation uniform 0..10 bohr, seed 1) x 5 operators "
-            "(overlap, 1/r, erfc(0.11r)/r, erf(0.11r)/r, exp(-1.0 r^2))" % (WORKLOAD, n))
+    return ("%s: %d shell pairs (la, lb in 0..6 with P(l) ~ 2^-l, contraction lengths 1..11 for 70%% of the "
+            "shells and 12..20 for 30%%, exponents log-uniform 0.03..5000, coefficients uniform -1..1 "
+            "shell-normalised, separation uniform 0..10 bohr, seed 2) x 2 operators (1/r, erfc(0.11r)/r)"
+            % (WORKLOAD, n))
 
 
 # --------------------------------------------------------------------------- #
@@ -126,55 +135,81 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # CPU oracle baseline                                                         #
 # --------------------------------------------------------------------------- #
-def oracle_rate(shells, pa, pb, n, nthreads):
+def oracle_stratified(shells, pa, pb, budget_s, nthreads, seed=11):
+    """Oracle throughput on the workload, estimated from a class-stratified sample.
+
+    Every (la, lb) class of the pair list is timed on its own random sample
+    (the contraction lengths inside a class in their workload proportions),
+    n_c pairs of the class's N_c, all operators; the workload's time is
+    extrapolated as sum_c (N_c / n_c) T_c.  The sample is sized from a pilot
+    so that it takes about budget_s, with at least min(N_c, 16) pairs per
+    class.  Runs the FP64 build of the oracle on nthreads OpenMP threads."""
+    import numpy as np
     import oracle
     from paper_1701_06588_gb300 import workloads as W
-    sub, spa, spb = W.subset_pairs(shells, pa, pb, range(n))
-    t0 = time.perf_counter()
-    for _, op, om in OPS:
-        oracle.eval_2c(sub, spa, spb, op, om, nthreads=nthreads)
-    dt = time.perf_counter() - t0
-    return n * len(OPS) / dt, dt
+    l = np.asarray(shells["l"])
+    cls = l[pa] * 7 + l[pb]
+    rng = np.random.default_rng(seed)
+
+    def run(idx):
+        sub, spa, spb = W.subset_pairs(shells, pa, pb, np.sort(idx))
+        t0 = time.perf_counter()
+        for _, op, om in OPS:
+            oracle.eval_2c(sub, spa, spb, op, om, nthreads=nthreads, long_double=False)
+        return time.perf_counter() - t0
+
+    pilot = rng.choice(len(pa), min(len(pa), 256), replace=False)
+    run(pilot[:16])
+    per_pair = run(pilot) / len(pilot)
+    frac = min(1.0, budget_s / max(per_pair * len(pa), 1e-9))
+    t_est, n_sample, t_sample = 0.0, 0, 0.0
+    for c in np.unique(cls):
+        members = np.where(cls == c)[0]
+        n_c = int(min(len(members), max(min(len(members), 16), round(frac * len(members)))))
+        t_c = run(rng.choice(members, n_c, replace=False))
+        t_est += len(members) / n_c * t_c
+        n_sample += n_c
+        t_sample += t_c
+    rate = len(pa) * len(OPS) / t_est
+    sample = ("class-stratified sample of %s: %d of %d pairs over %d (la, lb) classes (contraction lengths in "
+              "their workload proportions inside each class) x %d operators, %.1f s of oracle time; throughput "
+              "extrapolated to the whole workload as sum_c N_c/n_c T_c; FP64 build of the Obara-Saika oracle, "
+              "%d OpenMP threads (a reported baseline, not a tuned competitor)"
+              % (WORKLOAD, n_sample, len(pa), len(np.unique(cls)), len(OPS), t_sample, nthreads))
+    return rate, t_sample, sample
 
 
-def cpu_baseline(shells, pa, pb, budget_s=15.0):
+def cpu_baseline(shells, pa, pb, budget_s=20.0):
     nthreads = os.cpu_count() or 1
-    n = 64
-    rate, dt = oracle_rate(shells, pa, pb, n, nthreads)
-    n2 = int(min(len(pa), max(n, n * budget_s / max(dt, 1e-3))))
-    if n2 > n:
-        rate, dt = oracle_rate(shells, pa, pb, n2, nthreads)
-        n = n2
-    return {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": "first %d pairs of %s x 5 operators, long-double Obara-Saika oracle, %d OpenMP threads, %.1f s"
-                      % (n, WORKLOAD, nthreads, dt)}
+    rate, _, sample = oracle_stratified(shells, pa, pb, budget_s, nthreads)
+    return {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    """Reference arm: the CPU oracle as it stands, on the host cores; every
+    step is a class-stratified sample of the workload (see oracle_stratified)."""
     from paper_1701_06588_gb300 import workloads as W
     if rank != 0:
         return
     shells, pa, pb = W.make(WORKLOAD)
     nthreads = os.cpu_count() or 1
-    _, dt = oracle_rate(shells, pa, pb, 32, nthreads)
-    per_pair = dt / 32
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    n = int(max(32, min(len(pa), budget / per_pair)))
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_rate(shells, pa, pb, max(32, n // 8), nthreads)
-    times = []
-    for _ in range(args.steps):
-        _, dt = oracle_rate(shells, pa, pb, n, nthreads)
-        times.append(dt)
-    ms = 1e3 * statistics.mean(times)
-    value = n * len(OPS) / (ms * 1e-3)
-    sample = "first %d pairs of %s x 5 operators per step, long-double oracle, %d threads" % (n, WORKLOAD, nthreads)
+        oracle_stratified(shells, pa, pb, budget / 4, nthreads)
+    rates, times = [], []
+    sample = ""
+    for s in range(args.steps):
+        r, t, sample = oracle_stratified(shells, pa, pb, budget, nthreads, seed=100 + s)
+        rates.append(r)
+        times.append(t)
+    value = statistics.mean(rates)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f80/f128 (long double)", "data": "synthetic",
-        "config": {"workload": workload_description(len(pa)), "sample": sample},
+        "warmup": args.warmup, "ms_per_step": 1e3 * len(pa) * len(OPS) / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_description(len(pa)), "sample": sample,
+                   "ms_per_step": "extrapolated time of one whole step; each step timed %.1f s of oracle work on "
+                                  "its sample" % statistics.mean(times)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -206,6 +241,21 @@ def read_profile_traffic(precision):
         return None
 
 
+def rank_workload(shells, pa, pb, rank, world, replicas=False):
+    """The pairs this rank evaluates.  One rank, or replicas: the whole list.
+    Otherwise the cost-balanced contiguous slice of the one list that
+    shard.shard_bounds gives rank `rank` of `world` (estimated FP64 flops of
+    the count model), with its shells only.  Returns (shells, pair_a, pair_b,
+    first pair index, units of the whole job per step)."""
+    from paper_1701_06588_gb300 import shard, workloads as W
+    if world == 1 or replicas:
+        return shells, pa, pb, 0, world * len(pa) * len(OPS)
+    b = shard.shard_bounds(shard.pair_costs(shells["l"], shells["nprim"], pa, pb), world)
+    lo, hi = int(b[rank]), int(b[rank + 1])
+    sub, spa, spb = W.subset_pairs(shells, pa, pb, range(lo, hi))
+    return sub, spa, spb, lo, len(pa) * len(OPS)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -221,6 +271,8 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     shells, pa, pb = W.make(WORKLOAD, n=args.n_pairs)
+    n_pairs_job = len(pa)
+    shells, pa, pb, first_pair, job_units = rank_workload(shells, pa, pb, rank, world, args.replicas)
     n_pairs = len(pa)
     units_per_step = n_pairs * len(OPS)
     basis = api.Basis(shells)
@@ -235,6 +287,7 @@ def run_ours(args, rank, world):
 
     fp64_peak = max(L.shg_measure_alu_peak(0, 4096, s_handle) for _ in range(3))
     fp32_peak = max(L.shg_measure_alu_peak(1, 65536, s_handle) for _ in range(2))
+    dmma_peak = max(L.shg_measure_alu_peak(2, 1024, s_handle) for _ in range(2))
 
     def time_steps(step_fn, steps, per_op=False):
         """K steps, L2 flushed between steps outside the events; per-step ms
@@ -315,7 +368,7 @@ def run_ours(args, rank, world):
         t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    value = world * units_per_step / (ms_step * 1e-3)
+    value = job_units / (ms_step * 1e-3)
 
     flops_separate = sum(counts.workload_flops(shells, pa, pb, op) for _, op, _ in OPS)
     flops_step = (counts.workload_fused_flops(shells, pa, pb, [(op, om) for _, op, om in OPS]) if fused
@@ -388,7 +441,7 @@ def run_ours(args, rank, world):
         t3 = time.perf_counter()
         if fused:
             p2.exec_fused(names, d_off2, outs, omegas=omegas, precision=args.precision)
-            # the five outputs read back concurrently, one copy stream each
+            # the outputs read back concurrently, one copy stream each
             done = torch.cuda.Event()
             done.record()
             for o, oh, cs in zip(outs, outs_h, copy_streams):
@@ -411,7 +464,23 @@ def run_ours(args, rank, world):
             parts["h2d_and_set_centers"].append(t2 - t1)
             parts["plan_create"].append(t3 - t2)
             parts["exec_and_d2h"].append(t4 - t3)
-    e2e_s = statistics.mean(e2e_times) if e2e_times else float("nan")
+    e2e_single_s = statistics.mean(e2e_times) if e2e_times else float("nan")
+    e2e_s = e2e_single_s
+    if fused and args.e2e_chunks > 1:
+        # the public pipeline: the pair list planned in contiguous chunks, each
+        # chunk's read-back overlapping the next chunk's fused pass
+        pipe = api.HostPipeline2c(basis, n_chunks=args.e2e_chunks, launch=tuned[form])
+        times = []
+        for it in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pipe.run(pa_h, pb_h, off_h, names, outs_h, omegas=omegas, precision=args.precision,
+                     centers=cent_h.numpy())
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(time.perf_counter() - t1)
+        if times:
+            e2e_s = statistics.mean(times)
     if dist:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -422,15 +491,22 @@ def run_ours(args, rank, world):
     dtype = "f64" if args.precision == "fp64" else "f32x2 (double-float) with f64 output"
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak" if (world == 1 or args.replicas) else "strong", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": workload_description(n_pairs), "pairs": n_pairs, "operators": names,
+        "config": {"workload": workload_description(n_pairs_job), "pairs": n_pairs_job, "operators": names,
+                   "parallelism": ("1 GPU" if world == 1 else
+                                   "%d replicas of the whole workload" % world if args.replicas else
+                                   "dp%d: cost-balanced contiguous slices of the one pair list (shard.py), no "
+                                   "data-path collective; rank 0 evaluates pairs [%d, %d)" %
+                                   (world, first_pair, first_pair + n_pairs)),
                    "precision": args.precision,
                    "form": ("fused multi-operator pass (one kernel per step, geometry-only Q_j shared by the "
-                            "five operators), autotuned launch shape, one CUDA graph per step" if fused else
+                            "operators), autotuned launch shape, one CUDA graph per step" if fused else
                             "one pass per operator, autotuned launch shape, one CUDA graph per step"),
                    "launch": {k: tuned[form][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
-                   "units_per_step": units_per_step, "elements_per_step": total * len(OPS),
+                   "units_per_step": job_units, "units_per_step_this_rank": units_per_step,
+                   "elements_per_step_this_rank": total * len(OPS),
                    "l2": "flushed between steps by a 512 MB device write outside the timed events",
                    "wall_s_timed_loop": wall},
         "per_operator_kernel_ms": {n: m for n, m in zip(names, per_op_ms)} if per_op_ms else None,
@@ -444,23 +520,26 @@ def run_ours(args, rank, world):
                      "algorithmic flops are the FP64 formula count",
                      "algorithmic_flops_per_step": flops_step, "kernel_ms_per_step": kern_ms,
                      "separate_passes_flops_per_step": flops_separate,
-                     "kernel": ("k_2c_%s_fused_persistent (5 operators in one pass)" %
+                     "kernel": ("k_2c_%s_fused_persistent (1/r and erfc in one pass)" %
                                 ("fp64" if args.precision == "fp64" else "mixed") if fused else
-                                "k_2c_%s_persistent<op> / static (5 operators per step)" %
+                                "k_2c_%s_persistent<op> / static (one launch per operator)" %
                                 ("fp64" if args.precision == "fp64" else "mixed"))},
         "forms": forms,
-        "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "what": ("per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
-                         "shg_plan_2c_create, shg_plan_2c_exec_fused (5 operators), D2H of all blocks to pinned "
-                         "memory (the five outputs on five copy streams)" if fused else
+                "what": ("per step, api.HostPipeline2c: pinned H2D of pair lists, offsets and centers, "
+                         "shg_basis_set_centers, then the pair list in %d contiguous chunks: shg_plan_2c_create "
+                         "and shg_plan_2c_exec_fused (both operators) per chunk, the D2H of chunk k's blocks to "
+                         "pinned memory on a copy stream overlapping chunk k+1" % args.e2e_chunks if fused else
                          "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
-                         "shg_plan_2c_create, 5 x shg_plan_2c_exec, D2H of all blocks to pinned memory (operator "
+                         "shg_plan_2c_create, one shg_plan_2c_exec per operator, D2H of all blocks to pinned memory (operator "
                          "k's copy on a second stream overlaps operator k+1's kernel)"),
-                "ms_parts": {k: 1e3 * statistics.mean(v) for k, v in parts.items() if v}},
-        "gpu_launches": args.steps * (1 if fused else len(OPS)) * plan.launches,
+                "unchunked_ms": 1e3 * e2e_single_s,
+                "unchunked_ms_parts": {k: 1e3 * statistics.mean(v) for k, v in parts.items() if v}},
+        "gpu_launches": args.steps * (1 if fused else len(OPS)) * plan.launches_for(args.precision),
         "clocks": clk,
-        "measured_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12},
+        "measured_peaks_tflops": {"fp64": fp64_peak / 1e12, "fp32": fp32_peak / 1e12,
+                                  "fp64_tensor_mma_m8n8k4": dmma_peak / 1e12},
     }
     if args.configs:
         result["other_configs"] = other_configs(args)
@@ -550,7 +629,8 @@ def other_configs(args):
     res = {}
     for key, name, ops, precs in [
             ("c1_2k_l3_k4", "c1_2k_l3_k4", [("overlap", 0.0), ("coulomb", 0.0)], ("fp64", "mixed")),
-            ("c3_2m_l6_k20", "c3_2m_l6_k20", [("coulomb", 0.0), ("erfc", 0.11)], ("fp64", "mixed")),
+            ("c2_200k_l4_k8", "c2_200k_l4_k8", [("overlap", 0.0), ("coulomb", 0.0), ("erfc", 0.11), ("erf", 0.11),
+                                                ("gauss", 1.0)], ("fp64", "mixed")),
             ("c2_200k_l4_k8 exp(-0.3 r^2)/r", "c2_200k_l4_k8", [("gauss_coulomb", 0.3)], ("fp64", "mixed")),
             ("c2_200k_l4_k8 r_a^4 (n = 2)", "c2_200k_l4_k8", [("ra2n", 2.0)], ("fp64",))]:
         sh, pa, pb = W.make(name)

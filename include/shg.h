@@ -68,7 +68,12 @@ enum shg_operator {
 
 enum shg_precision {
     SHG_PREC_FP64 = 0,  /* every step in FP64                                     */
-    SHG_PREC_MIXED = 1  /* FP32-based compensated arithmetic, FP64 where needed   */
+    SHG_PREC_MIXED = 1  /* FP32-based compensated arithmetic, FP64 where needed:
+                           two-center passes evaluate the classes with both la
+                           and lb >= 4 in FP64 (their sum over j of Eq.
+                           final_r12int_ab cancels beyond double-float reach),
+                           every other class in double-float; the FP64 far
+                           field of 1/r (T >= 120) is summed on the FP64 pipe */
 };
 
 enum shg_schedule {
@@ -184,8 +189,14 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n_pairs, const int32_t 
 int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thresh, int precision,
                      const int64_t *d_out_offsets, double *d_out, void *stream);
 
-/* Number of kernel launches one shg_plan_2c_exec issues (for accounting). */
+/* Number of kernel launches one FP64 shg_plan_2c_exec (or fused pass) issues
+ * (for accounting). */
 int shg_plan_launches(const shg_plan_t *plan);
+
+/* Number of kernel launches one execution of the plan issues in `precision`
+ * (SHG_PREC_MIXED adds the FP64 launch of the classes with both l >= 4 to a
+ * persistent plan that holds any); -1 for a NULL plan or bad precision. */
+int shg_plan_launches_prec(const shg_plan_t *plan, int precision);
 
 /*
  * shg_plan_2c_set_launch - launch shape of later executions of a plan (the
@@ -315,7 +326,10 @@ int shg_eval_3c_aab_grad(const shg_basis_t *orb, const shg_basis_t *aux, int64_t
  *   limit          n_pairs <= 1,048,576; larger lists return SHG_ERANGE
  *                  with a message, before any device work
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call outside stream capture.
+ * (cudaGetSymbolAddress), so make that first call outside stream capture;
+ * the address is kept for the life of the process, so do not use this entry
+ * point across a cudaDeviceReset.  Any precision other than SHG_PREC_FP64
+ * returns SHG_EINVAL.
  * The call synchronises `stream` once, after planning, to read the pair-index
  * check and the tile count.  All calls share the one array and each clears
  * what must start at zero; calls whose GPU work overlaps (other streams or
@@ -398,8 +412,9 @@ int shg_debug_boys(int64_t n_T, const double *d_T, int nmax, double *d_F, void *
 /*
  * shg_measure_alu_peak - ALU throughput probe: a grid of independent FMA
  * chains in FP64 (kind 0) or FP32 (kind 1), `iters` FMAs per thread per
- * chain, timed with CUDA events on `stream`.  Writes FLOP/s (2 per FMA) to
- * *flops.  Synchronous.
+ * chain, or of FP64 tensor-core MMA chains (kind 2: mma.sync m8n8k4 with FP64
+ * operands and accumulator, 512 flops per warp instruction), timed with CUDA
+ * events on `stream`.  Writes FLOP/s (2 per FMA) to *flops.  Synchronous.
  */
 int shg_measure_alu_peak(int kind, int iters, double *flops, void *stream);
 

@@ -102,6 +102,10 @@ class Plan2c:
                                            _stream(stream))
         self.launches = L.shg_plan_launches(self.handle)
 
+    def launches_for(self, precision):
+        """Kernel launches one execution of this plan issues in `precision`."""
+        return L.shg_plan_launches_prec(self.handle, _prec(precision))
+
     def exec(self, op, out_offsets, out, omega=0.0, precision="fp64", screen_thresh=0.0, stream=None):
         L.shg_plan_2c_exec(self.handle, _op(op), float(omega), float(screen_thresh), _prec(precision),
                            out_offsets, out, _stream(stream))
@@ -286,6 +290,81 @@ class Graph2c:
             self.close()
         except Exception:
             pass
+
+
+class HostPipeline2c:
+    """Two-center blocks from host pair lists into host output arrays, with
+    the read-back overlapped with the computation.
+
+    The pair list is split into n_chunks contiguous slices, each planned on
+    the device (shg_plan_2c_create) and evaluated by one fused pass
+    (shg_plan_2c_exec_fused) on the compute stream; as soon as slice k is
+    done, its blocks (a contiguous range of every output, since the offsets
+    are the prefix sums of the block sizes) are copied to the host on a copy
+    stream while slice k+1 computes.  Inputs: pinned host tensors pair_a,
+    pair_b (int32), offsets (int64) and centers; outputs: pinned host float64
+    tensors, one per operator.  Device buffers are kept between calls.
+    """
+
+    def __init__(self, basis, n_chunks=4, launch=None, schedule="persistent"):
+        self.basis = basis
+        self.n_chunks = max(1, int(n_chunks))
+        self.launch = launch
+        self.schedule = schedule
+        self.copy_stream = torch.cuda.Stream()
+        self._dev = {}
+
+    def _buf(self, name, n, dtype):
+        t = self._dev.get(name)
+        if t is None or t.numel() < n or t.dtype != dtype:
+            t = torch.empty(max(n, 1), dtype=dtype, device="cuda")
+            self._dev[name] = t
+        return t[:n]
+
+    def run(self, pair_a, pair_b, offsets, ops, outs, omegas=None, precision="fp64", centers=None):
+        n = int(pair_a.numel())
+        total = int(outs[0].numel())
+        omegas = [0.0] * len(ops) if omegas is None else list(omegas)
+        stream = torch.cuda.current_stream()
+        d_pa = self._buf("pa", n, torch.int32)
+        d_pb = self._buf("pb", n, torch.int32)
+        d_off = self._buf("off", n, torch.int64)
+        d_out = [self._buf("out%d" % i, total, torch.float64) for i in range(len(ops))]
+        torch.cuda.nvtx.range_push("shg:h2d")
+        d_pa.copy_(pair_a, non_blocking=True)
+        d_pb.copy_(pair_b, non_blocking=True)
+        d_off.copy_(offsets, non_blocking=True)
+        if centers is not None:
+            self.basis.set_centers(centers)
+        torch.cuda.nvtx.range_pop()
+        off_h = offsets.numpy()
+        bounds = [n * k // self.n_chunks for k in range(self.n_chunks + 1)]
+        plans = []
+        for k in range(self.n_chunks):
+            lo, hi = bounds[k], bounds[k + 1]
+            if hi > lo:
+                plan = Plan2c(self.basis, d_pa[lo:hi], d_pb[lo:hi], schedule=self.schedule)
+                if self.launch:
+                    set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"])
+                plans.append((lo, hi, plan))
+        for lo, hi, plan in plans:
+            plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision)
+            e0 = int(off_h[lo])
+            e1 = int(off_h[hi]) if hi < n else total
+            done = torch.cuda.Event()
+            done.record(stream)
+            self.copy_stream.wait_event(done)
+            torch.cuda.nvtx.range_push("shg:d2h")
+            with torch.cuda.stream(self.copy_stream):
+                for o_h, o_d in zip(outs, d_out):
+                    o_h[e0:e1].copy_(o_d[e0:e1], non_blocking=True)
+            torch.cuda.nvtx.range_pop()
+        fin = torch.cuda.Event()
+        fin.record(self.copy_stream)
+        stream.wait_event(fin)
+        for _, _, plan in plans:
+            plan.close()
+        return outs
 
 
 def set_launch(plan, threads_per_cta=128, ctas_per_sm=0):

@@ -77,7 +77,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
         msg = "\n".join("%s:\n%s" % (s, t) for s, t in failed)
         raise RuntimeError("CUDA library build failed:\n" + msg)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-fopenmp", "-lgomp"])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl", "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

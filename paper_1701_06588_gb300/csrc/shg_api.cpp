@@ -14,7 +14,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace shg {
+
+// NVTX range around one phase of a call (plan, exec, copies), visible to
+// profilers that trace NVTX (ncu --nvtx, nsys); no cost without a tool.
+struct Phase {
+    explicit Phase(const char *name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
+};
 
 static thread_local std::string g_err;
 
@@ -28,6 +39,8 @@ int fail(int code, const char *fmt, ...)
     g_err = buf;
     return code;
 }
+
+void clear_error() { g_err.clear(); }
 
 #define SHG_CUDA(call)                                                                                    \
     do {                                                                                                  \
@@ -599,6 +612,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
                      int n_centers, const double *centers, const int32_t *center_of_shell, int normalize,
                      shg_basis_t **out)
 {
+    Phase phase_("shg:basis_create");
     g_err.clear();
     if (!out) return fail(SHG_EINVAL, "out is NULL");
     *out = nullptr;
@@ -622,6 +636,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
 
     std::vector<ShellRec> sh(n_shells);
     std::vector<PrimRec> pr(n_prims);
+    std::vector<CoulPrim> cpr(n_prims);
     std::vector<int64_t> first(n_shells + 1, 0);
     for (int s = 0; s < n_shells; ++s) first[s + 1] = first[s] + nprim[s];
     // per-l constants: sqrt(pi) (2l+2)! / (2^{2l+3} (l+1)!) and K_l = sqrt((2l+1)/(4 pi))
@@ -665,11 +680,15 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
             dd p2 = {1.0, 0.0};
             for (int t = 0; t < L; ++t) p2 = dd_mul(p2, dd{2 * a, 0.0});  // (2a)^l
             PrimRec p;
+            const dd ia = dd_div(dd{1.0, 0.0}, dd{a, 0.0});
+            const dd w2c = dd_div(c, p2);
             p.alpha = a;
-            p.inv_alpha = dd_div(dd{1.0, 0.0}, dd{a, 0.0}).hi;
-            p.w2c = dd_div(c, p2).hi;
+            p.inv_alpha = ia.hi;
+            p.w2c = w2c.hi;
             p.wN = c.hi;
             pr[off + i] = p;
+            const dd cw = dd_mul(w2c, ia);
+            cpr[off + i] = CoulPrim{cw.hi, dd_mul(cw, dd_sqrt(ia)).hi};
         }
         sh[s] = ShellRec{L, K, (int)off, center_of_shell[s]};
     }
@@ -716,7 +735,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         const dd ia = dd_div(dd{1.0, 0.0}, dd{a, 0.0});
         const float ih = (float)ia.hi;
         mpr[o] = MixPrim{split2d(a), make_float2(ih, (float)((ia.hi - (double)ih) + ia.lo)), split2d(pr[o].wN),
-                         make_float2(0, 0)};
+                         cpr[o].fw};
     }
 
     shg_basis_t *b = new (std::nothrow) shg_basis_t;
@@ -743,6 +762,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         cudaMalloc(&d.prims, sizeof(PrimRec) * n_prims) != cudaSuccess ||
         cudaMalloc(&d.centers, sizeof(Vec4) * n_centers) != cudaSuccess ||
         cudaMalloc(&d.mprims, sizeof(MixPrim) * n_prims) != cudaSuccess ||
+        cudaMalloc(&d.cprims, sizeof(CoulPrim) * n_prims) != cudaSuccess ||
         cudaMalloc(&d.screen, sizeof(ScreenRec) * n_shells) != cudaSuccess ||
         cudaMalloc(&d.mcenters, sizeof(MixCenter) * n_centers) != cudaSuccess) {
         shg_basis_destroy(b);
@@ -752,6 +772,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
         cudaMemcpy(d.prims, pr.data(), sizeof(PrimRec) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.centers, ctr.data(), sizeof(Vec4) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.mprims, mpr.data(), sizeof(MixPrim) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.cprims, cpr.data(), sizeof(CoulPrim) * n_prims, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.screen, scr.data(), sizeof(ScreenRec) * n_shells, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.mcenters, mctr.data(), sizeof(MixCenter) * n_centers, cudaMemcpyHostToDevice) != cudaSuccess) {
         shg_basis_destroy(b);
@@ -767,6 +788,7 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
 
 int shg_basis_set_centers(shg_basis_t *b, const double *centers)
 {
+    Phase phase_("shg:set_centers");
     g_err.clear();
     if (!b || !centers) return fail(SHG_EINVAL, "NULL argument");
     BasisDev &d = b->d;
@@ -810,6 +832,7 @@ void shg_basis_destroy(shg_basis_t *b)
     cudaFree(b->d.prims);
     cudaFree(b->d.centers);
     cudaFree(b->d.mprims);
+    cudaFree(b->d.cprims);
     cudaFree(b->d.mcenters);
     cudaFree(b->d.screen);
     cudaFree(b->d.stage_raw);
@@ -861,6 +884,7 @@ int64_t shg_triple_offsets(const shg_basis_t *orb, const shg_basis_t *aux, int64
 int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, const int32_t *pb, int schedule,
                        void *stream, shg_plan_t **out)
 {
+    Phase phase_("shg:plan_2c_create");
     g_err.clear();
     if (!out) return fail(SHG_EINVAL, "out is NULL");
     *out = nullptr;
@@ -911,16 +935,25 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
     if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) return cleanup(fail(SHG_ECUDA, "memset failed"));
     cudaError_t e = launch_plan_build(d, ws, kNBins, ranks[schedule], d_err, s);
     if (e != cudaSuccess) return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(e)));
-    std::vector<int> tile_start(kNBins + 1);
+    // first tile of every class chunk and the tile count: tile_start[c * kKbins2c], c = 0..kNClass
+    int chunk_tile[kNClass + 1];
     int h_err = 0;
     int *d_tile_start = ws + n + 3 * kNBins;
-    if (cudaMemcpyAsync(tile_start.data(), d_tile_start, sizeof(int) * (kNBins + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpy2DAsync(chunk_tile, sizeof(int), d_tile_start, sizeof(int) * kKbins2c, sizeof(int), kNClass + 1,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(cudaGetLastError())));
     if (h_err) return cleanup(fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", basis->d.n_shells - 1));
-    d.n_tiles = tile_start[kNBins];
-    for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = tile_start[cls * kKbins2c];
+    d.n_tiles = chunk_tile[kNClass];
+    for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = chunk_tile[cls];
+    if (schedule == SHG_SCHED_PERSISTENT) {
+        // the persistent rank order is J-major (J descending), so the classes with
+        // both l >= kMixedFp64MinL are its first chunks
+        int n_hi = 0;
+        for (int cls = 0; cls < kNClass; ++cls) n_hi += mixed_runs_fp64(cls);
+        d.mixed_fp64_tiles = chunk_tile[n_hi];
+    }
     if (schedule == SHG_SCHED_PERSISTENT) {
         p->launches = d.n_tiles > 0 ? 1 : 0;
     } else {
@@ -932,6 +965,13 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
 }
 
 int shg_plan_launches(const shg_plan_t *p) { return p ? p->launches : 0; }
+
+int shg_plan_launches_prec(const shg_plan_t *p, int precision)
+{
+    if (!p || (precision != SHG_PREC_FP64 && precision != SHG_PREC_MIXED)) return -1;
+    if (precision == SHG_PREC_FP64 || p->d.schedule != SHG_SCHED_PERSISTENT) return p->launches;
+    return (p->d.mixed_fp64_tiles > 0) + (p->d.n_tiles > p->d.mixed_fp64_tiles);
+}
 
 int shg_plan_2c_set_launch(shg_plan_t *p, int threads, int ctas_per_sm)
 {
@@ -1013,6 +1053,7 @@ int shg_graph_2c_create(shg_plan_t *p, int n_ops, const int *ops, const double *
 
 int shg_graph_launch(shg_graph_t *g, void *stream)
 {
+    Phase phase_("shg:graph_launch");
     g_err.clear();
     if (!g) return fail(SHG_EINVAL, "graph is NULL");
     SHG_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
@@ -1035,12 +1076,16 @@ void shg_plan_destroy(shg_plan_t *p)
 }
 
 
+// which classes an FP64 execution covers: all of them, or only those the
+// mixed-precision passes run in FP64
+enum { kAllClasses = 0, kMixedFp64Classes = 1 };
 static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const int64_t *off, double *out,
-                     const double *o_pre, cudaStream_t s);
+                     const double *o_pre, cudaStream_t s, int sel = kAllClasses);
 
 int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int precision, const int64_t *off,
                      double *out, void *stream)
 {
+    Phase phase_("shg:plan_2c_exec");
     g_err.clear();
     if (!p) return fail(SHG_EINVAL, "plan is NULL");
     int r = check_op(op, omega, precision);
@@ -1072,15 +1117,20 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         m.boys = t->boys_mix;
         m.boys_e = t->boys_e_mix;
         m.km = consts_mix();
+        // classes with both l >= kMixedFp64MinL in FP64
+        r = exec_fp64(p, op, omega, screen, off, out, nullptr, s, kMixedFp64Classes);
+        if (r) return r;
         if (p->d.schedule == SHG_SCHED_PERSISTENT) {
-            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
-            m.tile_begin = 0;
+            m.tile_begin = p->d.mixed_fp64_tiles;
             m.tile_end = p->d.n_tiles;
+            if (m.tile_end <= m.tile_begin) return SHG_OK;
+            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
             m.counter = p->d.counter;
             SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op, p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
         } else {
             m.counter = nullptr;
             for (int cls = 0; cls < kNClass; ++cls) {
+                if (mixed_runs_fp64(cls)) continue;
                 m.tile_begin = p->d.class_tile_begin[cls];
                 m.tile_end = p->d.class_tile_begin[cls + 1];
                 if (m.tile_end <= m.tile_begin) continue;
@@ -1095,7 +1145,7 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
 // FP64 execution of a plan; o_pre != null runs the angular part on
 // precomputed contracted radial terms (op = OP_PRE, family path).
 static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const int64_t *off, double *out,
-                     const double *o_pre, cudaStream_t s)
+                     const double *o_pre, cudaStream_t s, int sel)
 {
     const DeviceTables *t = device_tables();
     if (!t) return SHG_ECUDA;
@@ -1118,15 +1168,17 @@ static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const i
     a.o_pre = o_pre;
     a.k = consts();
     if (p->d.schedule == SHG_SCHED_PERSISTENT) {
-        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
         a.tile_begin = 0;
-        a.tile_end = p->d.n_tiles;
+        a.tile_end = sel == kAllClasses ? p->d.n_tiles : p->d.mixed_fp64_tiles;
+        if (a.tile_end <= 0) return SHG_OK;
+        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
         a.counter = p->d.counter;
         SHG_CUDA(launch_2c(a, op, precision, persistent_grid_2c(op, precision, p->d.threads, p->d.ctas_per_sm), true, s,
                            p->d.threads));
     } else {
         a.counter = nullptr;
         for (int cls = 0; cls < kNClass; ++cls) {
+            if (sel == kMixedFp64Classes && !mixed_runs_fp64(cls)) continue;
             a.tile_begin = p->d.class_tile_begin[cls];
             a.tile_end = p->d.class_tile_begin[cls + 1];
             if (a.tile_end <= a.tile_begin) continue;
@@ -1168,6 +1220,7 @@ static int fused_args(shg_plan_t *p, int n_ops, const int *ops, const double *om
 int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const double *omegas, int precision,
                            const int64_t *off, double *const *outs, void *stream)
 {
+    Phase phase_("shg:plan_2c_exec_fused");
     g_err.clear();
     ArgsFused a;
     int r = fused_args(p, n_ops, ops, omegas, precision, off, outs, a);
@@ -1178,44 +1231,6 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     const DeviceTables *t = device_tables();
     if (!t) return SHG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == SHG_PREC_MIXED) {
-        ArgsMixFused m;
-        m.shells = p->d.basis->shells;
-        m.prims = p->d.basis->mprims;
-        m.centers = p->d.basis->mcenters;
-        m.pair_a = p->d.pair_a;
-        m.pair_b = p->d.pair_b;
-        m.perm = p->d.perm;
-        m.tiles = p->d.tiles;
-        m.out_off = reinterpret_cast<const long long *>(off);
-        for (int i = 0; i < 5; ++i) m.out[i] = a.out[i];
-        m.w_erf = split2(a.w_erf);
-        m.w_erf2 = split2((long double)a.w_erf * a.w_erf);
-        m.w_erfc = split2(a.w_erfc);
-        m.w_erfc2 = split2((long double)a.w_erfc * a.w_erfc);
-        m.w_gauss = split2(a.w_gauss);
-        m.share_att = a.share_att;
-        m.boys = t->boys_mix;
-        m.boys_e = t->boys_e_mix;
-        m.km = consts_mix();
-        if (p->d.schedule == SHG_SCHED_PERSISTENT) {
-            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
-            m.tile_begin = 0;
-            m.tile_end = p->d.n_tiles;
-            m.counter = p->d.counter;
-            SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm), true, s,
-                                           p->d.threads));
-        } else {
-            m.counter = nullptr;
-            for (int cls = 0; cls < kNClass; ++cls) {
-                m.tile_begin = p->d.class_tile_begin[cls];
-                m.tile_end = p->d.class_tile_begin[cls + 1];
-                if (m.tile_end <= m.tile_begin) continue;
-                SHG_CUDA(launch_2c_mixed_fused(m, 0, false, s, p->d.threads));
-            }
-        }
-        return SHG_OK;
-    }
     a.shells = p->d.basis->shells;
     a.prims = p->d.basis->prims;
     a.centers = p->d.basis->centers;
@@ -1226,20 +1241,66 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     a.out_off = reinterpret_cast<const long long *>(off);
     a.boys = t->boys;
     a.boys_e = t->boys_e;
+    a.cprims = p->d.basis->cprims;
     a.k = consts();
+    const bool mixed = precision == SHG_PREC_MIXED;
+    // FP64 pass: every tile, or under mixed precision the classes with both
+    // l >= kMixedFp64MinL (a prefix of the persistent tile order)
     if (p->d.schedule == SHG_SCHED_PERSISTENT) {
-        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
         a.tile_begin = 0;
-        a.tile_end = p->d.n_tiles;
-        a.counter = p->d.counter;
-        SHG_CUDA(launch_2c_fused(a, persistent_grid_2c_fused(p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
+        a.tile_end = mixed ? p->d.mixed_fp64_tiles : p->d.n_tiles;
+        if (a.tile_end > 0) {
+            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+            a.counter = p->d.counter;
+            SHG_CUDA(launch_2c_fused(a, persistent_grid_2c_fused(p->d.threads, p->d.ctas_per_sm), true, s,
+                                     p->d.threads));
+        }
     } else {
         a.counter = nullptr;
         for (int cls = 0; cls < kNClass; ++cls) {
+            if (mixed && !mixed_runs_fp64(cls)) continue;
             a.tile_begin = p->d.class_tile_begin[cls];
             a.tile_end = p->d.class_tile_begin[cls + 1];
             if (a.tile_end <= a.tile_begin) continue;
             SHG_CUDA(launch_2c_fused(a, 0, false, s, p->d.threads));
+        }
+    }
+    if (!mixed) return SHG_OK;
+    ArgsMixFused m;
+    m.shells = p->d.basis->shells;
+    m.prims = p->d.basis->mprims;
+    m.centers = p->d.basis->mcenters;
+    m.pair_a = p->d.pair_a;
+    m.pair_b = p->d.pair_b;
+    m.perm = p->d.perm;
+    m.tiles = p->d.tiles;
+    m.out_off = reinterpret_cast<const long long *>(off);
+    for (int i = 0; i < 5; ++i) m.out[i] = a.out[i];
+    m.w_erf = split2(a.w_erf);
+    m.w_erf2 = split2((long double)a.w_erf * a.w_erf);
+    m.w_erfc = split2(a.w_erfc);
+    m.w_erfc2 = split2((long double)a.w_erfc * a.w_erfc);
+    m.w_gauss = split2(a.w_gauss);
+    m.share_att = a.share_att;
+    m.boys = t->boys_mix;
+    m.boys_e = t->boys_e_mix;
+    m.km = consts_mix();
+    if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+        m.tile_begin = p->d.mixed_fp64_tiles;
+        m.tile_end = p->d.n_tiles;
+        if (m.tile_end <= m.tile_begin) return SHG_OK;
+        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+        m.counter = p->d.counter;
+        SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm), true, s,
+                                       p->d.threads));
+    } else {
+        m.counter = nullptr;
+        for (int cls = 0; cls < kNClass; ++cls) {
+            if (mixed_runs_fp64(cls)) continue;
+            m.tile_begin = p->d.class_tile_begin[cls];
+            m.tile_end = p->d.class_tile_begin[cls + 1];
+            if (m.tile_end <= m.tile_begin) continue;
+            SHG_CUDA(launch_2c_mixed_fused(m, 0, false, s, p->d.threads));
         }
     }
     return SHG_OK;
@@ -1277,6 +1338,7 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
                           const int32_t *tt, const int32_t *tb, int precision, const int64_t *off, double *out,
                           const double *w, double *grad_a, double *grad_b, void *stream, double screen = 0.0)
 {
+    Phase phase_("shg:eval_3c");
     if (!orb || !aux) return fail(SHG_EINVAL, "basis is NULL");
     if (precision != SHG_PREC_FP64 && (precision != SHG_PREC_MIXED || grad_a))
         return fail(SHG_EINVAL, "precision %d not available for the (aab) %s", precision,
@@ -1381,6 +1443,7 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
                      int precision, const int64_t *w_off, const double *w, double *grad_a, double *grad_b,
                      void *stream)
 {
+    Phase phase_("shg:eval_2c_grad");
     g_err.clear();
     int r = check_op(op, omega, precision);
     if (r) return r;
@@ -1441,6 +1504,7 @@ void shg_family_plan_destroy(shg_family_plan_t *fp)
 int shg_family_plan_create(const shg_basis_t *basis, int64_t n, const int32_t *d_pa, const int32_t *d_pb, void *stream,
                            shg_family_plan_t **out)
 {
+    Phase phase_("shg:family_plan_create");
     g_err.clear();
     if (!basis || !out || n < 0 || (n > 0 && (!d_pa || !d_pb))) return fail(SHG_EINVAL, "bad argument");
     if (n > (int64_t)INT32_MAX / 2) return fail(SHG_ERANGE, "n_pairs %lld out of range", (long long)n);
@@ -1562,6 +1626,7 @@ int64_t shg_family_plan_counts(const shg_family_plan_t *fp, int64_t *n_family_pa
 
 int shg_family_plan_exec(shg_family_plan_t *fp, int op, double omega, const int64_t *off, double *out, void *stream)
 {
+    Phase phase_("shg:family_plan_exec");
     g_err.clear();
     if (!fp) return fail(SHG_EINVAL, "plan is NULL");
     int r = check_op(op, omega, SHG_PREC_FP64);
@@ -1657,7 +1722,7 @@ int shg_debug_boys(int64_t n, const double *T, int nmax, double *F, void *stream
 int shg_measure_alu_peak(int kind, int iters, double *flops, void *stream)
 {
     g_err.clear();
-    if ((kind != 0 && kind != 1) || iters < 1 || !flops) return fail(SHG_EINVAL, "bad argument");
+    if (kind < 0 || kind > 2 || iters < 1 || !flops) return fail(SHG_EINVAL, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     SHG_CUDA(cudaGetDevice(&dev));
@@ -1679,7 +1744,10 @@ int shg_measure_alu_peak(int kind, int iters, double *flops, void *stream)
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (le != cudaSuccess || se != cudaSuccess) return fail(SHG_ECUDA, "probe failed");
-    *flops = 2.0 * 8.0 * (double)iters * threads * (double)blocks / (ms * 1e-3);
+    // flops per thread per chain step: one FMA (2) for kinds 0 and 1; kind 2 a
+    // warp-wide m8n8k4 MMA (512 flops) shared by the warp's 32 threads (16)
+    const double per = kind == 2 ? 16.0 : 2.0;
+    *flops = per * 8.0 * (double)iters * threads * (double)blocks / (ms * 1e-3);
     return SHG_OK;
 }
 

@@ -29,6 +29,36 @@ enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP
 // ------------------------------------------------------------------------- //
 __device__ __forceinline__ double powi(double x, int n);
 
+// F_kmax by the Taylor head of the table, T < kBoysTmax; with NeedE also
+// exp(-T) (else e is left untouched).
+template <bool NeedE>
+__device__ __forceinline__ void boys_head_near(double T, int kmax, const double *__restrict__ tab,
+                                               const double *__restrict__ etab, double &f, double &e)
+{
+    const int i = __double2int_rn(T * 16.0);
+    const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
+    const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
+    const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
+    f = fma(c67.y, y, c67.x);
+    f = fma(f, y, c45.y);
+    f = fma(f, y, c45.x);
+    f = fma(f, y, c23.y);
+    f = fma(f, y, c23.x);
+    f = fma(f, y, c01.y);
+    f = fma(f, y, c01.x);
+    if (NeedE) {
+        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
+        double x = fma(1.0 / 5040.0, y, 1.0 / 720.0);
+        x = fma(x, y, 1.0 / 120.0);
+        x = fma(x, y, 1.0 / 24.0);
+        x = fma(x, y, 1.0 / 6.0);
+        x = fma(x, y, 0.5);
+        x = fma(x, y, 1.0);
+        x = fma(x, y, 1.0);
+        e = x * __ldg(etab + i);
+    }
+}
+
 // F_kmax and exp(-T) (0 where it is below 1e-52).
 __device__ __forceinline__ void boys_head(double T, int kmax, const double *__restrict__ tab,
                                           const double *__restrict__ etab, const Consts &k, double &f, double &e)

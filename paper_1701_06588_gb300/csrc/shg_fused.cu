@@ -59,28 +59,45 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
     const bool f_co = g.out[OP_COULOMB] != nullptr || g.out[OP_ERFC] != nullptr;
     const bool f_er = g.out[OP_ERF] != nullptr;
     const bool f_x = g.out[OP_ERFC] != nullptr && !(f_er && g.share_att);
+    // exp(-T) from the Boys head: the downward recursion needs it for J > 1,
+    // the overlap reuses it
+    const bool need_e = J > 1 || f_ov;
 
     double Oov[J], Oco[J], Oer[J], Ox[J], Oga[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) Oov[j] = Oco[j] = Oer[j] = Ox[j] = Oga[j] = 0.0;
+    // far-field part of the 1/r sum: sum of fw_a fw_b over the primitive pairs
+    // with T >= kBoysTmax (see CoulPrim), multiplied by the per-pair order
+    // factors after the loop
+    double far = 0.0;
 
     const int Kb = sb.nprim, npp = sa.nprim * Kb;
     for (int q = 0; q < npp; ++q) {
         const int ia = q / Kb, ib = q - ia * Kb;
         const PrimRec pa = g.prims[sa.prim_off + ia], pb = g.prims[sb.prim_off + ib];
-        const double w = pa.w2c * pb.w2c;
         const double c = pa.alpha + pb.alpha;
         const double rc = rsqrt(c);
         const double ic = rc * rc;
         const double rho = pa.alpha * pb.alpha * ic;
         const double T = rho * R2;
-        const double mrk = powi(-rho, kmin);
+        const bool near = T < kBoysTmax;
+        const double mrk = (f_ov || (f_co && near)) ? powi(-rho, kmin) : 0.0;
         // Boys head of the 1/r sum first: it also yields exp(-T) for the overlap
         // (0 for T >= kBoysTmax, where the overlap term is below e^-120 of its prefactor)
         double Fc[J], eT = 0.0;
-        if (f_co) boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, Fc, eT);
+        if (f_co && near) {
+            double f;
+            if (need_e) boys_head_near<true>(T, kmax, g.boys, g.boys_e, f, eT);
+            else boys_head_near<false>(T, kmax, g.boys, g.boys_e, f, eT);
+            // downward recursion F_{k-1} = (2T F_k + exp(-T)) / (2k-1)
+            Fc[0] = f;
+            const double twoT = T + T;
+#pragma unroll
+            for (int j = 1; j < J; ++j) Fc[j] = fma(twoT, Fc[j - 1], eT) * g.k.inv_int[2 * (kmax - j + 1) - 1];
+        }
         if (f_ov) {
             // (pi/c)^{3/2} exp(-T) (-rho)^k
+            const double w = pa.w2c * pb.w2c;
             double t = w * kPi32 * ic * rc * (f_co ? eT : exp(-T)) * mrk;
 #pragma unroll
             for (int j = J - 1; j >= 0; --j) {
@@ -90,6 +107,7 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
         }
         if (f_ga) {
             // (pi^2/(c (rho+w)))^{3/2} exp(-w T/(rho+w)) (-w rho/(rho+w))^k
+            const double w = pa.w2c * pb.w2c;
             const double rd = rsqrt(rho + g.w_gauss);
             const double id = rd * rd;
             const double f = -g.w_gauss * rho * id;
@@ -101,18 +119,33 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
             }
         }
         if (f_co || f_er || f_x) {
-            // 2 pi^{5/2} / (alpha beta sqrt(c)) times the Boys sums
-            const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
+            // 2 pi^{5/2} w / (alpha beta sqrt(c)) times the Boys sums
+            const CoulPrim ca = g.cprims[sa.prim_off + ia], cb = g.cprims[sb.prim_off + ib];
+            const double pre = kTwoPi52 * ca.cw * cb.cw * rc;
             if (f_co) {
-                double t = pre * mrk;
+                if (near) {
+                    double t = pre * mrk;
 #pragma unroll
-                for (int j = J - 1; j >= 0; --j) {
-                    Oco[j] = fma(t, Fc[j], Oco[j]);
-                    t *= -rho;
+                    for (int j = J - 1; j >= 0; --j) {
+                        Oco[j] = fma(t, Fc[j], Oco[j]);
+                        t *= -rho;
+                    }
+                } else {
+                    far = fma(ca.fw, cb.fw, far);
                 }
             }
             if (f_er) att_acc<J>(g.w_erf, rho, T, kmax, kmin, pre, g, Oer);
             if (f_x) att_acc<J>(g.w_erfc, rho, T, kmax, kmin, pre, g, Ox);
+        }
+    }
+    if (far != 0.0) {
+        // pi^3 (-1)^n (2n-1)!! (2R^2)^{-n} / R for n = kmin .. kmax (R > 0: T >= kBoysTmax)
+        const double ir2 = 1.0 / R2;
+        double t = far * kPi3 * sqrt(ir2) * g.k.dfact[kmin] * powi(-0.5 * ir2, kmin);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            Oco[j] += t;
+            t *= -0.5 * ir2 * g.k.dint[2 * (kmax - j) + 1];
         }
     }
     // erfc = coulomb - attenuated; then every operator's orders scaled by 2^{kmax-j}

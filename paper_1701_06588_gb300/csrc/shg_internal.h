@@ -16,6 +16,12 @@ constexpr int kJmax = 7;          // min(la, lb) + 1 <= 7
 constexpr int kRa2nMax = 5;                // largest n of the (a|r_a^{2n}|b) operator
 constexpr int kNClass = (kLmax2c + 1) * (kLmax2c + 1);
 constexpr int kTile = 32;         // pairs per warp tile
+// Two-center classes that the mixed-precision passes evaluate in FP64: both
+// la and lb >= kMixedFp64MinL (J = min(la, lb) + 1 >= 5).  There the sum over
+// j of Eq. final_r12int_ab cancels by up to ~1e4 (l = 6, exponents to 5000),
+// beyond what double-float (2^-44 of the largest term) carries to 1e-10.
+constexpr int kMixedFp64MinL = 4;
+inline bool mixed_runs_fp64(int cls) { return cls / 7 >= kMixedFp64MinL && cls % 7 >= kMixedFp64MinL; }
 
 // Boys table: F_{n+t}(T_i)/t!, T_i = i/16, i = 0..kBoysGrid-1, n < kBoysN,
 // t = 0..7; Taylor expansion about the nearest grid point (|delta| <= 1/32).
@@ -55,10 +61,20 @@ struct GauntEnt {
     int L, M;
 };
 
+// Per-primitive weights of the Coulomb-type radial terms (Table S1), 16 bytes:
+//   cw = w2c / alpha            so that 2 pi^{5/2} w / (alpha beta sqrt(c)) = 2 pi^{5/2} cw_a cw_b / sqrt(c)
+//   fw = w2c alpha^{-3/2}       the far-field weight: for T >= kBoysTmax every order of
+//                               w 2 pi^{5/2} / (alpha beta sqrt(c)) (-rho)^n F_n(T) equals
+//                               fw_a fw_b pi^3 (-1)^n (2n-1)!! (2R^2)^{-n} / R
+struct alignas(16) CoulPrim {
+    double cw, fw;
+};
+
 // Mixed-precision (double-float) copies: each value v as float2 (hi, lo),
-// hi = fl32(v), lo = fl32(v - hi).
+// hi = fl32(v), lo = fl32(v - hi); fw is the FP64 far-field weight of CoulPrim.
 struct alignas(32) MixPrim {
-    float2 alpha, inv_alpha, wN, pad;
+    float2 alpha, inv_alpha, wN;
+    double fw;
 };
 struct alignas(32) MixCenter {
     float2 x, y, z, pad;
@@ -124,6 +140,7 @@ const DeviceTables *device_tables_if_ready(const int **ranks);
 
 // Host helpers of shg_api.cpp.
 int fail(int code, const char *fmt, ...);          // sets shg_last_error(), returns code
+void clear_error();                                // empties shg_last_error() (start of a call)
 const Consts &consts();                            // constant tables (host copy)
 int check_op(int op, double omega, int precision);  // operator / omega / precision check
 
@@ -138,6 +155,7 @@ struct BasisDev {
     PrimRec *prims = nullptr;     // device
     Vec4 *centers = nullptr;      // device
     MixPrim *mprims = nullptr;    // device, double-float copies for the mixed path
+    CoulPrim *cprims = nullptr;   // device, Coulomb-type weights (fused passes)
     ScreenRec *screen = nullptr;  // device, per-shell screening data
     MixCenter *mcenters = nullptr;
     // shg_basis_set_centers staging (allocated on its first call): raw
@@ -180,6 +198,8 @@ struct PlanDev {
     int *counter = nullptr;        // device, persistent work counter
     int n_tiles = 0;
     int class_tile_begin[kNClass + 1] = {};   // host, per-class tile ranges (class-major)
+    int mixed_fp64_tiles = 0;      // persistent order: leading tiles of the classes that the
+                                   // mixed-precision passes run in FP64 (both l >= kMixedFp64MinL)
     int threads = 128;             // launch shape (autotuned): threads per CTA (32, 64 or 128)
     int ctas_per_sm = 0;           // persistent CTAs per SM, 0 = occupancy limit
     void *owner_block = nullptr;   // device allocation holding all of the above
@@ -230,6 +250,7 @@ struct ArgsFused {
     double w_erf, w_erfc, w_gauss;
     int share_att;                // erf and erfc requested with the same omega
     const double *boys, *boys_e;
+    const CoulPrim *cprims;       // Coulomb-type weights per primitive
     Consts k;
 };
 

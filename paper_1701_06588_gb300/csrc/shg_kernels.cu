@@ -207,87 +207,107 @@ __global__ void k_classify_3c(int64_t n, const int32_t *__restrict__ ta, const i
     }
 }
 
-// Exclusive prefix sums over the bins in rank order: pair offsets bin_start
-// (and the scatter cursors) and tile offsets tile_start.  Tiles are cut per
-// chunk of `chunk` consecutive ranks: chunk = 1 cuts every bin on its own;
-// the planners pass the bins of one class (a contiguous chunk in their
-// class-major rank orders), so each class ends in one partial tile instead of
-// each of its (class, K-product) bins.  One block of 1024 threads.
-__global__ void k_scan_bins(int n_bins, int chunk, const int *__restrict__ hist, int *__restrict__ bin_start,
-                            int *__restrict__ cursor, int *__restrict__ tile_start)
+// Exclusive prefix sums over the bins in rank order, one block per chunk of
+// `chunk` consecutive ranks (blockDim.x == chunk <= 1024).  Both planners'
+// rank orders are class-major, and a chunk is the bins of one class: tiles
+// are cut per chunk, so each class ends in one partial tile.
+//   cursor[r]            offset of bin r inside its chunk (the scatter cursor)
+//   bin_start[c*chunk]   first pair of chunk c
+//   tile_start[c*chunk]  first tile of chunk c; tile_start[n_bins] = all tiles
+// Every block scans its own chunk and posts the chunk's count; the last block
+// to finish (an atomic ticket, *ticket zero on entry) scans the counts.  No
+// block waits for another.
+__device__ __forceinline__ int block_incl_scan(int x, int *s_warp)
 {
-    __shared__ long long s_cnt[1024], s_til[1024];
-    const int per = (n_bins + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per;
-    long long c = 0;
-    for (int i = b0; i < b0 + per && i < n_bins; ++i) c += hist[i];
-    s_cnt[threadIdx.x] = c;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        const long long vc = threadIdx.x >= off ? s_cnt[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_cnt[threadIdx.x] += vc;
-        __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    long long rc = s_cnt[threadIdx.x] - c;
-    const long long total = s_cnt[blockDim.x - 1];
-    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
-        bin_start[i] = (int)rc;
-        cursor[i] = (int)rc;
-        rc += hist[i];
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
     }
     __syncthreads();
-    // tiles of each rank: its own bin (chunk = 1) or, at the first rank of a chunk, the chunk's pairs
-    auto tiles_of = [&](int i) -> long long {
-        if (chunk == 1) return (hist[i] + kTile - 1) / kTile;
-        if (i % chunk) return 0;
-        const long long end = i + chunk < n_bins ? bin_start[i + chunk] : total;
-        return (end - bin_start[i] + kTile - 1) / kTile;
-    };
-    long long t = 0;
-    for (int i = b0; i < b0 + per && i < n_bins; ++i) t += tiles_of(i);
-    s_til[threadIdx.x] = t;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        const long long vt = threadIdx.x >= off ? s_til[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_til[threadIdx.x] += vt;
-        __syncthreads();
-    }
-    long long rt = s_til[threadIdx.x] - t;
-    for (int i = b0; i < b0 + per && i < n_bins; ++i) {
-        tile_start[i] = (int)rt;
-        rt += tiles_of(i);
-    }
-    if (threadIdx.x == blockDim.x - 1) tile_start[n_bins] = (int)s_til[blockDim.x - 1];
+    const int r = x + (warp ? s_warp[warp - 1] : 0);
+    __syncthreads();   // s_warp free for the next scan
+    return r;
 }
 
-__global__ void k_scatter(int64_t n, const int *__restrict__ key, int *__restrict__ cursor, int32_t *__restrict__ perm)
+__global__ void __launch_bounds__(1024) k_scan_chunks(int n_bins, int chunk, const int *__restrict__ hist,
+                                                      int *__restrict__ bin_start, int *__restrict__ cursor,
+                                                      int *__restrict__ tile_start, int *ticket)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_last;
+    const int c = blockIdx.x;
+    const int r = c * chunk + threadIdx.x;
+    const int v = hist[r];
+    const int incl = block_incl_scan(v, s_warp);
+    cursor[r] = incl - v;
+    if (threadIdx.x == blockDim.x - 1) {
+        bin_start[c * chunk] = incl;                  // the chunk's count for now
+        __threadfence();
+        s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last block: offsets of the chunks (gridDim.x <= blockDim.x chunks, one per thread)
+    const int k = threadIdx.x;
+    const int cnt = k < (int)gridDim.x ? __ldcg(bin_start + k * chunk) : 0;
+    const int til = (cnt + kTile - 1) / kTile;
+    const int ic = block_incl_scan(cnt, s_warp);
+    const int it = block_incl_scan(til, s_warp);
+    if (k < (int)gridDim.x) {
+        bin_start[k * chunk] = ic - cnt;
+        tile_start[k * chunk] = it - til;
+    }
+    if (k == (int)gridDim.x - 1) {
+        tile_start[n_bins] = it;
+        *ticket = 0;
+    }
+}
+
+__global__ void k_scatter(int64_t n, int chunk, const int *__restrict__ key, const int *__restrict__ bin_start,
+                          int *__restrict__ cursor, int32_t *__restrict__ perm)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const int pos = atomicAdd(cursor + key[p], 1);
+        const int r = key[p];
+        const int pos = bin_start[r - r % chunk] + atomicAdd(cursor + r, 1);
         perm[pos] = (int32_t)p;
     }
 }
 
-__global__ void k_make_tiles(int n_bins, int bins_per_class, int chunk, int n_pairs, const int *__restrict__ hist,
-                             const int *__restrict__ bin_start, const int *__restrict__ tile_start,
-                             const int *__restrict__ rank_to_bin, Tile *__restrict__ tiles)
+// One thread per tile: the tile's chunk by bisection over the chunks' first tiles.
+__global__ void k_make_tiles(int n_chunks, int chunk, int bins_per_class, int n_pairs, const int *__restrict__ bin_start,
+                             const int *__restrict__ tile_start, const int *__restrict__ rank_to_bin,
+                             Tile *__restrict__ tiles)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_bins; r += gridDim.x * blockDim.x) {
-        if (r % chunk) continue;
-        const int c = chunk == 1 ? hist[r] : (r + chunk < n_bins ? bin_start[r + chunk] : n_pairs) - bin_start[r];
-        if (!c) continue;
-        const int cls = rank_to_bin[r] / bins_per_class;
-        const int nt = (c + kTile - 1) / kTile;
-        for (int t = 0; t < nt; ++t) {
-            Tile tl;
-            tl.start = bin_start[r] + t * kTile;
-            tl.count = (c - t * kTile) < kTile ? (c - t * kTile) : kTile;
-            tl.cls = cls;
-            tl.pad = 0;
-            tiles[tile_start[r] + t] = tl;
+    const int total = tile_start[n_chunks * chunk];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_chunks;                    // tile_start[lo*chunk] <= t < tile_start[hi*chunk]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tile_start[mid * chunk] <= t) lo = mid;
+            else hi = mid;
         }
+        const int first = bin_start[lo * chunk] + (t - tile_start[lo * chunk]) * kTile;
+        const int end = lo + 1 < n_chunks ? bin_start[(lo + 1) * chunk] : n_pairs;
+        Tile tl;
+        tl.start = first;
+        tl.count = end - first < kTile ? end - first : kTile;
+        tl.cls = rank_to_bin[lo * chunk] / bins_per_class;
+        tl.pad = 0;
+        tiles[t] = tl;
     }
 }
 
@@ -345,6 +365,27 @@ __global__ void __launch_bounds__(256) k_alu_probe(int iters, T *sink)
     if (s == (T)-12345.0) sink[0] = s;
 }
 
+// FP64 tensor-core probe: 8 independent chains of mma.sync m8n8k4 (FP64 in,
+// FP64 accumulate) per warp; 2*8*8*4 = 512 flops per warp instruction.
+__global__ void __launch_bounds__(256) k_dmma_probe(int iters, double *sink)
+{
+    const double a = 1e-3 * (double)((threadIdx.x & 31) + 1), b = 0.999;
+    double c0[8], c1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c0[i] = c1[i] = 1e-3 * (double)i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(c0[i]), "+d"(c1[i])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += c0[i] + c1[i];
+    if (s == -12345.0) sink[0] = s;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------- //
@@ -375,11 +416,16 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
     }
     // both rank orders are class-major (each class a chunk of bins_per_class ranks): one tiling per class
     const int bpc = plan.kind == 2 ? kKbins2c : kKbins3c;
-    const int chunk = bpc;
-    k_scan_bins<<<1, 1024, 0, s>>>(n_bins, chunk, hist, bin_start, cursor, tile_start);
-    if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, key, cursor, plan.perm);
-    k_make_tiles<<<(n_bins + 255) / 256, 256, 0, s>>>(n_bins, bpc, chunk, (int)n, hist, bin_start, tile_start,
-                                                       d_bin_rank + n_bins, plan.tiles);
+    const int n_chunks = n_bins / bpc;
+    int *ticket = tile_start + n_bins - 1;            // never a chunk start (bpc > 1): free for the ticket
+    e = cudaMemsetAsync(ticket, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_scan_chunks<<<n_chunks, bpc, 0, s>>>(n_bins, bpc, hist, bin_start, cursor, tile_start, ticket);
+    if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, bpc, key, bin_start, cursor, plan.perm);
+    const int64_t max_tiles = n / kTile + n_chunks + 1;
+    const int tb = (int)((max_tiles + 255) / 256 < 1024 ? (max_tiles + 255) / 256 : 1024);
+    k_make_tiles<<<tb, 256, 0, s>>>(n_chunks, bpc, bpc, (int)n, bin_start, tile_start, d_bin_rank + n_bins,
+                                    plan.tiles);
     return cudaGetLastError();
 }
 
@@ -458,8 +504,10 @@ cudaError_t launch_alu_probe(int kind, int iters, int blocks, int threads, doubl
 {
     if (kind == 0)
         k_alu_probe<double><<<blocks, threads, 0, s>>>(iters, sink);
-    else
+    else if (kind == 1)
         k_alu_probe<float><<<blocks, threads, 0, s>>>(iters, reinterpret_cast<float *>(sink));
+    else
+        k_dmma_probe<<<blocks, threads, 0, s>>>(iters, sink);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,31 @@ __device__ __forceinline__ void boys_head_mix(df T, int kmax, const float4 *__re
     }
 }
 
+// F_kmax (and exp(-T)) for T < kBoysTmax only: the Taylor head of boys_head_mix.
+__device__ __forceinline__ void boys_head_mix_near(df T, int kmax, const float4 *__restrict__ tab,
+                                                   const float2 *__restrict__ etab, const ConstsMix &k, df &f, df &e)
+{
+    const int i = __float2int_rn(T.hi * 16.0f);
+    const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
+    const df y = two_sum(-d0, -T.lo);                          // -(T - T_i)
+    const float4 *c = tab + ((size_t)i * kBoysN + kmax) * 4;
+    const float4 q0 = __ldg(c), q1 = __ldg(c + 1), q2 = __ldg(c + 2);
+    float t = fmaf(q2.w, y.hi, q2.z);
+    t = fmaf(t, y.hi, q2.y);
+    t = fmaf(t, y.hi, q2.x);
+    f = add(mul_f(y, t), df{q1.z, q1.w});
+    f = add(mul(y, f), df{q1.x, q1.y});
+    f = add(mul(y, f), df{q0.z, q0.w});
+    f = add(mul(y, f), df{q0.x, q0.y});
+    const float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi,
+                          k.inv_fact_f[4]);
+    e = add(mul_f(y, te), ldf(k.inv_fact[3]));
+    e = add(mul(y, e), ldf(k.inv_fact[2]));
+    e = add(mul(y, e), df_f(1.0f));
+    e = add(mul(y, e), df_f(1.0f));
+    e = mul(e, ldf(__ldg(etab + i)));
+}
+
 // Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}: head, then one shared
 // downward recursion.
 template <int J>
@@ -173,6 +198,21 @@ __device__ __forceinline__ void mix_gauss(const MixPair &m, const df (&hp)[J], d
         S[j] = add(S[j], mul(hp[j], X));
         X = mul(X, wd);
     }
+}
+
+// the 1/r part for T < kBoysTmax (the fused pass sums the far field separately)
+template <int J>
+__device__ __forceinline__ void mix_coulomb_near(const MixPair &m, const df (&hp)[J], df pre, int kmax,
+                                                 const float4 *boys, const float2 *boys_e, const ConstsMix &km,
+                                                 df (&S)[J])
+{
+    df F[J], e;
+    boys_head_mix_near(m.T, kmax, boys, boys_e, km, F[0], e);
+    const df twoT = scale2(m.T, 2.0f);
+#pragma unroll
+    for (int j = 1; j < J; ++j) F[j] = mul(add(mul(twoT, F[j - 1]), e), ldf(km.inv_int[2 * (kmax - j + 1) - 1]));
+#pragma unroll
+    for (int j = 0; j < J; ++j) S[j] = add(S[j], mul(mul(hp[j], pre), F[j]));
 }
 
 template <int J>
@@ -416,6 +456,9 @@ __device__ void pair_2c_mix_fused(const ArgsMixFused &g, int p)
     df Sov[J], Sco[J], Sx[J], Ser[J], Sga[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) Sov[j] = Sco[j] = Sx[j] = Ser[j] = Sga[j] = df_f(0.0f);
+    // far field of the 1/r sum, T >= kBoysTmax: sum of the FP64 weights fw_a fw_b
+    // (on the FP64 pipe), times the per-pair order factors after the loop
+    double far = 0.0;
     const int Kb = sb.nprim, npp = sa.nprim * Kb;
     for (int q = 0; q < npp; ++q) {
         const int ia = q / Kb, ib = q - ia * Kb;
@@ -426,11 +469,29 @@ __device__ void pair_2c_mix_fused(const ArgsMixFused &g, int p)
         if (f_ga) mix_gauss<J>(m, hp, ldf(g.w_gauss), kmax, g.km, Sga);
         if (f_co || f_er || f_x) {
             const df pre = mix_boys_prefactor(m, pa, pb, g.km);
-            if (f_co) mix_coulomb<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, Sco);
+            if (f_co) {
+                if (m.T.hi < (float)kBoysTmax) mix_coulomb_near<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, Sco);
+                else far = fma(pa.fw, pb.fw, far);
+            }
             if (f_er)
                 mix_attenuated<J>(m, hp, pre, ldf(g.w_erf), ldf(g.w_erf2), false, kmax, g.boys, g.boys_e, g.km, Ser);
             if (f_x)
                 mix_attenuated<J>(m, hp, pre, ldf(g.w_erfc), ldf(g.w_erfc2), false, kmax, g.boys, g.boys_e, g.km, Sx);
+        }
+    }
+    if (far != 0.0) {
+        // pi^3 (-1)^n (2n-1)!! R^{-2n-1}, n = kmax - j: the far-field orders with the
+        // 2^n of this path's scaling (R > 0: T >= kBoysTmax)
+        const int kmin = kmax - J + 1;
+        const double ir2 = 1.0 / to_double(R2);
+        double dfk = 1.0;                                       // (2 kmin - 1)!!
+        for (int i = 2 * kmin - 1; i > 1; i -= 2) dfk *= (double)i;
+        double t = far * kPi3 * sqrt(ir2) * dfk * powi(-ir2, kmin);
+#pragma unroll
+        for (int j = J - 1; j >= 0; --j) {
+            const float th = __double2float_rn(t);
+            Sco[j] = add(Sco[j], df{th, __double2float_rn(t - (double)th)});
+            t *= -ir2 * (double)(2 * (kmax - j) + 1);
         }
     }
     df Sr[5][kJmax];

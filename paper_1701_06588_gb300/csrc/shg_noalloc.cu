@@ -14,7 +14,8 @@
 // Host code cannot use its name as a device address; the address is taken
 // with cudaGetSymbolAddress once per device, on the first call made on that
 // device (so that first call should not be made while a stream is being
-// captured).
+// captured), and kept for the life of the process: after cudaDeviceReset the
+// cached address is stale, so the entry point must not be used across one.
 //
 // All calls share the one array and it keeps the contents of the previous
 // call; every part that has to start at zero is cleared by the call itself.
@@ -70,7 +71,10 @@ extern "C" int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, co
                                    const int32_t *d_pair_b, int op, double omega, int precision,
                                    const int64_t *d_out_offsets, double *d_out, void *stream)
 {
+    clear_error();
     if (!basis) return fail(SHG_EINVAL, "basis is NULL");
+    if (precision != SHG_PREC_FP64)
+        return fail(SHG_EINVAL, "shg_eval_2c_noalloc: precision %d not available (FP64 only)", precision);
     int r = check_op(op, omega, precision);
     if (r) return r;
     if (n_pairs < 0) return fail(SHG_EINVAL, "n_pairs < 0");

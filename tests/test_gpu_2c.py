@@ -315,3 +315,17 @@ def test_full_size_c3_sampled(shg, precision):
         del out
     plan.close()
     b.close()
+
+
+def test_alu_peak_probes_report_positive_rates():
+    """The three throughput probes (FP64 FMA, FP32 FMA, FP64 tensor-core MMA)
+    run and report finite positive rates; a bad kind is rejected."""
+    import torch
+    from paper_1701_06588_gb300 import _lib as L, build
+    build.build()
+    st = torch.cuda.current_stream().cuda_stream
+    rates = [L.shg_measure_alu_peak(k, 256, st) for k in (0, 1, 2)]
+    assert all(np.isfinite(r) and r > 1e9 for r in rates), rates
+    assert rates[1] > rates[0]
+    with pytest.raises(L.ShgError):
+        L.shg_measure_alu_peak(3, 256, st)

@@ -148,3 +148,40 @@ def test_mixed_error_table_c3_classes_up_to_l6(shg):
             json.dump(table, f, indent=1, sort_keys=True)
     assert len(table) == 2 * 49
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "per_class"])
+def test_mixed_runs_high_l_classes_in_fp64(shg, schedule):
+    """Classes with both l >= 4 run the FP64 kernels inside the mixed passes
+    (their sum over j cancels beyond double-float reach): those blocks equal
+    the FP64 pass bit for bit, in the single-operator and the fused form;
+    every other class runs double-float and differs from FP64 in the last
+    bits somewhere."""
+    import torch
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=4000)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    d_off = torch.from_numpy(off).cuda()
+    plan = shg.Plan2c(b, pa, pb, schedule=schedule)
+    l = sh["l"]
+    sizes = (2 * l[pa].astype(np.int64) + 1) * (2 * l[pb].astype(np.int64) + 1)
+    hi = (l[pa] >= 4) & (l[pb] >= 4)
+    assert hi.sum() >= 5
+    el_hi = np.concatenate([np.arange(off[p], off[p] + sizes[p]) for p in np.where(hi)[0]])
+    el_lo = np.concatenate([np.arange(off[p], off[p] + sizes[p]) for p in np.where(~hi)[0]])
+    ops = [("coulomb", 0.0), ("erfc", 0.11)]
+    res = {}
+    for prec in ("fp64", "mixed"):
+        outs = [torch.full((total,), float("nan"), dtype=torch.float64, device="cuda") for _ in ops]
+        plan.exec_fused([o[0] for o in ops], d_off, outs, omegas=[o[1] for o in ops], precision=prec)
+        sep = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+        plan.exec("coulomb", d_off, sep, precision=prec)
+        torch.cuda.synchronize()
+        res[prec] = [o.cpu().numpy() for o in outs] + [sep.cpu().numpy()]
+    for f64, mix in zip(res["fp64"], res["mixed"]):
+        assert np.array_equal(f64[el_hi], mix[el_hi])
+        assert not np.array_equal(f64[el_lo], mix[el_lo])
+    if schedule == "persistent":
+        assert plan.launches_for("mixed") == 2 and plan.launches_for("fp64") == 1
+    plan.close()
+    b.close()
