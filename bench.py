@@ -336,7 +336,7 @@ def run_ours(args, rank, world):
         if args.no_extras and f != form:
             continue
         if args.no_tune:
-            tuned[f] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0}
+            tuned[f] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0, "variant": 0}
         else:
             tuned[f] = autotune.tune_2c(basis, pa, pb, names, omegas, d_off, outs, precision=f)
 
@@ -371,7 +371,10 @@ def run_ours(args, rank, world):
     value = job_units / (ms_step * 1e-3)
 
     flops_separate = sum(counts.workload_flops(shells, pa, pb, op) for _, op, _ in OPS)
-    flops_step = (counts.workload_fused_flops(shells, pa, pb, [(op, om) for _, op, om in OPS]) if fused
+    # the fused passes sum the far field of 1/r (T >= 120) as one multiply-add per
+    # primitive pair: count those pairs exactly
+    n_far = counts.far_primitive_pairs(shells, pa, pb) if fused else None
+    flops_step = (counts.workload_fused_flops(shells, pa, pb, [(op, om) for _, op, om in OPS], n_far) if fused
                   else flops_separate)
     achieved = flops_step / (kern_ms * 1e-3) / 1e12
     # double-float: one multiply-add of the FP64 formula costs 18 FP32 instructions
@@ -403,13 +406,13 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             ms_o, _ = time_steps(graph_step(go), args.steps)
             forms[other + "_tuned_graph"] = {"ms_per_step": ms_o, "value": units_per_step / (ms_o * 1e-3),
-                                             "launch": {k: tuned[other][k] for k in ("schedule", "threads_per_cta",
-                                                                                      "ctas_per_sm")}}
+                                             "launch": {k: tuned[other].get(k, 0) for k in
+                                                        ("schedule", "threads_per_cta", "ctas_per_sm", "variant")}}
             go.close()
             po.close()
         forms[form + "_tuned_graph"] = {"ms_per_step": ms_step, "value": units_per_step / (ms_step * 1e-3),
-                                        "launch": {k: tuned[form][k] for k in
-                                                   ("schedule", "threads_per_cta", "ctas_per_sm")}}
+                                        "launch": {k: tuned[form].get(k, 0) for k in
+                                                   ("schedule", "threads_per_cta", "ctas_per_sm", "variant")}}
         for f in ("fp64_fused", "mixed_fused", "mixed"):
             forms[f + "_speedup_vs_fp64_per_class"] = ms_pc / forms[f + "_tuned_graph"]["ms_per_step"]
             forms[f + "_speedup_vs_fp64_tuned_graph"] = (forms["fp64_tuned_graph"]["ms_per_step"] /
@@ -504,7 +507,7 @@ def run_ours(args, rank, world):
                    "form": ("fused multi-operator pass (one kernel per step, geometry-only Q_j shared by the "
                             "operators), autotuned launch shape, one CUDA graph per step" if fused else
                             "one pass per operator, autotuned launch shape, one CUDA graph per step"),
-                   "launch": {k: tuned[form][k] for k in ("schedule", "threads_per_cta", "ctas_per_sm")},
+                   "launch": {k: tuned[form].get(k, 0) for k in ("schedule", "threads_per_cta", "ctas_per_sm", "variant")},
                    "units_per_step": job_units, "units_per_step_this_rank": units_per_step,
                    "elements_per_step_this_rank": total * len(OPS),
                    "l2": "flushed between steps by a 512 MB device write outside the timed events",
@@ -519,6 +522,7 @@ def run_ours(args, rank, world):
                      "in this run: FP32 rate / 18 (FP32 instructions of one double-float multiply-add); "
                      "algorithmic flops are the FP64 formula count",
                      "algorithmic_flops_per_step": flops_step, "kernel_ms_per_step": kern_ms,
+                     "far_field_primitive_pairs": (int(n_far.sum()) if n_far is not None else None),
                      "separate_passes_flops_per_step": flops_separate,
                      "kernel": ("k_2c_%s_fused_persistent (1/r and erfc in one pass)" %
                                 ("fp64" if args.precision == "fp64" else "mixed") if fused else
@@ -650,7 +654,8 @@ def other_configs(args):
             # the same operators in one fused pass
             outs = [out] + [torch.empty(total, dtype=torch.float64, device="cuda") for _ in ops[1:]]
             names, oms = [n for n, _ in ops], [w for _, w in ops]
-            ff = counts.workload_fused_flops(sh, pa, pb, [(api.L.OPERATORS[n], w) for n, w in ops])
+            ff = counts.workload_fused_flops(sh, pa, pb, [(api.L.OPERATORS[n], w) for n, w in ops],
+                                             counts.far_primitive_pairs(sh, pa, pb))
             for prec in precs:
                 ms = _events_ms(lambda: plan.exec_fused(names, d_off, outs, omegas=oms, precision=prec),
                                 3 if len(pa) > 1e5 else 50)

@@ -189,6 +189,16 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n_pairs, const int32_t 
 int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thresh, int precision,
                      const int64_t *d_out_offsets, double *d_out, void *stream);
 
+/*
+ * shg_plan_2c_set_variant - compiled variant of the double-float fused kernel
+ * used by later mixed-precision executions of the plan (an autotuner knob):
+ * 0 = registers as the compiler allocates them (126 per thread, four
+ * 128-thread CTAs per SM), 1 = at most 96 registers (five CTAs per SM, a few
+ * values spilled).  Results are the same up to the order of operations.
+ * SHG_EINVAL for another value.
+ */
+int shg_plan_2c_set_variant(shg_plan_t *plan, int variant);
+
 /* Number of kernel launches one FP64 shg_plan_2c_exec (or fused pass) issues
  * (for accounting). */
 int shg_plan_launches(const shg_plan_t *plan);

@@ -39,6 +39,7 @@ SIGNATURES = [
     ("shg_plan_2c_exec", _I, [_P, _I, _D, _D, _I, _P, _P, _P]),
     ("shg_plan_launches", _I, [_P]),
     ("shg_plan_launches_prec", _I, [_P, _I]),
+    ("shg_plan_2c_set_variant", _I, [_P, _I]),
     ("shg_plan_destroy", None, [_P]),
     ("shg_family_plan_create", _I, [_P, _L, _P, _P, _P, ctypes.POINTER(_P)]),
     ("shg_family_plan_exec", _I, [_P, _I, _D, _P, _P, _P]),
@@ -174,6 +175,10 @@ def shg_family_plan_destroy(plan):
 
 def shg_plan_launches(plan):
     return load().shg_plan_launches(plan)
+
+
+def shg_plan_2c_set_variant(plan, variant):
+    return check(load().shg_plan_2c_set_variant(plan, variant))
 
 
 def shg_plan_launches_prec(plan, precision):

@@ -345,7 +345,8 @@ class HostPipeline2c:
             if hi > lo:
                 plan = Plan2c(self.basis, d_pa[lo:hi], d_pb[lo:hi], schedule=self.schedule)
                 if self.launch:
-                    set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"])
+                    set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"],
+                               self.launch.get("variant", 0))
                 plans.append((lo, hi, plan))
         for lo, hi, plan in plans:
             plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision)
@@ -367,8 +368,12 @@ class HostPipeline2c:
         return outs
 
 
-def set_launch(plan, threads_per_cta=128, ctas_per_sm=0):
+def set_launch(plan, threads_per_cta=128, ctas_per_sm=0, variant=0):
+    """Launch shape of later executions of a plan: threads per CTA, persistent
+    CTAs per SM (0 = occupancy limit) and the compiled variant of the
+    double-float fused kernel (0 or 1, see shg_plan_2c_set_variant)."""
     L.shg_plan_2c_set_launch(plan.handle, int(threads_per_cta), int(ctas_per_sm))
+    L.shg_plan_2c_set_variant(plan.handle, int(variant))
 
 
 def eval_3c_aab_grad(orb, aux, t_a, t_atilde, t_b, upstream, offsets=None, precision="fp64", stream=None):

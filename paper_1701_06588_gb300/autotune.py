@@ -2,7 +2,9 @@
 
 Candidates: schedule (one launch per class, or one persistent launch with
 tiles in decreasing estimated cost), threads per CTA (1, 2 or 4 warps, each
-warp owning a class-pure tile of up to 32 pairs) and persistent CTAs per SM.
+warp owning a class-pure tile of up to 32 pairs), persistent CTAs per SM and,
+for the double-float fused pass, the compiled kernel variant (register count
+left to the compiler, or capped for one more resident CTA per SM).
 Each candidate runs the requested operators a few times (CUDA events, after a
 warm-up); the fastest is cached in a JSON file keyed by GPU name, precision,
 operators and a signature of the workload's (la, lb, Ka*Kb) histogram.
@@ -19,6 +21,7 @@ from . import api
 
 CANDIDATES = ([("per_class", t, 0) for t in (32, 64, 128)] +
               [("persistent", t, c) for t in (32, 64, 128) for c in (0, 1, 2, 4, 8)])
+VARIANTS = {"mixed_fused": (0, 1)}
 
 
 def cache_path():
@@ -63,7 +66,7 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
             for op, om, o in zip(ops, omegas, outs):
                 plan.exec(op, out_offsets, o, omega=om, precision=precision)
 
-    key = "|".join([torch.cuda.get_device_name(), precision, ",".join(map(str, ops)),
+    key = "|".join(["v2", torch.cuda.get_device_name(), precision, ",".join(map(str, ops)),
                     workload_signature(basis, pair_a, pair_b)])
     db = _load()
     if not force and key in db:
@@ -74,23 +77,24 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
         if sched not in plans:
             plans[sched] = api.Plan2c(basis, pair_a, pair_b, schedule=sched)
         plan = plans[sched]
-        api.set_launch(plan, threads, ctas)
-        one_pass(plan)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
+        for variant in VARIANTS.get(precision, (0,)):
+            api.set_launch(plan, threads, ctas, variant)
             one_pass(plan)
-        e1.record()
-        torch.cuda.synchronize()
-        results.append((e0.elapsed_time(e1) / reps, sched, threads, ctas))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                one_pass(plan)
+            e1.record()
+            torch.cuda.synchronize()
+            results.append((e0.elapsed_time(e1) / reps, sched, threads, ctas, variant))
     for p in plans.values():
         p.close()
     results.sort()
-    ms, sched, threads, ctas = results[0]
-    best = {"schedule": sched, "threads_per_cta": threads, "ctas_per_sm": ctas, "ms": ms,
-            "candidates": [{"ms": r[0], "schedule": r[1], "threads_per_cta": r[2], "ctas_per_sm": r[3]}
-                           for r in results]}
+    ms, sched, threads, ctas, variant = results[0]
+    best = {"schedule": sched, "threads_per_cta": threads, "ctas_per_sm": ctas, "variant": variant, "ms": ms,
+            "candidates": [{"ms": r[0], "schedule": r[1], "threads_per_cta": r[2], "ctas_per_sm": r[3],
+                            "variant": r[4]} for r in results]}
     db[key] = best
     _save(db)
     return best
@@ -98,5 +102,5 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
 
 def tuned_plan(basis, pair_a, pair_b, config):
     plan = api.Plan2c(basis, pair_a, pair_b, schedule=config["schedule"])
-    api.set_launch(plan, config["threads_per_cta"], config["ctas_per_sm"])
+    api.set_launch(plan, config["threads_per_cta"], config["ctas_per_sm"], config.get("variant", 0))
     return plan

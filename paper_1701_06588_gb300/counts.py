@@ -35,6 +35,12 @@ def os_contracted_elements(l_a, l_b, k_a, k_b, gradients=False):
 # FP64 flop model of one shell pair                                           #
 # --------------------------------------------------------------------------- #
 _BOYS = 2 * 8 + 2 * 8 + 1          # Taylor of F_kmax (8 fma), exp Taylor (8 fma), scale by exp(-T_i)
+_BOYS_F = 2 * 8                     # Taylor of F_kmax alone: J = 1 needs no exp(-T) (no recursion)
+KBOYS_TMAX = 120.0                  # T = rho R^2 at and above which the fused 1/r sum takes the far field
+
+
+def _boys(J):
+    return _BOYS if J > 1 else _BOYS_F
 
 
 def _radial_flops(op, J, kmin):
@@ -57,8 +63,8 @@ def _radial_flops(op, J, kmin):
         # shrinking vector; J accumulations
         kmax = kmin + J - 1
         return setup + 12 + _BOYS + 3 * kmax + 3 * kmax * (kmax + 1) // 2 + J * (1 + 1)
-    coul = 4 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
-    att = 6 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1)
+    coul = 4 + _boys(J) + 3 * (J - 1) + powk + J * (2 + 1)
+    att = 6 + _boys(J) + 3 * (J - 1) + powk + J * (2 + 1)
     if op == OP_COULOMB:
         return setup + coul
     if op == OP_ERF:
@@ -94,31 +100,64 @@ def pair_flops(la, lb, ka, kb, op):
     return radial + harmonics + w_rows + scale + assembly
 
 
-def _fused_radial_flops(ops, J, kmin):
+def _fused_radial_flops(ops, J, kmin, far=False):
     """Per primitive pair of the fused pass (shg_plan_2c_exec_fused), with the
     per-term counts of _radial_flops: shared setup and (-rho)^kmin, one Boys
-    sum for 1/r and erfc, one attenuated sum per distinct omega of erf/erfc."""
+    sum for 1/r and erfc, one attenuated sum per distinct omega of erf/erfc.
+    far: the pair has T >= KBOYS_TMAX, where the 1/r sum is one multiply-add
+    of the per-primitive far-field weights (the Boys head, (-rho)^kmin and
+    the J orders are applied once per shell pair, fused_pair_flops)."""
     ops = dict(ops)                     # op id -> omega
     setup = 1 + 1 + 2 + 1 + 1
     powk = 2 * max(int(np.ceil(np.log2(kmin + 1))), 0)
+    boys_sums = (OP_COULOMB in ops or OP_ERFC in ops)
     f = setup
-    if OP_OVERLAP in ops or OP_COULOMB in ops or OP_ERFC in ops:
+    if OP_OVERLAP in ops or (boys_sums and not far):
         f += powk
     if OP_OVERLAP in ops:
         f += 4 + J * 2
     if OP_GAUSS in ops:
         f += 10 + powk + J * 2
-    boys_sums = (OP_COULOMB in ops or OP_ERFC in ops)
     atts = {ops[o] for o in (OP_ERF, OP_ERFC) if o in ops}
     if boys_sums or atts:
-        f += 4                          # 2 pi^{5/2} w / (alpha beta sqrt(c))
+        f += 2                          # 2 pi^{5/2} cw_a cw_b / sqrt(c)
     if boys_sums:
-        f += _BOYS + 3 * (J - 1) + J * (2 + 1)
-    f += len(atts) * (6 + _BOYS + 3 * (J - 1) + powk + J * (2 + 1))
+        f += 2 if far else _boys(max(J, 2 if OP_OVERLAP in ops else 1)) + 3 * (J - 1) + J * (2 + 1)
+    f += len(atts) * (6 + _boys(J) + 3 * (J - 1) + powk + J * (2 + 1))
     return f
 
 
-def fused_pair_flops(la, lb, ka, kb, ops):
+def far_primitive_pairs(shells, pair_a, pair_b, tmax=KBOYS_TMAX, chunk=1 << 16):
+    """Per pair, the number of primitive pairs with rho R^2 >= tmax (FP64);
+    pairs grouped by (Ka, Kb), one broadcast per group and chunk."""
+    K = np.asarray(shells["nprim"]).astype(np.int64)
+    off = np.zeros(len(K) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(K)
+    ex = np.asarray(shells["exps"], dtype=np.float64)
+    c = np.asarray(shells["centers"], dtype=np.float64).reshape(-1, 3)
+    co = np.asarray(shells["center_of"])
+    pa = np.asarray(pair_a)
+    pb = np.asarray(pair_b)
+    out = np.zeros(len(pa), dtype=np.int64)
+    if not len(pa):
+        return out
+    R2 = ((c[co[pa]] - c[co[pb]]) ** 2).sum(axis=1)
+    ka, kb = K[pa], K[pb]
+    key = ka * 4096 + kb
+    order = np.argsort(key, kind="stable")
+    bounds = np.flatnonzero(np.diff(key[order])) + 1
+    for grp in np.split(order, bounds):
+        Ka, Kb = int(ka[grp[0]]), int(kb[grp[0]])
+        for lo in range(0, len(grp), chunk):
+            g = grp[lo:lo + chunk]
+            A = ex[off[pa[g]][:, None] + np.arange(Ka)]
+            B = ex[off[pb[g]][:, None] + np.arange(Kb)]
+            rho = A[:, :, None] * B[:, None, :] / (A[:, :, None] + B[:, None, :])
+            out[g] = np.count_nonzero(rho * R2[g, None, None] >= tmax, axis=(1, 2))
+    return out
+
+
+def fused_pair_flops(la, lb, ka, kb, ops, n_far=None):
     """Algorithmic FP64 flops of one contracted shell pair in the fused pass
     over `ops` ((op id, omega) pairs; numpy-vectorised over la, lb, ka, kb):
     radial sums as _fused_radial_flops, then per pair the harmonics, both W
@@ -133,24 +172,38 @@ def fused_pair_flops(la, lb, ka, kb, ops):
     lmax = np.maximum(la, lb)
     na, nb = 2 * la + 1, 2 * lb + 1
     nop = len(ops)
-    rad = np.zeros(np.broadcast(la, lb, kk).shape, dtype=np.float64)
+    shape = np.broadcast(la, lb, kk).shape
+    rad = np.zeros(shape, dtype=np.float64)
+    kkb = np.broadcast_to(kk, shape).astype(np.float64)
+    nfar = np.zeros(shape) if n_far is None else np.broadcast_to(np.asarray(n_far, dtype=np.float64), shape)
+    J = np.broadcast_to(J, shape)
+    kmin = np.broadcast_to(kmin, shape)
+    finish = np.zeros(shape)
+    coul = any(o in (OP_COULOMB, OP_ERFC) for o, _ in ops)
     for j in range(1, 8):
         for km in range(0, 7):
             m = (J == j) & (kmin == km)
             if np.any(m):
-                rad[m] = _fused_radial_flops(ops, j, km)
+                near_f = _fused_radial_flops(ops, j, km)
+                far_f = _fused_radial_flops(ops, j, km, far=True)
+                rad[m] = (kkb[m] - nfar[m]) * near_f + nfar[m] * far_f
+                if coul:
+                    # far-field order factors, once per pair that has far primitive pairs
+                    finish[m] = (nfar[m] > 0) * (8 + 2 * max(int(np.ceil(np.log2(km + 1))), 0) + 4 * j)
     post = J * (nop + (1 if any(o == OP_ERFC for o, _ in ops) else 0))   # 2^{kmax-j} scaling, erfc = 1/r - erf
     harmonics = 8.0 * (lmax + 1) * (lmax + 2) / 2
     w_rows = (na + nb) * J * J
     scale = na * J * J                                                    # (2j-1)!! B weights on W_a
     assembly = na * nb * (2 * J * J + 1 + nop * (2 * J + 1))
-    return kk * rad + post + harmonics + w_rows + scale + assembly
+    return rad + finish + post + harmonics + w_rows + scale + assembly
 
 
-def workload_fused_flops(shells, pair_a, pair_b, ops):
+def workload_fused_flops(shells, pair_a, pair_b, ops, n_far=None):
+    """Fused-pass flops of a pair list; n_far (far_primitive_pairs) per pair,
+    else every primitive pair is counted as near."""
     l = np.asarray(shells["l"])
     k = np.asarray(shells["nprim"])
-    return float(np.sum(fused_pair_flops(l[pair_a], l[pair_b], k[pair_a], k[pair_b], ops)))
+    return float(np.sum(fused_pair_flops(l[pair_a], l[pair_b], k[pair_a], k[pair_b], ops, n_far)))
 
 
 def workload_flops(shells, pair_a, pair_b, op):

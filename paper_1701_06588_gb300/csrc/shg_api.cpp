@@ -122,12 +122,17 @@ void fill_consts(Consts &k)
     for (int j = 0; j < kJmax; ++j) {
         long double df = 1;
         for (int i = 2 * j - 1; i > 1; i -= 2) df *= i;
-        for (int kp = 0; kp <= j; ++kp)
-            k.jB[j][kp] = (double)(df / ((kp == 0 ? 1 : 2) * lfact(j + kp) * lfact(j - kp)));
+        for (int kp = 0; kp <= j; ++kp) {
+            const long double v = df / ((kp == 0 ? 1 : 2) * lfact(j + kp) * lfact(j - kp));
+            k.jB[j][kp] = (double)v;
+            k.jB_lo[j][kp] = (double)(v - (long double)k.jB[j][kp]);
+        }
     }
     for (int i = 0; i < 32; ++i) k.pow2[i] = std::ldexp(1.0, i);
     for (int i = 0; i < 64; ++i) k.dint[i] = (double)i;
     for (int i = 1; i < 192; ++i) k.inv_int[i] = (double)(1.0L / (long double)i);
+    k.inv_int_lo[0] = 0.0;
+    for (int i = 1; i < 64; ++i) k.inv_int_lo[i] = (double)(1.0L / (long double)i - (long double)k.inv_int[i]);
     long double df = 1;
     for (int n = 0; n < 32; ++n) {
         k.dfact[n] = (double)df;                 // (2n-1)!!
@@ -973,6 +978,15 @@ int shg_plan_launches_prec(const shg_plan_t *p, int precision)
     return (p->d.mixed_fp64_tiles > 0) + (p->d.n_tiles > p->d.mixed_fp64_tiles);
 }
 
+int shg_plan_2c_set_variant(shg_plan_t *p, int variant)
+{
+    g_err.clear();
+    if (!p) return fail(SHG_EINVAL, "plan is NULL");
+    if (variant != 0 && variant != 1) return fail(SHG_EINVAL, "kernel variant must be 0 or 1");
+    p->d.variant = variant;
+    return SHG_OK;
+}
+
 int shg_plan_2c_set_launch(shg_plan_t *p, int threads, int ctas_per_sm)
 {
     g_err.clear();
@@ -1072,15 +1086,35 @@ void shg_plan_destroy(shg_plan_t *p)
 {
     if (!p) return;
     cudaFreeAsync(p->d.owner_block, p->d.stream);
+    if (p->d.ev_fork) cudaEventDestroy(p->d.ev_fork);
+    if (p->d.ev_join) cudaEventDestroy(p->d.ev_join);
+    if (p->d.side) cudaStreamDestroy(p->d.side);
     delete p;
 }
 
+
+// Second stream and fork/join events of a persistent plan, created on the
+// first mixed-precision execution that needs them: the FP64 launch of the
+// classes with both l >= kMixedFp64MinL (a few hundred heavy tiles) runs on it
+// beside the double-float persistent launch, so that the FP64 pipes work on
+// those tiles while the FP32 pipes of the rest of the GPU run the others.
+static int plan_side_stream(shg_plan_t *p)
+{
+    if (p->d.side) return SHG_OK;
+    if (cudaStreamCreateWithFlags(&p->d.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->d.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->d.ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(SHG_ECUDA, "side stream: %s", cudaGetErrorString(cudaGetLastError()));
+    return SHG_OK;
+}
 
 // which classes an FP64 execution covers: all of them, or only those the
 // mixed-precision passes run in FP64
 enum { kAllClasses = 0, kMixedFp64Classes = 1 };
 static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const int64_t *off, double *out,
                      const double *o_pre, cudaStream_t s, int sel = kAllClasses);
+static int exec_fp64_static_range(shg_plan_t *p, int op, double omega, double screen, const int64_t *off,
+                                  double *out, int tile_begin, int tile_end, cudaStream_t s);
 
 int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int precision, const int64_t *off,
                      double *out, void *stream)
@@ -1117,9 +1151,22 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         m.boys = t->boys_mix;
         m.boys_e = t->boys_e_mix;
         m.km = consts_mix();
-        // classes with both l >= kMixedFp64MinL in FP64
-        r = exec_fp64(p, op, omega, screen, off, out, nullptr, s, kMixedFp64Classes);
-        if (r) return r;
+        // classes with both l >= kMixedFp64MinL in FP64: beside the double-float
+        // launch on the side stream (persistent plans holding both kinds), else first
+        const bool fork = p->d.schedule == SHG_SCHED_PERSISTENT && p->d.mixed_fp64_tiles > 0 &&
+                          p->d.n_tiles > p->d.mixed_fp64_tiles;
+        if (fork) {
+            r = plan_side_stream(p);
+            if (r) return r;
+            SHG_CUDA(cudaEventRecord(p->d.ev_fork, s));
+            SHG_CUDA(cudaStreamWaitEvent(p->d.side, p->d.ev_fork, 0));
+            r = exec_fp64_static_range(p, op, omega, screen, off, out, 0, p->d.mixed_fp64_tiles, p->d.side);
+            if (r) return r;
+            SHG_CUDA(cudaEventRecord(p->d.ev_join, p->d.side));
+        } else {
+            r = exec_fp64(p, op, omega, screen, off, out, nullptr, s, kMixedFp64Classes);
+            if (r) return r;
+        }
         if (p->d.schedule == SHG_SCHED_PERSISTENT) {
             m.tile_begin = p->d.mixed_fp64_tiles;
             m.tile_end = p->d.n_tiles;
@@ -1127,6 +1174,7 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
             SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
             m.counter = p->d.counter;
             SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op, p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
+            if (fork) SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join, 0));
         } else {
             m.counter = nullptr;
             for (int cls = 0; cls < kNClass; ++cls) {
@@ -1188,6 +1236,38 @@ static int exec_fp64(shg_plan_t *p, int op, double omega, double screen, const i
     return SHG_OK;
 }
 
+// FP64 single-operator pass over the tiles [tile_begin, tile_end) of a plan,
+// one warp per tile (no work counter: it may run beside a persistent launch
+// of the same plan)
+static int exec_fp64_static_range(shg_plan_t *p, int op, double omega, double screen, const int64_t *off,
+                                  double *out, int tile_begin, int tile_end, cudaStream_t s)
+{
+    const DeviceTables *t = device_tables();
+    if (!t) return SHG_ECUDA;
+    Args2c a;
+    a.shells = p->d.basis->shells;
+    a.prims = p->d.basis->prims;
+    a.centers = p->d.basis->centers;
+    a.pair_a = p->d.pair_a;
+    a.pair_b = p->d.pair_b;
+    a.perm = p->d.perm;
+    a.tiles = p->d.tiles;
+    a.out_off = reinterpret_cast<const long long *>(off);
+    a.out = out;
+    a.omega = omega;
+    a.screen_thresh = screen;
+    a.screen = p->d.basis->screen;
+    a.boys = t->boys;
+    a.boys_e = t->boys_e;
+    a.o_pre = nullptr;
+    a.k = consts();
+    a.tile_begin = tile_begin;
+    a.tile_end = tile_end;
+    a.counter = nullptr;
+    SHG_CUDA(launch_2c(a, op, SHG_PREC_FP64, 0, false, s, 32));
+    return SHG_OK;
+}
+
 // Arguments of a fused pass: the operators are checked (each of overlap,
 // 1/r, erfc, erf and the Gaussian at most once, in the given precision),
 // outputs placed by operator id.
@@ -1244,9 +1324,23 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     a.cprims = p->d.basis->cprims;
     a.k = consts();
     const bool mixed = precision == SHG_PREC_MIXED;
-    // FP64 pass: every tile, or under mixed precision the classes with both
-    // l >= kMixedFp64MinL (a prefix of the persistent tile order)
-    if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+    const bool persistent = p->d.schedule == SHG_SCHED_PERSISTENT;
+    // mixed precision on a persistent plan with both kinds of classes: the FP64
+    // tiles (one warp each) on the side stream, beside the double-float launch
+    const bool fork = mixed && persistent && p->d.mixed_fp64_tiles > 0 && p->d.n_tiles > p->d.mixed_fp64_tiles;
+    if (fork) {
+        r = plan_side_stream(p);
+        if (r) return r;
+        SHG_CUDA(cudaEventRecord(p->d.ev_fork, s));
+        SHG_CUDA(cudaStreamWaitEvent(p->d.side, p->d.ev_fork, 0));
+        a.tile_begin = 0;
+        a.tile_end = p->d.mixed_fp64_tiles;
+        a.counter = nullptr;
+        SHG_CUDA(launch_2c_fused(a, 0, false, p->d.side, 32));
+        SHG_CUDA(cudaEventRecord(p->d.ev_join, p->d.side));
+    } else if (persistent) {
+        // FP64 pass: every tile, or under mixed precision the classes with both
+        // l >= kMixedFp64MinL (a prefix of the persistent tile order)
         a.tile_begin = 0;
         a.tile_end = mixed ? p->d.mixed_fp64_tiles : p->d.n_tiles;
         if (a.tile_end > 0) {
@@ -1285,14 +1379,15 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     m.boys = t->boys_mix;
     m.boys_e = t->boys_e_mix;
     m.km = consts_mix();
-    if (p->d.schedule == SHG_SCHED_PERSISTENT) {
+    if (persistent) {
         m.tile_begin = p->d.mixed_fp64_tiles;
         m.tile_end = p->d.n_tiles;
         if (m.tile_end <= m.tile_begin) return SHG_OK;
         SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
         m.counter = p->d.counter;
-        SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm), true, s,
-                                       p->d.threads));
+        SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm, p->d.variant),
+                                       true, s, p->d.threads, p->d.variant));
+        if (fork) SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join, 0));
     } else {
         m.counter = nullptr;
         for (int cls = 0; cls < kNClass; ++cls) {
@@ -1300,7 +1395,7 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
             m.tile_begin = p->d.class_tile_begin[cls];
             m.tile_end = p->d.class_tile_begin[cls + 1];
             if (m.tile_end <= m.tile_begin) continue;
-            SHG_CUDA(launch_2c_mixed_fused(m, 0, false, s, p->d.threads));
+            SHG_CUDA(launch_2c_mixed_fused(m, 0, false, s, p->d.threads, p->d.variant));
         }
     }
     return SHG_OK;

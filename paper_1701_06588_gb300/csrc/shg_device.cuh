@@ -264,6 +264,11 @@ __device__ __forceinline__ ddv dd_mul_d(ddv a, double b)
     const double e = fma(a.l, b, fma(a.h, b, -p));
     return dd_fast(p, e);
 }
+__device__ __forceinline__ ddv dd_neg(ddv a) { return ddv{-a.h, -a.l}; }
+__device__ __forceinline__ ddv dd_sub(ddv a, ddv b) { return dd_add(a, dd_neg(b)); }
+// a b + c
+__device__ __forceinline__ ddv dd_fma(ddv a, ddv b, ddv c) { return dd_add(dd_mul(a, b), c); }
+
 // 1/a: FP64 reciprocal and one Newton step r + r (1 - a r) carried in double-double
 __device__ __forceinline__ ddv dd_inv(ddv a)
 {

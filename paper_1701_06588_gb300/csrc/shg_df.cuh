@@ -70,16 +70,22 @@ __device__ __forceinline__ df scale2(df a, float p2) { return df{a.hi * p2, a.lo
 // a*b + c
 __device__ __forceinline__ df fma_df(df a, df b, df c) { return add(mul(a, b), c); }
 
-// 1/sqrt(a), a > 0: FP32 estimate and one Newton step in double-float
+// 1/sqrt(a), a > 0: FP32 estimate r (relative error ~2^-23) and one Newton
+// step r + r (1 - a r^2) / 2.  a r^2 = q + s with q = fl(a.hi r^2) and the
+// rest s from the exact FP32 products (FMA); q is within 2^-21 of 1, so 1 - q
+// is exact and e = (1 - q) - s carries 1 - a r^2 to ~2^-46 absolute.  The
+// correction r e / 2 (~2^-23 r) in FP32 then adds an error of ~2^-47 r.
 __device__ __forceinline__ df rsqrt_df(df a)
 {
     const float r = rsqrtf(a.hi);
-    const float r2h = r * r;
-    const df r2 = df{r2h, fmaf(r, r, -r2h)};
-    const df t = mul(a, r2);                     // ~1
-    const df e = add_f(neg(t), 1.0f);            // 1 - a r^2, small
-    const df corr = mul_f(e, 0.5f * r);
-    return add_f(corr, r);
+    const float p = r * r;
+    const float pe = fmaf(r, r, -p);                // r^2 = p + pe exactly
+    const float q = a.hi * p;
+    float t = fmaf(a.hi, p, -q);                    // a.hi p = q + t exactly
+    t = fmaf(a.hi, pe, t);
+    t = fmaf(a.lo, p, t);
+    const float e = (1.0f - q) - t;
+    return fast_two_sum(r, (0.5f * r) * e);
 }
 
 __device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }

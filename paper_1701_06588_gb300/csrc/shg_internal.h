@@ -90,6 +90,10 @@ struct Consts {
     double dfact[32];                      // (2n-1)!!, (-1)!! = 1
     double binom[kRa2nMax + 1][kRa2nMax + 1];  // C(n, j)
     double ra2n_k[kRa2nMax + 1][kRa2nMax + 1]; // 2^{d-m} (2m+1)!! C(m,d) / (2d+1)!!, [m][d], d <= m
+    // low parts of jB and inv_int (value - double(value), from long double) for
+    // the double-double (a|r_a^{2n}|b) path
+    double jB_lo[kJmax][kJmax];
+    double inv_int_lo[64];
 };
 
 void fill_consts(Consts &k);
@@ -202,6 +206,10 @@ struct PlanDev {
                                    // mixed-precision passes run in FP64 (both l >= kMixedFp64MinL)
     int threads = 128;             // launch shape (autotuned): threads per CTA (32, 64 or 128)
     int ctas_per_sm = 0;           // persistent CTAs per SM, 0 = occupancy limit
+    int variant = 0;               // compiled kernel variant of the double-float fused pass
+                                   // (0: free register count, 1: <= 96 registers, 5 CTAs per SM)
+    cudaStream_t side = nullptr;   // second stream of the mixed passes (FP64 high-l classes)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *owner_block = nullptr;   // device allocation holding all of the above
     cudaStream_t stream = nullptr;
 };
@@ -352,8 +360,8 @@ cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persiste
                             int threads = 128);
 int persistent_grid_2c_mixed(int op, int threads = 128, int ctas_per_sm = 0);
 cudaError_t launch_2c_mixed_fused(const ArgsMixFused &args, int grid, bool persistent, cudaStream_t s,
-                                  int threads);
-int persistent_grid_2c_mixed_fused(int threads = 128, int ctas_per_sm = 0);
+                                  int threads, int variant = 0);
+int persistent_grid_2c_mixed_fused(int threads = 128, int ctas_per_sm = 0, int variant = 0);
 int persistent_grid_2c_grad(int op, int precision);
 int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,

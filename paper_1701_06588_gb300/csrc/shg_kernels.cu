@@ -103,9 +103,231 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
     }
 }
 
+// ------------------------------------------------------------------------- //
+// (a|r_a^{2n}|b) in double-double (Sec. II C, Eqs. ara2nb and T_rab2_deriv). //
+// Its radial orders grow like (beta^2 R^2 / c)^n while the block does not:  //
+// the sum over j of Eq. final_r12int_ab cancels by up to ~1e8 at n = 5 for a //
+// diffuse a and a tight b, so every term of it must carry ~1e-20 relative   //
+// precision: the contracted orders, the harmonics of the (exact) separation,//
+// the W rows, the (2j-1)!! B weights and the block sums run in double-      //
+// double.  Factors common to all orders of one primitive pair (weights,     //
+// exp(-rho R^2)) and to a whole block (A_{l,m}) stay FP64: their rounding   //
+// scales a term of the sum as a whole and does not survive the cancellation.//
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ ddv dd_const(double h, double l) { return ddv{h, l}; }
+
+__device__ __forceinline__ ddv rcd_get(const ddv *Rc, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return ddv{0.0, 0.0};
+    const ddv v = Rc[L * (L + 1) / 2 + am];
+    return (m < 0 && (am & 1)) ? dd_neg(v) : v;
+}
+__device__ __forceinline__ ddv rsd_get(const ddv *Rs, int L, int m)
+{
+    const int am = m < 0 ? -m : m;
+    if (L < 0 || am > L) return ddv{0.0, 0.0};
+    const ddv v = Rs[L * (L + 1) / 2 + am];
+    return (m < 0 && !(am & 1)) ? dd_neg(v) : v;
+}
+
+// scaled_harmonics with double-double arithmetic and constants
+__device__ void scaled_harmonics_dd(ddv x, ddv y, ddv z, int lmax, const Consts &k, ddv *Rc, ddv *Rs)
+{
+    const ddv r2 = dd_add(dd_add(dd_mul(x, x), dd_mul(y, y)), dd_mul(z, z));
+    Rc[0] = ddv{1.0, 0.0};
+    Rs[0] = ddv{0.0, 0.0};
+    for (int l = 0; l < lmax; ++l) {
+        const int d0 = l * (l + 1) / 2, d1 = (l + 1) * (l + 2) / 2, dm = (l - 1) * l / 2;
+        const ddv cll = Rc[d0 + l], sll = Rs[d0 + l];
+        const ddv inv = dd_const(k.inv_int[2 * l + 2], k.inv_int_lo[2 * l + 2]);
+        Rc[d1 + l + 1] = dd_neg(dd_mul(dd_sub(dd_mul(x, cll), dd_mul(y, sll)), inv));
+        Rs[d1 + l + 1] = dd_neg(dd_mul(dd_add(dd_mul(y, cll), dd_mul(x, sll)), inv));
+        const ddv zl = dd_mul_d(z, k.dint[2 * l + 1]);
+        for (int m = 0; m <= l; ++m) {
+            const int q = (l + m + 1) * (l - m + 1);
+            const ddv im = dd_const(k.inv_int[q], k.inv_int_lo[q]);
+            ddv vc = dd_mul(zl, Rc[d0 + m]);
+            if (m <= l - 1) vc = dd_sub(vc, dd_mul(r2, Rc[dm + m]));
+            Rc[d1 + m] = dd_mul(vc, im);
+            if (m == 0) {
+                Rs[d1] = ddv{0.0, 0.0};
+            } else {
+                ddv vs = dd_mul(zl, Rs[d0 + m]);
+                if (m <= l - 1) vs = dd_sub(vs, dd_mul(r2, Rs[dm + m]));
+                Rs[d1 + m] = dd_mul(vs, im);
+            }
+        }
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void w_row_dd(const ddv *Rc, const ddv *Rs, int l, int m, ddv (&w)[J * J])
+{
+    const int mu = m < 0 ? -m : m;
+    const bool sine = m < 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int L = l - j;
+        w[j * j] = sine ? rsd_get(Rs, L, mu) : rcd_get(Rc, L, mu);
+#pragma unroll
+        for (int kp = 1; kp <= j; ++kp) {
+            const int e0 = j * j + 2 * kp - 1;
+            const ddv cm = rcd_get(Rc, L, mu - kp), cp = rcd_get(Rc, L, mu + kp);
+            const ddv sm = rsd_get(Rs, L, mu - kp), sp = rsd_get(Rs, L, mu + kp);
+            const bool odd = kp & 1;
+            if (!sine) {
+                w[e0] = odd ? dd_sub(cm, cp) : dd_add(cm, cp);
+                w[e0 + 1] = odd ? dd_neg(dd_add(sm, sp)) : dd_sub(sp, sm);
+            } else {
+                w[e0] = odd ? dd_sub(sm, sp) : dd_add(sm, sp);
+                w[e0 + 1] = odd ? dd_add(cm, cp) : dd_sub(cm, cp);
+            }
+        }
+    }
+}
+
+// Radial orders of one primitive pair, accumulated in double-double into
+// O[j] = O^{(kmax-j)} (the FP64 radial_acc_fp64<OP_RA2N> with the Horner
+// variable R^2 and the accumulation kept in double-double).
+template <int J>
+__device__ __forceinline__ void radial_ra2n_dd(const PrimRec &pa, const PrimRec &pb, ddv R2d, int kmax, int la,
+                                               const Args2c &g, ddv (&O)[J])
+{
+    const int kmin = kmax - J + 1;
+    const double w = pa.w2c * pb.w2c;
+    const double c = pa.alpha + pb.alpha;
+    const double rc = rsqrt(c);
+    const double ic = rc * rc;
+    const double rho = pa.alpha * pb.alpha * ic;
+    const double T = rho * R2d.h;
+    const int n = __double2int_rn(g.omega);
+    const ddv cc = dd_sum(pa.alpha, pb.alpha);
+    const ddv icd = dd_inv(cc);
+    const ddv rhod = dd_mul(dd_prod(pa.alpha, pb.alpha), icd);
+    const ddv bcd = dd_mul(dd_prod(pb.alpha, pb.alpha), icd);
+    const ddv iad = dd_inv(ddv{pa.alpha, 0.0});
+    ddv tm[kRa2nMax + 1];
+#pragma unroll
+    for (int m = 0; m <= kRa2nMax; ++m) {
+        tm[m] = ddv{0.0, 0.0};
+        if (m <= n) {
+            const int j = n - m;
+            double rf = g.k.binom[n][j];                 // C(n, j) (la)_j: exact integer
+            for (int i = 0; i < j; ++i) rf *= (double)(la + i);
+            ddv t = ddv{rf, 0.0};
+            for (int i = 0; i < j; ++i) t = dd_mul(t, iad);
+            for (int i = 0; i < m; ++i) t = dd_mul(t, icd);
+            tm[m] = t;
+        }
+    }
+    ddv q[kRa2nMax + 2];
+    ddv bd = ddv{1.0, 0.0};
+#pragma unroll
+    for (int d = 0; d <= kRa2nMax; ++d) {
+        ddv sum = ddv{0.0, 0.0};
+#pragma unroll
+        for (int m = d; m <= kRa2nMax; ++m) sum = dd_add(sum, dd_mul_d(tm[m], g.k.ra2n_k[m][d]));
+        q[d] = dd_mul(bd, sum);
+        bd = dd_mul(bd, bcd);
+    }
+    q[kRa2nMax + 1] = ddv{0.0, 0.0};
+    const ddv mrho = dd_neg(rhod);
+    for (int k = 0; k < kmin; ++k) {
+#pragma unroll
+        for (int d = 0; d <= kRa2nMax; ++d) q[d] = dd_add(dd_mul_d(q[d + 1], (double)(d + 1)), dd_mul(mrho, q[d]));
+    }
+    // common factor of every order of this primitive pair (FP64: it scales each
+    // pair's term of the final sum as a whole)
+    const double we = w * kPi32 * ic * rc * exp(-T);
+#pragma unroll
+    for (int t = 0; t < J; ++t) {
+        ddv val = q[kRa2nMax];
+#pragma unroll
+        for (int d = kRa2nMax - 1; d >= 0; --d) val = dd_add(dd_mul(val, R2d), q[d]);
+        O[J - 1 - t] = dd_add(O[J - 1 - t], dd_mul_d(val, we));
+        if (t + 1 < J) {
+#pragma unroll
+            for (int d = 0; d <= kRa2nMax; ++d)
+                q[d] = dd_add(dd_mul_d(q[d + 1], (double)(d + 1)), dd_mul(mrho, q[d]));
+        }
+    }
+}
+
+template <int J>
+__device__ void pair_2c_ra2n_dd(const Args2c &g, int p)
+{
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l;
+    const Vec4 A = g.centers[sa.center];
+    const Vec4 B = g.centers[sb.center];
+    // the separation exactly (TwoSum) and R^2 in double-double
+    const ddv vx = dd_sum(A.x, -B.x), vy = dd_sum(A.y, -B.y), vz = dd_sum(A.z, -B.z);
+    const ddv R2d = dd_add(dd_add(dd_mul(vx, vx), dd_mul(vy, vy)), dd_mul(vz, vz));
+    const int kmax = la + lb;
+    ddv O[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) O[j] = ddv{0.0, 0.0};
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        radial_ra2n_dd<J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2d, kmax, la, g, O);
+    }
+    // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}
+    ddv ge[J * J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const ddv oj = ddv{O[j].h * g.k.pow2[kmax - j], O[j].l * g.k.pow2[kmax - j]};
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const ddv v = dd_mul(oj, dd_const(g.k.jB[j][kp], g.k.jB_lo[j][kp]));
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            ge[e0] = v;
+            if (kp) ge[e0 + 1] = v;
+        }
+    }
+    ddv Rc[(kLmax2c + 1) * (kLmax2c + 2) / 2], Rs[(kLmax2c + 1) * (kLmax2c + 2) / 2];
+    scaled_harmonics_dd(vx, vy, vz, la > lb ? la : lb, g.k, Rc, Rs);
+    const int nb = 2 * lb + 1;
+    ddv Ub[2 * kLmax2c + 1][J * J];
+    for (int mb = -lb; mb <= lb; ++mb) {
+        ddv w[J * J];
+        w_row_dd<J>(Rc, Rs, lb, mb, w);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) Ub[mb + lb][e] = w[e];
+    }
+    const double sgn_b = (lb & 1) ? -1.0 : 1.0;
+    double *out = g.out + g.out_off[p];
+    for (int ma = -la; ma <= la; ++ma) {
+        ddv ua[J * J];
+        w_row_dd<J>(Rc, Rs, la, ma, ua);
+#pragma unroll
+        for (int e = 0; e < J * J; ++e) ua[e] = dd_mul(ua[e], ge[e]);
+        const double Aa = g.k.A[la][ma < 0 ? -ma : ma] * sgn_b;
+        for (int mb = -lb; mb <= lb; ++mb) {
+            ddv s = ddv{0.0, 0.0};
+#pragma unroll
+            for (int e = 0; e < J * J; ++e) s = dd_fma(ua[e], Ub[mb + lb][e], s);
+            out[(ma + la) * nb + (mb + lb)] = Aa * (g.k.A[lb][mb < 0 ? -mb : mb] * (s.h + s.l));
+        }
+    }
+}
+
 template <int OP>
 __device__ __forceinline__ void pair_2c_fp64_dispatch(const Args2c &g, int p, int J)
 {
+    if (OP == OP_RA2N) {
+        switch (J) {
+        case 1: pair_2c_ra2n_dd<1>(g, p); return;
+        case 2: pair_2c_ra2n_dd<2>(g, p); return;
+        case 3: pair_2c_ra2n_dd<3>(g, p); return;
+        case 4: pair_2c_ra2n_dd<4>(g, p); return;
+        case 5: pair_2c_ra2n_dd<5>(g, p); return;
+        case 6: pair_2c_ra2n_dd<6>(g, p); return;
+        default: pair_2c_ra2n_dd<7>(g, p); return;
+        }
+    }
     switch (J) {
     case 1: pair_2c_fp64<OP, 1>(g, p); break;
     case 2: pair_2c_fp64<OP, 2>(g, p); break;

@@ -511,18 +511,23 @@ __device__ __forceinline__ void run_tile_mix_fused(const ArgsMixFused &g, const 
     if (lane >= tl.count) return;
     const int p = g.perm[tl.start + lane];
     const int la = tl.cls / (kLmax2c + 1), lb = tl.cls % (kLmax2c + 1);
+    // J = min(la, lb) + 1 <= 4: the host runs the classes with both l >=
+    // kMixedFp64MinL (J >= 5) in FP64, so they never reach this kernel
     switch ((la < lb ? la : lb) + 1) {
     case 1: pair_2c_mix_fused<1>(g, p); break;
     case 2: pair_2c_mix_fused<2>(g, p); break;
     case 3: pair_2c_mix_fused<3>(g, p); break;
     case 4: pair_2c_mix_fused<4>(g, p); break;
-    case 5: pair_2c_mix_fused<5>(g, p); break;
-    case 6: pair_2c_mix_fused<6>(g, p); break;
-    default: pair_2c_mix_fused<7>(g, p); break;
+    default: break;
     }
 }
 
-__global__ void __launch_bounds__(128) k_2c_mixed_fused_persistent(const ArgsMixFused g)
+// MinB = 0: registers as the compiler sees fit (126, four 128-thread CTAs
+// per SM); MinB = 5: at most 96 per thread, five CTAs per SM (more warps to
+// hide load and instruction-fetch latency, a few spilled values).  The
+// autotuner picks (shg_plan_2c_set_variant).
+template <int MinB>
+__global__ void __launch_bounds__(128, MinB) k_2c_mixed_fused_persistent(const ArgsMixFused g)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -535,7 +540,8 @@ __global__ void __launch_bounds__(128) k_2c_mixed_fused_persistent(const ArgsMix
     }
 }
 
-__global__ void __launch_bounds__(128) k_2c_mixed_fused_static(const ArgsMixFused g)
+template <int MinB>
+__global__ void __launch_bounds__(128, MinB) k_2c_mixed_fused_static(const ArgsMixFused g)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -547,14 +553,13 @@ __global__ void __launch_bounds__(128) k_2c_mixed_fused_static(const ArgsMixFuse
 template <int OP>
 __device__ __forceinline__ void mix_dispatch(const ArgsMix &g, int p, int J)
 {
+    // J <= 4 only: the classes with J >= 5 run in FP64 (see run_tile_mix_fused)
     switch (J) {
     case 1: pair_2c_mix<OP, 1>(g, p); break;
     case 2: pair_2c_mix<OP, 2>(g, p); break;
     case 3: pair_2c_mix<OP, 3>(g, p); break;
     case 4: pair_2c_mix<OP, 4>(g, p); break;
-    case 5: pair_2c_mix<OP, 5>(g, p); break;
-    case 6: pair_2c_mix<OP, 6>(g, p); break;
-    default: pair_2c_mix<OP, 7>(g, p); break;
+    default: break;
     }
 }
 
@@ -632,26 +637,31 @@ cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent,
     }
 }
 
-cudaError_t launch_2c_mixed_fused(const ArgsMixFused &a, int grid, bool persistent, cudaStream_t s, int threads)
+cudaError_t launch_2c_mixed_fused(const ArgsMixFused &a, int grid, bool persistent, cudaStream_t s, int threads,
+                                  int variant)
 {
     if (persistent) {
-        k_2c_mixed_fused_persistent<<<grid, threads, 0, s>>>(a);
+        if (variant) k_2c_mixed_fused_persistent<5><<<grid, threads, 0, s>>>(a);
+        else k_2c_mixed_fused_persistent<0><<<grid, threads, 0, s>>>(a);
     } else {
         const int tiles = a.tile_end - a.tile_begin;
         if (tiles <= 0) return cudaSuccess;
         const int wpb = threads / 32;
-        k_2c_mixed_fused_static<<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
+        if (variant) k_2c_mixed_fused_static<5><<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
+        else k_2c_mixed_fused_static<0><<<(tiles + wpb - 1) / wpb, threads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-int persistent_grid_2c_mixed_fused(int threads, int ctas_per_sm)
+int persistent_grid_2c_mixed_fused(int threads, int ctas_per_sm, int variant)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent, threads, 0) != cudaSuccess ||
-        per < 1)
+    const cudaError_t e = variant
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent<5>, threads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent<0>, threads, 0);
+    if (e != cudaSuccess || per < 1)
         per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     return (sms > 0 ? sms : 1) * per;

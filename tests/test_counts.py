@@ -61,3 +61,33 @@ def test_fused_flop_model():
         rest = [o for o in five if o[0] != op]
         extra = counts.fused_pair_flops(4, 4, 8, 8, five) - counts.fused_pair_flops(4, 4, 8, 8, rest)
         assert 0 < extra < counts.pair_flops(4, 4, 8, 8, op)
+
+
+def test_far_primitive_pairs_against_brute_force():
+    from paper_1701_06588_gb300 import workloads as W
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=400)
+    nf = counts.far_primitive_pairs(sh, pa, pb)
+    off = np.concatenate([[0], np.cumsum(sh["nprim"])])
+    c, co = sh["centers"], sh["center_of"]
+    for p in range(len(pa)):
+        A = sh["exps"][off[pa[p]]:off[pa[p] + 1]]
+        B = sh["exps"][off[pb[p]]:off[pb[p] + 1]]
+        R2 = float(((c[co[pa[p]]] - c[co[pb[p]]]) ** 2).sum())
+        assert nf[p] == sum(1 for a in A for b in B if a * b / (a + b) * R2 >= counts.KBOYS_TMAX)
+    assert 0 < nf.sum() < (sh["nprim"][pa] * sh["nprim"][pb]).sum()
+
+
+def test_fused_flops_count_far_pairs_as_one_multiply_add():
+    ops = [(counts.OP_COULOMB, 0.0), (counts.OP_ERFC, 0.11)]
+    la, lb, ka, kb = np.array([0, 2]), np.array([3, 2]), np.array([5, 4]), np.array([6, 3])
+    near = counts.fused_pair_flops(la, lb, ka, kb, ops)
+    half = counts.fused_pair_flops(la, lb, ka, kb, ops, n_far=(ka * kb) // 2)
+    allfar = counts.fused_pair_flops(la, lb, ka, kb, ops, n_far=ka * kb)
+    assert np.all(allfar < half) and np.all(half < near)
+    # per far primitive pair the 1/r part costs 2 flops instead of the Boys head,
+    # (-rho)^kmin and J orders; the attenuated erfc part is unchanged
+    J = np.minimum(la, lb) + 1
+    kmin = np.maximum(la, lb)
+    for i in range(2):
+        d = counts._fused_radial_flops(ops, J[i], kmin[i]) - counts._fused_radial_flops(ops, J[i], kmin[i], far=True)
+        assert d == (2 * int(np.ceil(np.log2(kmin[i] + 1))) + counts._boys(J[i]) + 3 * (J[i] - 1) + 3 * J[i] - 2)
