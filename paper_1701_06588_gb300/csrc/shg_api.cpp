@@ -1088,23 +1088,54 @@ void shg_plan_destroy(shg_plan_t *p)
     cudaFreeAsync(p->d.owner_block, p->d.stream);
     if (p->d.ev_fork) cudaEventDestroy(p->d.ev_fork);
     if (p->d.ev_join) cudaEventDestroy(p->d.ev_join);
+    if (p->d.ev_join2) cudaEventDestroy(p->d.ev_join2);
     if (p->d.side) cudaStreamDestroy(p->d.side);
+    if (p->d.side2) cudaStreamDestroy(p->d.side2);
     delete p;
 }
 
 
-// Second stream and fork/join events of a persistent plan, created on the
-// first mixed-precision execution that needs them: the FP64 launch of the
-// classes with both l >= kMixedFp64MinL (a few hundred heavy tiles) runs on it
-// beside the double-float persistent launch, so that the FP64 pipes work on
-// those tiles while the FP32 pipes of the rest of the GPU run the others.
-static int plan_side_stream(shg_plan_t *p)
+// Streams and events of a forked mixed-precision pass, created on the first
+// execution that needs them: the FP64 launch of the classes with both l >=
+// kMixedFp64MinL (a few hundred heavy tiles, one warp each) runs on `side`,
+// the double-float persistent launch on `side2`, so that the FP64 pipes work
+// on those tiles while the FP32 pipes of the rest of the GPU run the others.
+// Neither launch goes to the caller's stream, which only forks and joins (on
+// the legacy default stream a launch beside another stream's does not overlap
+// it).  `side` has the highest stream priority: its CTAs are dispatched first
+// and are resident before the persistent launch fills the SMs.
+static int plan_side_streams(shg_plan_t *p)
 {
     if (p->d.side) return SHG_OK;
-    if (cudaStreamCreateWithFlags(&p->d.side, cudaStreamNonBlocking) != cudaSuccess ||
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&p->d.side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->d.side2, cudaStreamNonBlocking, lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->d.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->d.ev_join, cudaEventDisableTiming) != cudaSuccess)
-        return fail(SHG_ECUDA, "side stream: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaEventCreateWithFlags(&p->d.ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->d.ev_join2, cudaEventDisableTiming) != cudaSuccess)
+        return fail(SHG_ECUDA, "side streams: %s", cudaGetErrorString(cudaGetLastError()));
+    return SHG_OK;
+}
+
+// fork: both side streams wait for the work already on s
+static int fork_sides(shg_plan_t *p, cudaStream_t s)
+{
+    int r = plan_side_streams(p);
+    if (r) return r;
+    SHG_CUDA(cudaEventRecord(p->d.ev_fork, s));
+    SHG_CUDA(cudaStreamWaitEvent(p->d.side, p->d.ev_fork, 0));
+    SHG_CUDA(cudaStreamWaitEvent(p->d.side2, p->d.ev_fork, 0));
+    return SHG_OK;
+}
+
+// join: s waits for both side streams
+static int join_sides(shg_plan_t *p, cudaStream_t s)
+{
+    SHG_CUDA(cudaEventRecord(p->d.ev_join, p->d.side));
+    SHG_CUDA(cudaEventRecord(p->d.ev_join2, p->d.side2));
+    SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join, 0));
+    SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join2, 0));
     return SHG_OK;
 }
 
@@ -1152,17 +1183,14 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
         m.boys_e = t->boys_e_mix;
         m.km = consts_mix();
         // classes with both l >= kMixedFp64MinL in FP64: beside the double-float
-        // launch on the side stream (persistent plans holding both kinds), else first
+        // launch on the side streams (persistent plans holding both kinds), else first
         const bool fork = p->d.schedule == SHG_SCHED_PERSISTENT && p->d.mixed_fp64_tiles > 0 &&
                           p->d.n_tiles > p->d.mixed_fp64_tiles;
         if (fork) {
-            r = plan_side_stream(p);
+            r = fork_sides(p, s);
             if (r) return r;
-            SHG_CUDA(cudaEventRecord(p->d.ev_fork, s));
-            SHG_CUDA(cudaStreamWaitEvent(p->d.side, p->d.ev_fork, 0));
             r = exec_fp64_static_range(p, op, omega, screen, off, out, 0, p->d.mixed_fp64_tiles, p->d.side);
             if (r) return r;
-            SHG_CUDA(cudaEventRecord(p->d.ev_join, p->d.side));
         } else {
             r = exec_fp64(p, op, omega, screen, off, out, nullptr, s, kMixedFp64Classes);
             if (r) return r;
@@ -1171,10 +1199,12 @@ int shg_plan_2c_exec(shg_plan_t *p, int op, double omega, double screen, int pre
             m.tile_begin = p->d.mixed_fp64_tiles;
             m.tile_end = p->d.n_tiles;
             if (m.tile_end <= m.tile_begin) return SHG_OK;
-            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+            const cudaStream_t sm = fork ? p->d.side2 : s;
+            SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), sm));
             m.counter = p->d.counter;
-            SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op, p->d.threads, p->d.ctas_per_sm), true, s, p->d.threads));
-            if (fork) SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join, 0));
+            SHG_CUDA(launch_2c_mixed(m, op, persistent_grid_2c_mixed(op, p->d.threads, p->d.ctas_per_sm), true, sm,
+                                     p->d.threads));
+            if (fork) return join_sides(p, s);
         } else {
             m.counter = nullptr;
             for (int cls = 0; cls < kNClass; ++cls) {
@@ -1326,18 +1356,16 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
     const bool mixed = precision == SHG_PREC_MIXED;
     const bool persistent = p->d.schedule == SHG_SCHED_PERSISTENT;
     // mixed precision on a persistent plan with both kinds of classes: the FP64
-    // tiles (one warp each) on the side stream, beside the double-float launch
+    // tiles (one warp each) and the double-float launch side by side on the plan's
+    // side streams
     const bool fork = mixed && persistent && p->d.mixed_fp64_tiles > 0 && p->d.n_tiles > p->d.mixed_fp64_tiles;
     if (fork) {
-        r = plan_side_stream(p);
+        r = fork_sides(p, s);
         if (r) return r;
-        SHG_CUDA(cudaEventRecord(p->d.ev_fork, s));
-        SHG_CUDA(cudaStreamWaitEvent(p->d.side, p->d.ev_fork, 0));
         a.tile_begin = 0;
         a.tile_end = p->d.mixed_fp64_tiles;
         a.counter = nullptr;
         SHG_CUDA(launch_2c_fused(a, 0, false, p->d.side, 32));
-        SHG_CUDA(cudaEventRecord(p->d.ev_join, p->d.side));
     } else if (persistent) {
         // FP64 pass: every tile, or under mixed precision the classes with both
         // l >= kMixedFp64MinL (a prefix of the persistent tile order)
@@ -1383,11 +1411,12 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
         m.tile_begin = p->d.mixed_fp64_tiles;
         m.tile_end = p->d.n_tiles;
         if (m.tile_end <= m.tile_begin) return SHG_OK;
-        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
+        const cudaStream_t sm = fork ? p->d.side2 : s;
+        SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), sm));
         m.counter = p->d.counter;
         SHG_CUDA(launch_2c_mixed_fused(m, persistent_grid_2c_mixed_fused(p->d.threads, p->d.ctas_per_sm, p->d.variant),
-                                       true, s, p->d.threads, p->d.variant));
-        if (fork) SHG_CUDA(cudaStreamWaitEvent(s, p->d.ev_join, 0));
+                                       true, sm, p->d.threads, p->d.variant));
+        if (fork) return join_sides(p, s);
     } else {
         m.counter = nullptr;
         for (int cls = 0; cls < kNClass; ++cls) {

@@ -35,8 +35,12 @@ template <bool NeedE>
 __device__ __forceinline__ void boys_head_near(double T, int kmax, const double *__restrict__ tab,
                                                const double *__restrict__ etab, double &f, double &e)
 {
-    const int i = __double2int_rn(T * 16.0);
-    const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
+    // grid index i = rint(16 T) without conversions: adding 1.5 * 2^52 rounds
+    // 16 T (< 2^31) to an integer held in the low word; T_i = i / 16 exactly
+    constexpr double kRound = 6755399441055744.0;
+    const double t16 = fma(T, 16.0, kRound);
+    const int i = __double2loint(t16);
+    const double y = fma(t16 - kRound, 0.0625, -T);        // -(T - T_i), exact
     const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
     const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
     f = fma(c67.y, y, c67.x);
@@ -64,8 +68,10 @@ __device__ __forceinline__ void boys_head(double T, int kmax, const double *__re
                                           const double *__restrict__ etab, const Consts &k, double &f, double &e)
 {
     if (T < kBoysTmax) {
-        const int i = __double2int_rn(T * 16.0);
-        const double y = fma(-0.0625, (double)i, T) * -1.0;   // -(T - T_i), exact
+        constexpr double kRound = 6755399441055744.0;          // 1.5 * 2^52: see boys_head_near
+        const double t16 = fma(T, 16.0, kRound);
+        const int i = __double2loint(t16);
+        const double y = fma(t16 - kRound, 0.0625, -T);        // -(T - T_i), exact
         const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
         const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
         f = fma(c67.y, y, c67.x);

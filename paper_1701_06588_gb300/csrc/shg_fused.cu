@@ -22,12 +22,12 @@ namespace shg {
 namespace {
 using namespace dev;
 
-// attenuated radial sum (the erf(omega r)/r part of Table S1) of one primitive pair
+// attenuated radial sum (the erf(omega r)/r part of Table S1) of one primitive pair;
+// T' = omega^2 T / (omega^2 + rho) < omega^2 R^2 stays on the Taylor grid here
 template <int J>
-__device__ __forceinline__ void att_acc(double om, double rho, double T, int kmax, int kmin, double pre,
+__device__ __forceinline__ void att_acc(double om, double w2, double rho, double T, int kmax, int kmin, double pre,
                                         const ArgsFused &g, double (&O)[J])
 {
-    const double w2 = om * om;
     const double rw = rsqrt(w2 + rho);
     const double s = w2 * rw * rw;
     const double f = -rho * s;
@@ -62,6 +62,7 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
     // exp(-T) from the Boys head: the downward recursion needs it for J > 1,
     // the overlap reuses it
     const bool need_e = J > 1 || f_ov;
+    const double w2_erf = g.w_erf * g.w_erf, w2_erfc = g.w_erfc * g.w_erfc;
 
     double Oov[J], Oco[J], Oer[J], Ox[J], Oga[J];
 #pragma unroll
@@ -134,8 +135,8 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
                     far = fma(ca.fw, cb.fw, far);
                 }
             }
-            if (f_er) att_acc<J>(g.w_erf, rho, T, kmax, kmin, pre, g, Oer);
-            if (f_x) att_acc<J>(g.w_erfc, rho, T, kmax, kmin, pre, g, Ox);
+            if (f_er) att_acc<J>(g.w_erf, w2_erf, rho, T, kmax, kmin, pre, g, Oer);
+            if (f_x) att_acc<J>(g.w_erfc, w2_erfc, rho, T, kmax, kmin, pre, g, Ox);
         }
     }
     if (far != 0.0) {

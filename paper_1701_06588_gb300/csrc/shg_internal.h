@@ -208,8 +208,11 @@ struct PlanDev {
     int ctas_per_sm = 0;           // persistent CTAs per SM, 0 = occupancy limit
     int variant = 0;               // compiled kernel variant of the double-float fused pass
                                    // (0: free register count, 1: <= 96 registers, 5 CTAs per SM)
-    cudaStream_t side = nullptr;   // second stream of the mixed passes (FP64 high-l classes)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // streams of a mixed-precision pass that runs the FP64 high-l tiles beside the
+    // double-float launch (created on first use): side (highest priority) takes the
+    // FP64 launch, side2 the double-float one; the caller's stream forks and joins
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     void *owner_block = nullptr;   // device allocation holding all of the above
     cudaStream_t stream = nullptr;
 };

@@ -658,9 +658,8 @@ int persistent_grid_2c_mixed_fused(int threads, int ctas_per_sm, int variant)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const cudaError_t e = variant
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent<5>, threads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_mixed_fused_persistent<0>, threads, 0);
+    const void *kern = variant ? (const void *)k_2c_mixed_fused_persistent<5> : (const void *)k_2c_mixed_fused_persistent<0>;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
     if (e != cudaSuccess || per < 1)
         per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
