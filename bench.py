@@ -706,6 +706,10 @@ def other_configs(args):
         ms = _events_ms(lambda: L.shg_eval_2c_grad(b.handle, len(pa), d_pa, d_pb, op, om, 0, d_off, w, ga, gb, st), 3)
         entry[opn] = {"ms_per_pass": ms, "pair_gradients_per_s": len(pa) / (ms * 1e-3),
                       "algorithmic_tflops": counts.workload_grad_flops(sh, pa, pb, op) / (ms * 1e-3) / 1e12}
+        # mixed: double-float radial orders (classes with both l >= 4 in FP64)
+        ms = _events_ms(lambda: L.shg_eval_2c_grad(b.handle, len(pa), d_pa, d_pb, op, om, L.SHG_PREC_MIXED, d_off, w,
+                                                   ga, gb, st), 3)
+        entry[opn + "_mixed"] = {"ms_per_pass": ms, "pair_gradients_per_s": len(pa) / (ms * 1e-3)}
     res["c5_grad_500k_l5_k12"] = entry
     b.close()
     # molecular assembly: 300-atom molecule with family basis sets, all shell pairs a <= b

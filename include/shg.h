@@ -301,6 +301,12 @@ int shg_eval_3c_aab(const shg_basis_t *orb, const shg_basis_t *aux, int64_t n_tr
  *   d_w_offsets, d_upstream_w   device int64[n_pairs] / doubles: W_p blocks,
  *                               same layout as shg_eval_2c output
  *   d_grad_a, d_grad_b          device double[n_pairs][3]; d_grad_b may be NULL
+ *   precision                   SHG_PREC_FP64, or SHG_PREC_MIXED: radial orders
+ *                               in double-float on the FP32 pipes, the angular
+ *                               part (harmonics, their gradients, W and the
+ *                               contractions with W_p) in FP64; the classes with
+ *                               both la and lb >= 4 wholly in FP64.  Not for
+ *                               SHG_OP_RA2N (SHG_EINVAL)
  * No atomics: per-atom sums are left to the caller.
  */
 int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n_pairs, const int32_t *d_pair_a, const int32_t *d_pair_b,

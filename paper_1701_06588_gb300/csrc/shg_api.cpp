@@ -1597,8 +1597,43 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
     a.grad_a = grad_a;
     a.grad_b = grad_b;
     a.k = consts();
-    cudaError_t e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
-    if (e == cudaSuccess && p->d.n_tiles > 0) e = launch_2c_grad(a, op, precision, persistent_grid_2c_grad(op, precision), s);
+    // mixed precision: the classes with both l >= kMixedFp64MinL (the leading
+    // tiles of the persistent order) in FP64, the others with double-float
+    // radial orders and the FP64 angular part
+    const bool mixed = precision == SHG_PREC_MIXED;
+    a.tile_end = mixed ? p->d.mixed_fp64_tiles : p->d.n_tiles;
+    cudaError_t e = cudaSuccess;
+    if (a.tile_end > 0) {
+        e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = launch_2c_grad(a, op, SHG_PREC_FP64, persistent_grid_2c_grad(op, SHG_PREC_FP64), s);
+    }
+    if (e == cudaSuccess && mixed && p->d.n_tiles > p->d.mixed_fp64_tiles) {
+        ArgsGradMix gm;
+        gm.g = a;
+        ArgsMix &m = gm.m;
+        m.shells = basis->d.shells;
+        m.prims = basis->d.mprims;
+        m.centers = basis->d.mcenters;
+        m.pair_a = pa;
+        m.pair_b = pb;
+        m.perm = p->d.perm;
+        m.tiles = p->d.tiles;
+        m.tile_begin = p->d.mixed_fp64_tiles;
+        m.tile_end = p->d.n_tiles;
+        m.counter = p->d.counter;
+        m.out_off = nullptr;
+        m.out = nullptr;
+        m.omega = split2(omega);
+        m.omega2 = split2((long double)omega * omega);
+        m.omega_d = omega;
+        m.screen_thresh = 0.0;
+        m.screen = basis->d.screen;
+        m.boys = t->boys_mix;
+        m.boys_e = t->boys_e_mix;
+        m.km = consts_mix();
+        e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = launch_2c_grad_mixed(gm, op, s);
+    }
     shg_plan_destroy(p);
     if (e != cudaSuccess) return fail(SHG_ECUDA, "gradient launch: %s", cudaGetErrorString(e));
     return SHG_OK;

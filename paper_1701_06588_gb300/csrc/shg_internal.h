@@ -309,6 +309,10 @@ struct ArgsMix {
     ConstsMix km;
 };
 
+// Mixed-precision gradient: double-float radial orders (m) and the FP64 angular
+// vector-Jacobian product (g: centers, constants, upstream weights, outputs).
+struct ArgsGradMix;
+
 // Fused multi-operator pass in double-float (outputs as ArgsFused).
 struct ArgsMixFused {
     const ShellRec *shells;
@@ -326,6 +330,11 @@ struct ArgsMixFused {
     const float4 *boys;
     const float2 *boys_e;
     ConstsMix km;
+};
+
+struct ArgsGradMix {
+    Args2c g;
+    ArgsMix m;
 };
 
 // Arguments of the three-index kernels (by value).
@@ -359,6 +368,7 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, 
                               int *d_err, cudaStream_t s);
 cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
 cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s);
+cudaError_t launch_2c_grad_mixed(const ArgsGradMix &args, int op, cudaStream_t s);
 cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s,
                             int threads = 128);
 int persistent_grid_2c_mixed(int op, int threads = 128, int ctas_per_sm = 0);

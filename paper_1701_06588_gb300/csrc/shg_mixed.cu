@@ -19,6 +19,7 @@
 #include "shg_device.cuh"
 #include "shg_df.cuh"
 #include "shg_mix_angular.cuh"
+#include "shg_grad_angular.cuh"
 
 namespace shg {
 namespace {
@@ -251,14 +252,13 @@ __device__ __forceinline__ df mix_boys_prefactor(const MixPair &m, const MixPrim
     return mul(mul(ldf(km.two_pi52), m.rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
 }
 
-// S_j += (-1)^k base (2 rho)^-j X_k for one primitive pair, k = la+lb-j.
+// S_j += hp[j] X_k for one primitive pair, k = kmax-j, j = 0..J-1: the
+// operator parts X_k of Table S1 without their (-rho)^k, which hp carries
+// (with the weights and the 2^k of the assembly).
 template <int OP, int J>
-__device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim &pb, df R2, int la, int lb,
-                                               const ArgsMix &g, df (&S)[J])
+__device__ __forceinline__ void radial_mix_orders(const MixPair &m, const df (&hp)[J], int kmax, const MixPrim &pa,
+                                                  const MixPrim &pb, const ArgsMix &g, df (&S)[J])
 {
-    const int kmax = la + lb;
-    df hp[J];                       // base (2 rho)^-j (-1)^{kmax-j}
-    const MixPair m = mix_setup<J>(pa, pb, R2, la, lb, hp);
     if (OP == OP_OVERLAP) {
         mix_overlap<J>(m, hp, g.km, S);
     } else if (OP == OP_GAUSS) {
@@ -295,6 +295,114 @@ __device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim 
         if (OP == OP_ERF || OP == OP_ERFC)
             mix_attenuated<J>(m, hp, pre, ldf(g.omega), ldf(g.omega2), OP == OP_ERFC, kmax, g.boys, g.boys_e, g.km, S);
     }
+}
+
+// S_j += (-1)^k base (2 rho)^-j X_k for one primitive pair, k = la+lb-j.
+template <int OP, int J>
+__device__ __forceinline__ void radial_acc_mix(const MixPrim &pa, const MixPrim &pb, df R2, int la, int lb,
+                                               const ArgsMix &g, df (&S)[J])
+{
+    df hp[J];                       // base (2 rho)^-j (-1)^{kmax-j}
+    const MixPair m = mix_setup<J>(pa, pb, R2, la, lb, hp);
+    radial_mix_orders<OP, J>(m, hp, la + lb, pa, pb, g, S);
+}
+
+// ------------------------------------------------------------------------- //
+// Vector-Jacobian product of the two-center blocks (Eq. dev_ab) with the     //
+// radial orders O^{(k)}, k = la+lb+1-J .. la+lb+1, in double-float and the   //
+// angular part (harmonics, their gradients, W and the contractions with the  //
+// upstream weights) in FP64 (gradang::grad_from_orders).  The orders carry   //
+// this path's scaling S_j = 2^k O^{(k)}: for k = la+lb+1-j,                  //
+//   2^k (-rho)^k (2 alpha)^-la (2 beta)^-lb = (-1)^k (beta/c)^la (alpha/c)^lb (2 rho)^{1-j},
+// so the weights are those of the integrals shifted by one order, with
+// (-1)^{kmax+1} base 2 rho in front.                                         //
+// ------------------------------------------------------------------------- //
+template <int OP, int J>
+__device__ void pair_grad_mix(const ArgsGradMix &a, int p)
+{
+    const ArgsMix &g = a.m;
+    const ShellRec sa = g.shells[g.pair_a[p]];
+    const ShellRec sb = g.shells[g.pair_b[p]];
+    const int la = sa.l, lb = sb.l, kmax = la + lb;
+    const MixCenter A = g.centers[sa.center];
+    const MixCenter B = g.centers[sb.center];
+    const df vx = sub(ldf(A.x), ldf(B.x)), vy = sub(ldf(A.y), ldf(B.y)), vz = sub(ldf(A.z), ldf(B.z));
+    const df R2 = add(add(mul(vx, vx), mul(vy, vy)), mul(vz, vz));
+    df S[J + 1];
+#pragma unroll
+    for (int j = 0; j <= J; ++j) S[j] = df_f(0.0f);
+    const int Kb = sb.nprim, npp = sa.nprim * Kb;
+    for (int q = 0; q < npp; ++q) {
+        const int ia = q / Kb, ib = q - ia * Kb;
+        const MixPrim pa = g.prims[sa.prim_off + ia], pb = g.prims[sb.prim_off + ib];
+        df hp[J];
+        const MixPair m = mix_setup<J>(pa, pb, R2, la, lb, hp);
+        df hq[J + 1];
+        hq[0] = neg(mul(scale2(m.rho, 2.0f), hp[0]));
+#pragma unroll
+        for (int j = 0; j < J; ++j) hq[j + 1] = hp[j];
+        radial_mix_orders<OP, J + 1>(m, hq, kmax + 1, pa, pb, g, S);
+    }
+    // f0[e] = 2^{kmax-j} (2j-1)!! B O^{(kmax-j)} = jB S_{j+1},
+    // f1[e] = 2^{kmax-j} (2j-1)!! B O^{(kmax-j+1)} = jB S_j / 2
+    const Args2c &f = a.g;
+    double f0[J * J], f1[J * J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const double s0 = to_double(S[j + 1]), s1 = 0.5 * to_double(S[j]);
+#pragma unroll
+        for (int kp = 0; kp <= j; ++kp) {
+            const int e0 = j * j + (kp == 0 ? 0 : 2 * kp - 1);
+            f0[e0] = f.k.jB[j][kp] * s0;
+            f1[e0] = f.k.jB[j][kp] * s1;
+            if (kp) {
+                f0[e0 + 1] = f0[e0];
+                f1[e0 + 1] = f1[e0];
+            }
+        }
+    }
+    const Vec4 Ad = f.centers[sa.center];
+    const Vec4 Bd = f.centers[sb.center];
+    const double v[3] = {Ad.x - Bd.x, Ad.y - Bd.y, Ad.z - Bd.z};
+    gradang::grad_from_orders<J>(f, p, la, lb, v, f0, f1);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_2c_grad_mixed_persistent(const ArgsGradMix a)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.m.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0) + a.m.tile_begin;
+        if (t >= a.m.tile_end) break;
+        const Tile tl = a.m.tiles[t];
+        if (lane < tl.count) {
+            const int la = tl.cls / (kLmax2c + 1), lb = tl.cls % (kLmax2c + 1);
+            const int p = a.m.perm[tl.start + lane];
+            // J <= 4: the classes with both l >= kMixedFp64MinL run in FP64
+            switch ((la < lb ? la : lb) + 1) {
+            case 1: pair_grad_mix<OP, 1>(a, p); break;
+            case 2: pair_grad_mix<OP, 2>(a, p); break;
+            case 3: pair_grad_mix<OP, 3>(a, p); break;
+            case 4: pair_grad_mix<OP, 4>(a, p); break;
+            default: break;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int OP>
+static int grid_grad_mix()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_grad_mixed_persistent<OP>, 128, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    return (sms > 0 ? sms : 1) * per;
 }
 
 // Angular part and store of one pair from its contracted S_j (runtime J).
@@ -623,6 +731,20 @@ static cudaError_t launch_mix_op(const ArgsMix &a, int grid, int threads, bool p
 }
 
 }  // namespace
+
+cudaError_t launch_2c_grad_mixed(const ArgsGradMix &a, int op, cudaStream_t s)
+{
+    switch (op) {
+    case OP_OVERLAP: k_2c_grad_mixed_persistent<OP_OVERLAP><<<grid_grad_mix<OP_OVERLAP>(), 128, 0, s>>>(a); break;
+    case OP_COULOMB: k_2c_grad_mixed_persistent<OP_COULOMB><<<grid_grad_mix<OP_COULOMB>(), 128, 0, s>>>(a); break;
+    case OP_ERFC: k_2c_grad_mixed_persistent<OP_ERFC><<<grid_grad_mix<OP_ERFC>(), 128, 0, s>>>(a); break;
+    case OP_ERF: k_2c_grad_mixed_persistent<OP_ERF><<<grid_grad_mix<OP_ERF>(), 128, 0, s>>>(a); break;
+    case OP_GAUSS: k_2c_grad_mixed_persistent<OP_GAUSS><<<grid_grad_mix<OP_GAUSS>(), 128, 0, s>>>(a); break;
+    case OP_GCOUL: k_2c_grad_mixed_persistent<OP_GCOUL><<<grid_grad_mix<OP_GCOUL>(), 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_2c_mixed(const ArgsMix &a, int op, int grid, bool persistent, cudaStream_t s, int threads)
 {

@@ -7,6 +7,7 @@ Element-wise bar, atomic units, normalised functions:
   FP64 integrals    rtol 1e-12, atol 1e-14, gamma 1e-15
   gradients         rtol 1e-10, atol 1e-12, gamma 1e-15
   mixed precision   rtol 1e-10, atol 1e-14, gamma 2e-13
+  mixed gradients   rtol 1e-10, atol 1e-12, gamma 2e-13
 
 Both conditioning terms belong to element e itself (no block maximum):
 
@@ -38,6 +39,7 @@ import numpy as np
 TOL_FP64 = (1e-12, 1e-14, 1e-15)
 TOL_GRAD = (1e-10, 1e-12, 1e-15)
 TOL_MIXED = (1e-10, 1e-14, 2e-13)
+TOL_GRAD_MIXED = (1e-10, 1e-12, 2e-13)
 
 # the bars with no conditioning term (the benchmark spec's plain tolerances)
 PLAIN_FP64 = (1e-12, 1e-14, 0.0)

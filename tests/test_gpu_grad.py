@@ -213,3 +213,48 @@ def test_grad_full_size_c5_sampled(shg, opname, op, omega):
     ex = np.abs(ga[idx] - ref) / bar
     assert ex.max() <= 1.0, (opname, ex.max())
     b.close()
+
+
+@pytest.mark.parametrize("name,n", [("c5_grad_500k_l5_k12", 1200), ("c2_200k_l4_k8", 800)])
+@pytest.mark.parametrize("opname,op,omega", GRAD_OPS)
+def test_grad_mixed_against_oracle(shg, name, n, opname, op, omega):
+    """Mixed precision: double-float radial orders, FP64 angular part; the
+    oracle's vector-Jacobian products with the mixed gradient bar."""
+    import torch
+    from tests.parity import TOL_GRAD_MIXED
+    sh, pa, pb = W.make(name, n=n)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = np.random.default_rng(4).uniform(-1, 1, total)
+    ga, gb = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega,
+                              precision="mixed")
+    torch.cuda.synchronize()
+    ga, gb = ga.cpu().numpy(), gb.cpu().numpy()
+    np.testing.assert_array_equal(gb, -ga)
+    ref, scale = _oracle_vjp(sh, pa, pb, op, omega, w)
+    rtol, atol, gamma = TOL_GRAD_MIXED
+    ex = np.abs(ga - ref) / (rtol * np.abs(ref) + atol + gamma * scale)
+    assert ex.max() <= 1.0, (opname, ex.max(), np.unravel_index(ex.argmax(), ex.shape))
+    b.close()
+
+
+def test_grad_mixed_runs_high_l_classes_in_fp64(shg):
+    """Pairs with both l >= 4 take the FP64 gradient kernel under mixed
+    precision (bitwise equal to FP64); the others the double-float radial
+    orders (not bitwise equal)."""
+    import torch
+    sh, pa, pb = W.make("c5_grad_500k_l5_k12", n=3000)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = torch.from_numpy(np.random.default_rng(9).uniform(-1, 1, total)).cuda()
+    g64, _ = shg.eval_2c_grad(b, pa, pb, "coulomb", w, offsets=off, precision="fp64")
+    gmx, _ = shg.eval_2c_grad(b, pa, pb, "coulomb", w, offsets=off, precision="mixed")
+    torch.cuda.synchronize()
+    g64, gmx = g64.cpu().numpy(), gmx.cpu().numpy()
+    hi = (sh["l"][pa] >= 4) & (sh["l"][pb] >= 4)
+    assert hi.sum() > 20
+    np.testing.assert_array_equal(g64[hi], gmx[hi])
+    assert not np.array_equal(g64[~hi], gmx[~hi])
+    with pytest.raises(Exception):
+        shg.eval_2c_grad(b, pa, pb, "ra2n", w, offsets=off, omega=1.0, precision="mixed")
+    b.close()

@@ -3,7 +3,7 @@ inputs:
 
   FP64 integrals   |x - ref| <= 1e-12 |ref| + 1e-14
   mixed precision  |x - ref| <= 1e-10 |ref| + 1e-14
-  gradients        |g - ref| <= 1e-10 |ref| + 1e-12
+  gradients        |g - ref| <= 1e-10 |ref| + 1e-12   (FP64 and mixed)
 
 Inputs: the synthetic recipes with every contraction coefficient replaced by
 its magnitude, so that no contraction over primitives cancels (Eq.
@@ -66,8 +66,9 @@ def test_plain_bars_same_sign_coefficients(shg, name):
         print("%s %-12s %-14s plain excess %.3g  well-conditioned %.4f  max rel %s" % ((name,) + r))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("opname,op,omega", [("coulomb", 1, 0.0), ("erfc", 2, 0.11)])
-def test_plain_gradient_bar_same_sign_coefficients(shg, opname, op, omega):
+def test_plain_gradient_bar_same_sign_coefficients(shg, opname, op, omega, precision):
     """Vector-Jacobian products with upstream weights uniform in [0, 1] on
     1,000 pairs of the gradient recipe (l up to 5, K up to 12), same-sign
     coefficients; components whose magnitude sum sum_e |W_e| |dI_e/dR| is
@@ -78,7 +79,8 @@ def test_plain_gradient_bar_same_sign_coefficients(shg, opname, op, omega):
     b = shg.Basis(sh)
     off, total = b.pair_offsets(pa, pb)
     w = np.random.default_rng(17).uniform(0.0, 1.0, total)
-    ga, _ = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega)
+    ga, _ = shg.eval_2c_grad(b, pa, pb, opname, torch.from_numpy(w).cuda(), offsets=off, omega=omega,
+                             precision=precision)
     torch.cuda.synchronize()
     ga = ga.cpu().numpy()
     b.close()
@@ -88,5 +90,6 @@ def test_plain_gradient_bar_same_sign_coefficients(shg, opname, op, omega):
     wc = scale <= KAPPA_WC * np.abs(ref)
     assert wc.mean() >= 0.9, wc.mean()
     ex = np.abs(ga - ref)[wc] / (PLAIN_GRAD[0] * np.abs(ref[wc]) + PLAIN_GRAD[1])
-    print("plain gradient bar %s: excess %.3g over %.4f of the components" % (opname, ex.max(), wc.mean()))
+    print("plain gradient bar %s %s: excess %.3g over %.4f of the components" % (precision, opname, ex.max(),
+                                                                                  wc.mean()))
     assert ex.max() <= 1.0, ex.max()
