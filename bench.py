@@ -624,6 +624,22 @@ def profile_case(args):
     print(json.dumps({"profile_case": case, "units": units, "ms": ms}))
 
 
+def _plan_create_ms(basis, plan, reps=20):
+    """Median host wall time of shg_plan_2c_create + shg_plan_destroy on
+    device-resident pair lists (the planner's one synchronisation included)."""
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    st = torch.cuda.current_stream().cuda_stream
+    ts = []
+    for _ in range(reps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = L.shg_plan_2c_create(basis.handle, plan.n, plan.pair_a, plan.pair_b, L.SHG_SCHED_PERSISTENT, st)
+        L.shg_plan_destroy(h)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return sorted(ts[2:])[reps // 2]
+
+
 def other_configs(args):
     """Throughput of the other synthetic workloads (CUDA events, inputs resident)."""
     import numpy as np
@@ -643,7 +659,7 @@ def other_configs(args):
         d_off = torch.from_numpy(off).cuda()
         out = torch.empty(total, dtype=torch.float64, device="cuda")
         plan = api.Plan2c(b, pa, pb)
-        entry = {"pairs": len(pa), "operators": [o[0] for o in ops]}
+        entry = {"pairs": len(pa), "operators": [o[0] for o in ops], "plan_create_ms": _plan_create_ms(b, plan)}
         flops = sum(counts.workload_flops(sh, pa, pb, api.L.OPERATORS[n]) for n, _ in ops)
         for prec in precs:
             ms = sum(_events_ms(lambda n=n, w=w: plan.exec(n, d_off, out, omega=w, precision=prec), 3 if len(pa) > 1e5

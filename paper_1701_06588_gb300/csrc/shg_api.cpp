@@ -1599,11 +1599,22 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
     a.k = consts();
     // mixed precision: the classes with both l >= kMixedFp64MinL (the leading
     // tiles of the persistent order) in FP64, the others with double-float
-    // radial orders and the FP64 angular part
+    // radial orders and the FP64 angular part.  With both kinds present the
+    // two launches run side by side on the plan's side streams (as in
+    // shg_plan_2c_exec_fused): the FP64 tiles one warp each, statically.
     const bool mixed = precision == SHG_PREC_MIXED;
+    const bool fork = mixed && p->d.mixed_fp64_tiles > 0 && p->d.n_tiles > p->d.mixed_fp64_tiles;
     a.tile_end = mixed ? p->d.mixed_fp64_tiles : p->d.n_tiles;
     cudaError_t e = cudaSuccess;
-    if (a.tile_end > 0) {
+    if (fork) {
+        r = fork_sides(p, s);
+        if (r) {
+            shg_plan_destroy(p);
+            return r;
+        }
+        a.counter = nullptr;
+        e = launch_2c_grad(a, op, SHG_PREC_FP64, 0, p->d.side, 32);
+    } else if (a.tile_end > 0) {
         e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
         if (e == cudaSuccess) e = launch_2c_grad(a, op, SHG_PREC_FP64, persistent_grid_2c_grad(op, SHG_PREC_FP64), s);
     }
@@ -1631,10 +1642,15 @@ int shg_eval_2c_grad(const shg_basis_t *basis, int64_t n, const int32_t *pa, con
         m.boys = t->boys_mix;
         m.boys_e = t->boys_e_mix;
         m.km = consts_mix();
-        e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = launch_2c_grad_mixed(gm, op, s);
+        const cudaStream_t sm = fork ? p->d.side2 : s;
+        e = cudaMemsetAsync(p->d.counter, 0, sizeof(int), sm);
+        if (e == cudaSuccess) e = launch_2c_grad_mixed(gm, op, sm);
     }
+    // the plan's memory is released in the order of s: join first, also after
+    // a failed launch (the other side stream may hold a running kernel)
+    if (fork) r = join_sides(p, s);
     shg_plan_destroy(p);
+    if (r) return r;
     if (e != cudaSuccess) return fail(SHG_ECUDA, "gradient launch: %s", cudaGetErrorString(e));
     return SHG_OK;
 }

@@ -79,14 +79,23 @@ __device__ __forceinline__ void grad_dispatch(const Args2c &g, int p, int J)
     }
 }
 
+// With a tile counter every warp takes tiles from it until none are left; with
+// none (g.counter == nullptr) warp w of block b takes tile tile_begin + b *
+// warps_per_block + w once (a static launch over a short tile range).
 template <int OP>
 __global__ void __launch_bounds__(128) k_2c_grad_fp64_persistent(const Args2c g)
 {
     const int lane = threadIdx.x & 31;
-    for (;;) {
+    const int nw = blockDim.x >> 5;
+    for (int it = 0;; ++it) {
         int t = 0;
-        if (lane == 0) t = atomicAdd(g.counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        if (g.counter) {
+            if (lane == 0) t = atomicAdd(g.counter, 1);
+            t = __shfl_sync(0xffffffffu, t, 0) + g.tile_begin;
+        } else {
+            if (it) break;
+            t = g.tile_begin + blockIdx.x * nw + (threadIdx.x >> 5);
+        }
         if (t >= g.tile_end) break;
         const Tile tl = g.tiles[t];
         if (lane < tl.count) {
@@ -111,17 +120,24 @@ static int grid_for()
 
 }  // namespace
 
-cudaError_t launch_2c_grad(const Args2c &a, int op, int precision, int grid, cudaStream_t s)
+cudaError_t launch_2c_grad(const Args2c &a, int op, int precision, int grid, cudaStream_t s, int threads)
 {
     (void)precision;
+    if (threads < 32 || threads > 128 || threads % 32) return cudaErrorInvalidValue;
+    if (!a.counter) {
+        // static: one warp per tile of [tile_begin, tile_end)
+        const int per = threads / 32;
+        grid = (a.tile_end - a.tile_begin + per - 1) / per;
+        if (grid <= 0) return cudaSuccess;
+    }
     switch (op) {
-    case OP_OVERLAP: k_2c_grad_fp64_persistent<OP_OVERLAP><<<grid, 128, 0, s>>>(a); break;
-    case OP_COULOMB: k_2c_grad_fp64_persistent<OP_COULOMB><<<grid, 128, 0, s>>>(a); break;
-    case OP_ERFC: k_2c_grad_fp64_persistent<OP_ERFC><<<grid, 128, 0, s>>>(a); break;
-    case OP_ERF: k_2c_grad_fp64_persistent<OP_ERF><<<grid, 128, 0, s>>>(a); break;
-    case OP_GAUSS: k_2c_grad_fp64_persistent<OP_GAUSS><<<grid, 128, 0, s>>>(a); break;
-    case OP_GCOUL: k_2c_grad_fp64_persistent<OP_GCOUL><<<grid, 128, 0, s>>>(a); break;
-    case OP_RA2N: k_2c_grad_fp64_persistent<OP_RA2N><<<grid, 128, 0, s>>>(a); break;
+    case OP_OVERLAP: k_2c_grad_fp64_persistent<OP_OVERLAP><<<grid, threads, 0, s>>>(a); break;
+    case OP_COULOMB: k_2c_grad_fp64_persistent<OP_COULOMB><<<grid, threads, 0, s>>>(a); break;
+    case OP_ERFC: k_2c_grad_fp64_persistent<OP_ERFC><<<grid, threads, 0, s>>>(a); break;
+    case OP_ERF: k_2c_grad_fp64_persistent<OP_ERF><<<grid, threads, 0, s>>>(a); break;
+    case OP_GAUSS: k_2c_grad_fp64_persistent<OP_GAUSS><<<grid, threads, 0, s>>>(a); break;
+    case OP_GCOUL: k_2c_grad_fp64_persistent<OP_GCOUL><<<grid, threads, 0, s>>>(a); break;
+    case OP_RA2N: k_2c_grad_fp64_persistent<OP_RA2N><<<grid, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

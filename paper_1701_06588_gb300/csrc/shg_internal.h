@@ -367,7 +367,8 @@ struct Args3c {
 cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, const int *d_bin_rank,
                               int *d_err, cudaStream_t s);
 cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
-cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s);
+// grid is ignored when args.counter is null (static launch, one warp per tile)
+cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s, int threads = 128);
 cudaError_t launch_2c_grad_mixed(const ArgsGradMix &args, int op, cudaStream_t s);
 cudaError_t launch_2c_mixed(const ArgsMix &args, int op, int grid, bool persistent, cudaStream_t s,
                             int threads = 128);
