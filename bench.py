@@ -54,8 +54,9 @@ def parse():
                    help="N > 1: every rank evaluates the whole workload (weak scaling) instead of its "
                         "cost-balanced slice of the one pair list (strong scaling, the default)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--e2e-chunks", type=int, default=4,
-                   help="contiguous chunks of the end-to-end pipeline (read-back of chunk k overlaps chunk k+1)")
+    p.add_argument("--e2e-chunks", type=int, default=0,
+                   help="contiguous chunks of the end-to-end pipeline (read-back of chunk k overlaps chunk k+1); "
+                        "0: the pipeline's default for the precision")
     p.add_argument("--n-pairs", type=int, default=None, help="smaller case of the same recipe (profiling only)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="precision of the headline path (the other forms are reported beside it)")
@@ -469,10 +470,11 @@ def run_ours(args, rank, world):
             parts["exec_and_d2h"].append(t4 - t3)
     e2e_single_s = statistics.mean(e2e_times) if e2e_times else float("nan")
     e2e_s = e2e_single_s
-    if fused and args.e2e_chunks > 1:
+    e2e_chunks = args.e2e_chunks or api.HostPipeline2c.default_chunks(args.precision)
+    if fused:
         # the public pipeline: the pair list planned in contiguous chunks, each
         # chunk's read-back overlapping the next chunk's fused pass
-        pipe = api.HostPipeline2c(basis, n_chunks=args.e2e_chunks, launch=tuned[form])
+        pipe = api.HostPipeline2c(basis, n_chunks=e2e_chunks, launch=tuned[form])
         times = []
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
@@ -534,7 +536,7 @@ def run_ours(args, rank, world):
                 "what": ("per step, api.HostPipeline2c: pinned H2D of pair lists, offsets and centers, "
                          "shg_basis_set_centers, then the pair list in %d contiguous chunks: shg_plan_2c_create "
                          "and shg_plan_2c_exec_fused (both operators) per chunk, the D2H of chunk k's blocks to "
-                         "pinned memory on a copy stream overlapping chunk k+1" % args.e2e_chunks if fused else
+                         "pinned memory on a copy stream overlapping chunk k+1" % e2e_chunks if fused else
                          "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
                          "shg_plan_2c_create, one shg_plan_2c_exec per operator, D2H of all blocks to pinned memory (operator "
                          "k's copy on a second stream overlaps operator k+1's kernel)"),

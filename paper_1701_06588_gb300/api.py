@@ -296,7 +296,8 @@ class HostPipeline2c:
     """Two-center blocks from host pair lists into host output arrays, with
     the read-back overlapped with the computation.
 
-    The pair list is split into n_chunks contiguous slices, each planned on
+    The pair list is split into n_chunks contiguous slices (default:
+    default_chunks(precision)), each planned on
     the device (shg_plan_2c_create) and evaluated by one fused pass
     (shg_plan_2c_exec_fused) on the compute stream; as soon as slice k is
     done, its blocks (a contiguous range of every output, since the offsets
@@ -306,13 +307,21 @@ class HostPipeline2c:
     tensors, one per operator.  Device buffers are kept between calls.
     """
 
-    def __init__(self, basis, n_chunks=4, launch=None, schedule="persistent"):
+    def __init__(self, basis, n_chunks=None, launch=None, schedule="persistent"):
         self.basis = basis
-        self.n_chunks = max(1, int(n_chunks))
+        self.n_chunks = None if n_chunks is None else max(1, int(n_chunks))
         self.launch = launch
         self.schedule = schedule
         self.copy_stream = torch.cuda.Stream()
         self._dev = {}
+
+    @staticmethod
+    def default_chunks(precision):
+        """FP64: two chunks (the read-back of the first hides behind the
+        second).  Mixed: one, since every chunk of a mixed pass waits for its
+        own FP64 launch of the classes with both l >= 4, whose slowest tile
+        sets a fixed time per chunk."""
+        return 1 if precision == "mixed" else 2
 
     def _buf(self, name, n, dtype):
         t = self._dev.get(name)
@@ -338,7 +347,8 @@ class HostPipeline2c:
             self.basis.set_centers(centers)
         torch.cuda.nvtx.range_pop()
         off_h = offsets.numpy()
-        bounds = [n * k // self.n_chunks for k in range(self.n_chunks + 1)]
+        chunks = self.n_chunks or self.default_chunks(precision)
+        bounds = [n * k // chunks for k in range(chunks + 1)]
         plans = []
         for k in range(self.n_chunks):
             lo, hi = bounds[k], bounds[k + 1]

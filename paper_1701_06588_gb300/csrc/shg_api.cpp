@@ -149,15 +149,17 @@ void fill_consts(Consts &k)
         }
 }
 
-// Boys table, computed in long double: F_N(T) from its power series
+// Boys tables, computed in long double: F_N(T) from its power series
 //   F_N(T) = exp(-T) sum_k (2T)^k / ((2N+1)(2N+3)...(2N+2k+1))
-// at N = 40, then the stable downward recursion
-//   F_{n-1}(T) = (2T F_n(T) + exp(-T)) / (2n-1).
-void make_boys_table(double *tab, double *etab)
+// at N = 48, then the stable downward recursion
+//   F_{n-1}(T) = (2T F_n(T) + exp(-T)) / (2n-1);
+// at T_i = i / per_unit, i = 0..ngrid-1: tab[(i kBoysN + n) nterms + t] =
+// F_{n+t}(T_i) / t!, etab[i] = exp(-T_i).
+void make_boys_table(int per_unit, int ngrid, int nterms, double *tab, double *etab)
 {
     const int ntop = 48;
-    for (int i = 0; i < kBoysGrid; ++i) {
-        const long double T = (long double)i / 16.0L;
+    for (int i = 0; i < ngrid; ++i) {
+        const long double T = (long double)i / (long double)per_unit;
         const long double e = std::exp(-T);
         long double term = 1.0L / (2 * ntop + 1), sum = term;
         for (int k = 1; k < 20000; ++k) {
@@ -170,9 +172,9 @@ void make_boys_table(double *tab, double *etab)
         for (int n = ntop; n > 0; --n) F[n - 1] = (2 * T * F[n] + e) / (long double)(2 * n - 1);
         for (int n = 0; n < kBoysN; ++n) {
             long double tf = 1;
-            for (int t = 0; t < kBoysTerms; ++t) {
+            for (int t = 0; t < nterms; ++t) {
                 if (t > 0) tf *= t;
-                tab[((size_t)i * kBoysN + n) * kBoysTerms + t] = (double)(F[n + t] / tf);
+                tab[((size_t)i * kBoysN + n) * nterms + t] = (double)(F[n + t] / tf);
             }
         }
         etab[i] = (double)e;
@@ -434,13 +436,25 @@ const DeviceTables *device_tables_impl(int **ranks, int **rank3 = nullptr)
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &st = g_dev[dev];
     if (!st.ready) {
-        std::vector<double> tab((size_t)kBoysGrid * kBoysN * kBoysTerms), etab(kBoysGrid);
-        make_boys_table(tab.data(), etab.data());
-        std::vector<float4> mtab((size_t)kBoysGrid * kBoysN * 4);
-        std::vector<float2> metab(kBoysGrid);
-        for (int i = 0; i < kBoysGrid; ++i) {
+        // FP64 table (step 1/32): c0..c3 as doubles, c4..c6 as floats
+        std::vector<double> raw((size_t)kBoysGrid * kBoysN * 7), etab(kBoysGrid);
+        make_boys_table(32, kBoysGrid, 7, raw.data(), etab.data());
+        std::vector<double> tab((size_t)kBoysGrid * kBoysN * kBoysStride, 0.0);
+        for (size_t q = 0; q < (size_t)kBoysGrid * kBoysN; ++q) {
+            double *d = &tab[q * kBoysStride];
+            const double *r = &raw[q * 7];
+            for (int t = 0; t < 4; ++t) d[t] = r[t];
+            const float f[4] = {(float)r[4], (float)r[5], (float)r[6], 0.0f};
+            std::memcpy(d + 4, f, sizeof f);
+        }
+        // double-float table (step 1/16)
+        std::vector<double> mraw((size_t)kBoysGridMix * kBoysN * kBoysTerms), metab_d(kBoysGridMix);
+        make_boys_table(16, kBoysGridMix, kBoysTerms, mraw.data(), metab_d.data());
+        std::vector<float4> mtab((size_t)kBoysGridMix * kBoysN * 4);
+        std::vector<float2> metab(kBoysGridMix);
+        for (int i = 0; i < kBoysGridMix; ++i) {
             for (int n = 0; n < kBoysN; ++n) {
-                const double *cf = &tab[((size_t)i * kBoysN + n) * kBoysTerms];
+                const double *cf = &mraw[((size_t)i * kBoysN + n) * kBoysTerms];
                 float4 *q = &mtab[((size_t)i * kBoysN + n) * 4];
                 const float2 c0 = split2(cf[0]), c1 = split2(cf[1]), c2 = split2(cf[2]), c3 = split2(cf[3]);
                 q[0] = make_float4(c0.x, c0.y, c1.x, c1.y);
@@ -448,7 +462,7 @@ const DeviceTables *device_tables_impl(int **ranks, int **rank3 = nullptr)
                 q[2] = make_float4((float)cf[4], (float)cf[5], (float)cf[6], (float)cf[7]);
                 q[3] = make_float4(0, 0, 0, 0);
             }
-            metab[i] = split2(etab[i]);
+            metab[i] = split2(metab_d[i]);
         }
         double *d_tab = nullptr, *d_e = nullptr;
         float4 *d_mtab = nullptr;
@@ -693,7 +707,9 @@ int shg_basis_create(int n_shells, const int32_t *l, const int32_t *nprim, const
             p.wN = c.hi;
             pr[off + i] = p;
             const dd cw = dd_mul(w2c, ia);
-            cpr[off + i] = CoulPrim{cw.hi, dd_mul(cw, dd_sqrt(ia)).hi};
+            // sqrt(2 pi^{5/2}) folded into cw: pre = cw_a cw_b / sqrt(c)
+            const dd s2p52 = dd_sqrt(dd_from(2.0L * 17.493418327624862846262821679871554L));   // 2 pi^{5/2}
+            cpr[off + i] = CoulPrim{dd_mul(cw, s2p52).hi, dd_mul(cw, dd_sqrt(ia)).hi};
         }
         sh[s] = ShellRec{L, K, (int)off, center_of_shell[s]};
     }

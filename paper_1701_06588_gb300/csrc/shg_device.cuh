@@ -8,7 +8,7 @@ namespace shg {
 namespace dev {
 
 constexpr double kPi32 = 5.568327996831707845284817982118835702;      // pi^{3/2}
-constexpr double kTwoPi52 = 34.98683665524972497843742820021;         // 2 pi^{5/2}
+constexpr double kTwoPi52 = 34.98683665524972569252564335974;         // 2 pi^{5/2}
 constexpr double kPi3 = 31.00627668029982017547631506710139520;       // pi^3
 constexpr double kSqrtPiHalf = 0.886226925452758013649083741670572591; // sqrt(pi)/2
 constexpr double kPi = 3.141592653589793238462643383279502884;        // pi
@@ -26,8 +26,73 @@ enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP
 //   F_{k-1} = (2T F_k + exp(-T)) / (2k-1).                                 //
 // The two branches differ only in how F_kmax and exp(-T) are obtained, so  //
 // a warp whose lanes straddle T = 120 runs both short heads and one tail.  //
+//                                                                          //
+// Grid T_i = i/32, |d| <= 1/64: seven terms leave a remainder below         //
+// (1/64)^7/7! = 5e-17 of F (F_{n+t} <= F_n).  Terms 0..3 are summed in      //
+// FP64; terms 4..6, together at most (1/64)^4/4! = 2.5e-9 of F, in FP32     //
+// (relative error ~2e-7 there, so ~5e-16 of F), which moves three of the    //
+// seven multiply-adds of each series off the FP64 pipe.  The float <->      //
+// double conversions are done on the integer pipe (dbl_to_flt, flt_to_dbl). //
 // ------------------------------------------------------------------------- //
 __device__ __forceinline__ double powi(double x, int n);
+
+// float with the sign, exponent and leading 23 significand bits of x
+// (truncated); 0 when |x| is below the normal float range.  For |x| < 2^127.
+__device__ __forceinline__ float dbl_to_flt(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;                     // float exponent field
+    const unsigned b = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return e > 0 ? __uint_as_float(b) : 0.0f;
+}
+
+// the double equal to x (normal x or 0; denormal floats read as 0)
+__device__ __forceinline__ double flt_to_dbl(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return e ? __hiloint2double((int)hi, (int)(b << 29)) : 0.0;
+}
+
+// One Taylor head: grid index i and y = T_i - T (exact) for T < kBoysTmax.
+// Adding 1.5 * 2^52 rounds 32 T (< 2^31) to an integer held in the low word,
+// so T_i = i / 32 needs no float-to-int conversion.
+__device__ __forceinline__ int boys_grid(double T, double &y)
+{
+    constexpr double kRound = 6755399441055744.0;
+    const double t32 = fma(T, 32.0, kRound);
+    y = fma(t32 - kRound, 0.03125, -T);
+    return __double2loint(t32);
+}
+
+// F_n(T) from the entry of (i, n): c0..c3 in FP64, c4..c6 in FP32 (see above)
+__device__ __forceinline__ double boys_series(const double *__restrict__ tab, int i, int n, double y)
+{
+    const double *c = tab + ((size_t)i * kBoysN + n) * kBoysStride;
+    const double2 c01 = __ldg(reinterpret_cast<const double2 *>(c));
+    const double2 c23 = __ldg(reinterpret_cast<const double2 *>(c) + 1);
+    const float4 c46 = __ldg(reinterpret_cast<const float4 *>(c + 4));
+    const float yf = dbl_to_flt(y);
+    const float t = fmaf(fmaf(c46.z, yf, c46.y), yf, c46.x);
+    double f = fma(flt_to_dbl(t), y, c23.y);
+    f = fma(f, y, c23.x);
+    f = fma(f, y, c01.y);
+    return fma(f, y, c01.x);
+}
+
+// exp(-T) = exp(-T_i) exp(y), |y| <= 1/64: Taylor to degree 6 (remainder
+// < 5e-17), terms 4..6 in FP32 as for F
+__device__ __forceinline__ double boys_exp(const double *__restrict__ etab, int i, double y)
+{
+    const float yf = dbl_to_flt(y);
+    const float t = fmaf(fmaf(1.0f / 720.0f, yf, 1.0f / 120.0f), yf, 1.0f / 24.0f);
+    double x = fma(flt_to_dbl(t), y, 1.0 / 6.0);
+    x = fma(x, y, 0.5);
+    x = fma(x, y, 1.0);
+    x = fma(x, y, 1.0);
+    return x * __ldg(etab + i);
+}
 
 // F_kmax by the Taylor head of the table, T < kBoysTmax; with NeedE also
 // exp(-T) (else e is left untouched).
@@ -35,32 +100,10 @@ template <bool NeedE>
 __device__ __forceinline__ void boys_head_near(double T, int kmax, const double *__restrict__ tab,
                                                const double *__restrict__ etab, double &f, double &e)
 {
-    // grid index i = rint(16 T) without conversions: adding 1.5 * 2^52 rounds
-    // 16 T (< 2^31) to an integer held in the low word; T_i = i / 16 exactly
-    constexpr double kRound = 6755399441055744.0;
-    const double t16 = fma(T, 16.0, kRound);
-    const int i = __double2loint(t16);
-    const double y = fma(t16 - kRound, 0.0625, -T);        // -(T - T_i), exact
-    const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
-    const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
-    f = fma(c67.y, y, c67.x);
-    f = fma(f, y, c45.y);
-    f = fma(f, y, c45.x);
-    f = fma(f, y, c23.y);
-    f = fma(f, y, c23.x);
-    f = fma(f, y, c01.y);
-    f = fma(f, y, c01.x);
-    if (NeedE) {
-        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
-        double x = fma(1.0 / 5040.0, y, 1.0 / 720.0);
-        x = fma(x, y, 1.0 / 120.0);
-        x = fma(x, y, 1.0 / 24.0);
-        x = fma(x, y, 1.0 / 6.0);
-        x = fma(x, y, 0.5);
-        x = fma(x, y, 1.0);
-        x = fma(x, y, 1.0);
-        e = x * __ldg(etab + i);
-    }
+    double y;
+    const int i = boys_grid(T, y);
+    f = boys_series(tab, i, kmax, y);
+    if (NeedE) e = boys_exp(etab, i, y);
 }
 
 // F_kmax and exp(-T) (0 where it is below 1e-52).
@@ -68,28 +111,10 @@ __device__ __forceinline__ void boys_head(double T, int kmax, const double *__re
                                           const double *__restrict__ etab, const Consts &k, double &f, double &e)
 {
     if (T < kBoysTmax) {
-        constexpr double kRound = 6755399441055744.0;          // 1.5 * 2^52: see boys_head_near
-        const double t16 = fma(T, 16.0, kRound);
-        const int i = __double2loint(t16);
-        const double y = fma(t16 - kRound, 0.0625, -T);        // -(T - T_i), exact
-        const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)i * kBoysN + kmax) * kBoysTerms);
-        const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c + 0);
-        f = fma(c67.y, y, c67.x);
-        f = fma(f, y, c45.y);
-        f = fma(f, y, c45.x);
-        f = fma(f, y, c23.y);
-        f = fma(f, y, c23.x);
-        f = fma(f, y, c01.y);
-        f = fma(f, y, c01.x);
-        // exp(y), |y| <= 1/32: Taylor to degree 7 (remainder < 3e-17)
-        e = fma(1.0 / 5040.0, y, 1.0 / 720.0);
-        e = fma(e, y, 1.0 / 120.0);
-        e = fma(e, y, 1.0 / 24.0);
-        e = fma(e, y, 1.0 / 6.0);
-        e = fma(e, y, 0.5);
-        e = fma(e, y, 1.0);
-        e = fma(e, y, 1.0);
-        e *= __ldg(etab + i);
+        double y;
+        const int i = boys_grid(T, y);
+        f = boys_series(tab, i, kmax, y);
+        e = boys_exp(etab, i, y);
     } else {
         // F_kmax = (2kmax-1)!! (2T)^-kmax sqrt(pi/(4T)); exp(-T) < 1e-52 is dropped
         const double rT = rsqrt(T);
@@ -288,10 +313,30 @@ __device__ __forceinline__ ddv dd_inv(ddv a)
 // Radial terms of one primitive pair, accumulated into the contracted        //
 // O[j] = O^{(kmax-j)}, j = 0..J-1 (Table S1 and Eq. O_rab2_deriv).          //
 //   w = w_alpha w_beta = N_a N_b c_alpha c_beta / ((2alpha)^la (2beta)^lb)  //
+// Coulomb-type operators (1/r, erfc, erf) accumulate only the top order     //
+// O[0] and the exp(-T') terms E[j], j >= 1, of the downward recursion,      //
+// which radial_finish_fp64 runs once on the contracted sums: for both the   //
+// 1/r and the attenuated term, X_n = P q^n F_n(T') satisfies                //
+//   X_n = (-2R^2 X_{n+1} + P q^n exp(-T')) / (2n+1)                        //
+// (2T'/q = -2R^2), the same for every primitive pair of the shell pair,     //
+// with the two terms of one sign for each primitive pair.                   //
 // ------------------------------------------------------------------------- //
+template <int OP>
+__device__ __forceinline__ constexpr bool coulomb_type() { return OP == OP_COULOMB || OP == OP_ERFC || OP == OP_ERF; }
+
+template <int OP, int J>
+__device__ __forceinline__ void radial_finish_fp64(double R2, int kmax, const Consts &k, double (&O)[J],
+                                                   const double (&E)[J])
+{
+    if (!coulomb_type<OP>()) return;
+    const double m2R2 = -2.0 * R2;
+#pragma unroll
+    for (int j = 1; j < J; ++j) O[j] = fma(m2R2, O[j - 1], E[j]) * k.inv_int[2 * (kmax - j) + 1];
+}
+
 template <int OP, int J>
 __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec &pb, double R2, int kmax, int la,
-                                                const Args2c &g, double (&O)[J])
+                                                const Args2c &g, double (&O)[J], double (&E)[J])
 {
     const int kmin = kmax - J + 1;
     const double w = pa.w2c * pb.w2c;
@@ -402,33 +447,35 @@ __device__ __forceinline__ void radial_acc_fp64(const PrimRec &pa, const PrimRec
             O[J - 1 - t] += pre * v[0];
         }
     } else {
-        // Coulomb-type: 2 pi^{5/2} / (alpha beta sqrt(c)) * ...
-        const double pre = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc;
+        // Coulomb-type: 2 pi^{5/2} / (alpha beta sqrt(c)) (-rho)^kmin * ...
+        const double pk = w * kTwoPi52 * pa.inv_alpha * pb.inv_alpha * rc * powi(-rho, kmin);
         if (OP == OP_COULOMB || OP == OP_ERFC) {
-            double F[J];
-            boys_top<J>(T, kmax, g.boys, g.boys_e, g.k, F);
-            double q = pre * powi(-rho, kmin);
+            double F, e;
+            boys_head(T, kmax, g.boys, g.boys_e, g.k, F, e);
+            double q = pk;
 #pragma unroll
-            for (int j = J - 1; j >= 0; --j) {
-                O[j] += q * F[j];
+            for (int j = J - 1; j >= 1; --j) {
+                E[j] = fma(q, e, E[j]);
                 q *= -rho;
             }
+            O[0] = fma(q, F, O[0]);
         }
         if (OP == OP_ERF || OP == OP_ERFC) {
-            // omega/sqrt(omega^2+rho) (-omega^2 rho/(omega^2+rho))^k F_k(omega^2 T/(omega^2+rho))
-            const double w2 = g.omega * g.omega;
-            const double rw = rsqrt(w2 + rho);
-            const double s = w2 * rw * rw;
-            const double f = -rho * s;
-            double F[J];
-            boys_top<J>(s * T, kmax, g.boys, g.boys_e, g.k, F);
-            double q = pre * g.omega * rw * powi(f, kmin);
+            // omega/sqrt(omega^2+rho) (-omega^2 rho/(omega^2+rho))^k F_k(omega^2 T/(omega^2+rho)):
+            // with u = omega/sqrt(omega^2+rho), s = u^2 the order kmin factor is pk u s^kmin
+            const double u = g.omega * rsqrt(g.omega * g.omega + rho);
+            const double s = u * u;
+            double F, e;
+            boys_head(s * T, kmax, g.boys, g.boys_e, g.k, F, e);
+            double q = pk * u * powi(s, kmin);
             if (OP == OP_ERFC) q = -q;
+            const double f = -rho * s;
 #pragma unroll
-            for (int j = J - 1; j >= 0; --j) {
-                O[j] += q * F[j];
+            for (int j = J - 1; j >= 1; --j) {
+                E[j] = fma(q, e, E[j]);
                 q *= f;
             }
+            O[0] = fma(q, F, O[0]);
         }
     }
 }

@@ -22,23 +22,37 @@ namespace shg {
 namespace {
 using namespace dev;
 
-// attenuated radial sum (the erf(omega r)/r part of Table S1) of one primitive pair;
-// T' = omega^2 T / (omega^2 + rho) < omega^2 R^2 stays on the Taylor grid here
+// Downward recursion after the contraction.  For one primitive pair the
+// Coulomb-type radial term of order n, X_n = P q^n F_n(T') (1/r: P = pre,
+// q = -rho, T' = T; attenuated: P = pre omega / sqrt(omega^2 + rho),
+// q = -rho s, T' = s T with s = omega^2 / (omega^2 + rho)), obeys, by the
+// Boys recursion F_n = (2T' F_{n+1} + exp(-T')) / (2n+1),
+//   X_n = (-2R^2 X_{n+1} + P q^n exp(-T')) / (2n+1),
+// since 2T'/q = -2R^2 for both.  -2R^2 is the same for every primitive pair
+// of the shell pair, so the contracted orders follow the same recursion:
+// per primitive pair only the top order (from the Taylor head) and the
+// terms E_n = P q^n exp(-T') are summed.  The two terms of each step have
+// the same sign for every primitive pair, so the contracted recursion
+// loses nothing against the magnitude sum of the contraction.
+
+// attenuated part (the erf(omega r)/r term of Table S1) of one primitive pair:
+// pk = pre (-rho)^kmin, so P q^kmin = pk u s^kmin with u = omega / sqrt(omega^2 + rho)
 template <int J>
-__device__ __forceinline__ void att_acc(double om, double w2, double rho, double T, int kmax, int kmin, double pre,
-                                        const ArgsFused &g, double (&O)[J])
+__device__ __forceinline__ void att_head(double om, double w2, double rho, double T, int kmax, int kmin, double pk,
+                                         const ArgsFused &g, double (&O)[J], double (&E)[J])
 {
-    const double rw = rsqrt(w2 + rho);
-    const double s = w2 * rw * rw;
-    const double f = -rho * s;
-    double F[J];
-    boys_top<J>(s * T, kmax, g.boys, g.boys_e, g.k, F);
-    double q = pre * om * rw * powi(f, kmin);
+    const double u = om * rsqrt(w2 + rho);
+    const double s = u * u;
+    double F, e;
+    boys_head(s * T, kmax, g.boys, g.boys_e, g.k, F, e);
+    double w = pk * u * powi(s, kmin);
+    const double q = -rho * s;
 #pragma unroll
-    for (int j = J - 1; j >= 0; --j) {
-        O[j] = fma(q, F[j], O[j]);
-        q *= f;
+    for (int j = J - 1; j >= 1; --j) {
+        E[j] = fma(w, e, E[j]);
+        w *= q;
     }
+    O[0] = fma(w, F, O[0]);
 }
 
 template <int J>
@@ -64,9 +78,11 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
     const bool need_e = J > 1 || f_ov;
     const double w2_erf = g.w_erf * g.w_erf, w2_erfc = g.w_erfc * g.w_erfc;
 
-    double Oov[J], Oco[J], Oer[J], Ox[J], Oga[J];
+    // O*[j]: contracted order kmax - j of each operator; E*[j], j >= 1: the
+    // exp(-T') terms of the contracted recursion (index 0 unused)
+    double Oov[J], Oco[J], Oer[J], Ox[J], Oga[J], Eco[J], Eer[J], Ex[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) Oov[j] = Oco[j] = Oer[j] = Ox[j] = Oga[j] = 0.0;
+    for (int j = 0; j < J; ++j) Oov[j] = Oco[j] = Oer[j] = Ox[j] = Oga[j] = Eco[j] = Eer[j] = Ex[j] = 0.0;
     // far-field part of the 1/r sum: sum of fw_a fw_b over the primitive pairs
     // with T >= kBoysTmax (see CoulPrim), multiplied by the per-pair order
     // factors after the loop
@@ -82,19 +98,13 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
         const double rho = pa.alpha * pb.alpha * ic;
         const double T = rho * R2;
         const bool near = T < kBoysTmax;
-        const double mrk = (f_ov || (f_co && near)) ? powi(-rho, kmin) : 0.0;
+        const double mrk = (f_ov || f_co || f_er || f_x) ? powi(-rho, kmin) : 0.0;
         // Boys head of the 1/r sum first: it also yields exp(-T) for the overlap
         // (0 for T >= kBoysTmax, where the overlap term is below e^-120 of its prefactor)
-        double Fc[J], eT = 0.0;
+        double Fc = 0.0, eT = 0.0;
         if (f_co && near) {
-            double f;
-            if (need_e) boys_head_near<true>(T, kmax, g.boys, g.boys_e, f, eT);
-            else boys_head_near<false>(T, kmax, g.boys, g.boys_e, f, eT);
-            // downward recursion F_{k-1} = (2T F_k + exp(-T)) / (2k-1)
-            Fc[0] = f;
-            const double twoT = T + T;
-#pragma unroll
-            for (int j = 1; j < J; ++j) Fc[j] = fma(twoT, Fc[j - 1], eT) * g.k.inv_int[2 * (kmax - j + 1) - 1];
+            if (need_e) boys_head_near<true>(T, kmax, g.boys, g.boys_e, Fc, eT);
+            else boys_head_near<false>(T, kmax, g.boys, g.boys_e, Fc, eT);
         }
         if (f_ov) {
             // (pi/c)^{3/2} exp(-T) (-rho)^k
@@ -120,24 +130,35 @@ __device__ void pair_2c_fused(const ArgsFused &g, int p)
             }
         }
         if (f_co || f_er || f_x) {
-            // 2 pi^{5/2} w / (alpha beta sqrt(c)) times the Boys sums
+            // 2 pi^{5/2} w / (alpha beta sqrt(c)) (-rho)^kmin, times the Boys sums
             const CoulPrim ca = g.cprims[sa.prim_off + ia], cb = g.cprims[sb.prim_off + ib];
-            const double pre = kTwoPi52 * ca.cw * cb.cw * rc;
+            const double pk = ca.cw * cb.cw * rc * mrk;
             if (f_co) {
                 if (near) {
-                    double t = pre * mrk;
+                    double w = pk;
 #pragma unroll
-                    for (int j = J - 1; j >= 0; --j) {
-                        Oco[j] = fma(t, Fc[j], Oco[j]);
-                        t *= -rho;
+                    for (int j = J - 1; j >= 1; --j) {
+                        Eco[j] = fma(w, eT, Eco[j]);
+                        w *= -rho;
                     }
+                    Oco[0] = fma(w, Fc, Oco[0]);
                 } else {
                     far = fma(ca.fw, cb.fw, far);
                 }
             }
-            if (f_er) att_acc<J>(g.w_erf, w2_erf, rho, T, kmax, kmin, pre, g, Oer);
-            if (f_x) att_acc<J>(g.w_erfc, w2_erfc, rho, T, kmax, kmin, pre, g, Ox);
+            if (f_er) att_head<J>(g.w_erf, w2_erf, rho, T, kmax, kmin, pk, g, Oer, Eer);
+            if (f_x) att_head<J>(g.w_erfc, w2_erfc, rho, T, kmax, kmin, pk, g, Ox, Ex);
         }
+    }
+    // contracted downward recursion, orders kmax-1 .. kmin (the far field,
+    // exact per order, is added afterwards)
+    const double m2R2 = -2.0 * R2;
+#pragma unroll
+    for (int j = 1; j < J; ++j) {
+        const double inv = g.k.inv_int[2 * (kmax - j) + 1];
+        Oco[j] = fma(m2R2, Oco[j - 1], Eco[j]) * inv;
+        Oer[j] = fma(m2R2, Oer[j - 1], Eer[j]) * inv;
+        Ox[j] = fma(m2R2, Ox[j - 1], Ex[j]) * inv;
     }
     if (far != 0.0) {
         // pi^3 (-1)^n (2n-1)!! (2R^2)^{-n} / R for n = kmin .. kmax (R > 0: T >= kBoysTmax)

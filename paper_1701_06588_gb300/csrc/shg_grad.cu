@@ -36,14 +36,15 @@ __device__ void pair_grad_fp64(const Args2c &g, int p)
     const int kmax = la + lb;
 
     // Ox[j] = O^{(kmax+1-j)}, j = 0..J
-    double Ox[J + 1];
+    double Ox[J + 1], Ex[J + 1];
 #pragma unroll
-    for (int j = 0; j <= J; ++j) Ox[j] = 0.0;
+    for (int j = 0; j <= J; ++j) Ox[j] = Ex[j] = 0.0;
     const int Kb = sb.nprim, npp = sa.nprim * Kb;
     for (int q = 0; q < npp; ++q) {
         const int ia = q / Kb, ib = q - ia * Kb;
-        radial_acc_fp64<OP, J + 1>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax + 1, la, g, Ox);
+        radial_acc_fp64<OP, J + 1>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax + 1, la, g, Ox, Ex);
     }
+    radial_finish_fp64<OP, J + 1>(R2, kmax + 1, g.k, Ox, Ex);
     // f0[e]: factor of Q~_j with O^{(kmax-j)}, f1[e]: with O^{(kmax-j+1)}
     double f0[J * J], f1[J * J];
 #pragma unroll

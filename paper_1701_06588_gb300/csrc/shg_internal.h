@@ -23,14 +23,21 @@ constexpr int kTile = 32;         // pairs per warp tile
 constexpr int kMixedFp64MinL = 4;
 inline bool mixed_runs_fp64(int cls) { return cls / 7 >= kMixedFp64MinL && cls % 7 >= kMixedFp64MinL; }
 
-// Boys table: F_{n+t}(T_i)/t!, T_i = i/16, i = 0..kBoysGrid-1, n < kBoysN,
-// t = 0..7; Taylor expansion about the nearest grid point (|delta| <= 1/32).
+// Boys tables: Taylor coefficients F_{n+t}(T_i)/t! about grid points T_i,
+// n < kBoysN; Taylor expansion about the nearest grid point.
+//   FP64 table: T_i = i/32, i = 0..kBoysGrid-1 (|delta| <= 1/64), t = 0..6,
+//     per (i, n) kBoysStride doubles: c0..c3 as doubles, c4..c6 as floats
+//     (and one float of padding), 48 bytes.
+//   double-float table: T_i = i/16, i = 0..kBoysGridMix-1 (|delta| <= 1/32),
+//     t = 0..7 (c0..c3 as hi/lo float pairs, c4..c7 as floats).
 // Above kBoysTmax, F_n(T) = (2n-1)!! / (2T)^n sqrt(pi/(4T)) to better than
 // 1e-30 relative for n <= 16 (the neglected terms carry exp(-T)).
-constexpr int kBoysGrid = 1921;   // covers T < 120
+constexpr int kBoysGrid = 3841;     // covers T < 120 at step 1/32
+constexpr int kBoysStride = 6;
+constexpr int kBoysGridMix = 1921;  // covers T < 120 at step 1/16
 constexpr double kBoysTmax = 120.0;
-constexpr int kBoysN = 16;        // orders n = 0..15 from the table
-constexpr int kBoysTerms = 8;
+constexpr int kBoysN = 16;          // orders n = 0..15 from the tables
+constexpr int kBoysTerms = 8;       // terms of the double-float table
 
 // Per-shell screening data (host-computed): smallest exponent, sum |N c| over
 // the primitives, and (l / (alpha_min e))^{l/2} (1 for l = 0).
@@ -62,7 +69,7 @@ struct GauntEnt {
 };
 
 // Per-primitive weights of the Coulomb-type radial terms (Table S1), 16 bytes:
-//   cw = w2c / alpha            so that 2 pi^{5/2} w / (alpha beta sqrt(c)) = 2 pi^{5/2} cw_a cw_b / sqrt(c)
+//   cw = sqrt(2 pi^{5/2}) w2c / alpha   so that 2 pi^{5/2} w / (alpha beta sqrt(c)) = cw_a cw_b / sqrt(c)
 //   fw = w2c alpha^{-3/2}       the far-field weight: for T >= kBoysTmax every order of
 //                               w 2 pi^{5/2} / (alpha beta sqrt(c)) (-rho)^n F_n(T) equals
 //                               fw_a fw_b pi^3 (-1)^n (2n-1)!! (2R^2)^{-n} / R
@@ -113,15 +120,15 @@ void fill_consts_mix(ConstsMix &k);
 
 // Device-resident tables owned by the library, one set per device.
 struct DeviceTables {
-    const double *boys;   // [kBoysGrid][kBoysN][kBoysTerms]
-    const double *boys_e; // [kBoysGrid] exp(-T_i)
+    const double *boys;   // [kBoysGrid][kBoysN][kBoysStride] (layout above)
+    const double *boys_e; // [kBoysGrid] exp(-T_i), T_i = i/32
     // real Gaunt coefficients for l, l~ <= 6 with l + l~ <= kLmaxAabA:
     // rows (l, l~, m, m~) -> entries [gaunt_row[r], gaunt_row[r+1]) of gaunt
     const int *gaunt_base;     // [7*7] first row of the (l, l~) block
     const int *gaunt_row;      // row pointers
     const GauntEnt *gaunt;     // entries
-    const float4 *boys_mix;    // [kBoysGrid][kBoysN][4] (c0..c3 as hi/lo, c4..c7 as float, pad)
-    const float2 *boys_e_mix;  // [kBoysGrid] exp(-T_i) as hi/lo
+    const float4 *boys_mix;    // [kBoysGridMix][kBoysN][4] (c0..c3 as hi/lo, c4..c7 as float, pad)
+    const float2 *boys_e_mix;  // [kBoysGridMix] exp(-T_i) as hi/lo, T_i = i/16
 };
 
 // Extra constants of the three-index kernels (by value).
@@ -149,7 +156,7 @@ const Consts &consts();                            // constant tables (host copy
 int check_op(int op, double omega, int precision);  // operator / omega / precision check
 
 // Host generation of the Boys table (long double arithmetic).
-void make_boys_table(double *tab, double *etab);
+void make_boys_table(int per_unit, int ngrid, int nterms, double *tab, double *etab);
 
 struct BasisDev {
     int n_shells = 0, n_centers = 0;

@@ -44,9 +44,9 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
         return;
     }
 
-    double O[J];
+    double O[J], E[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) O[j] = 0.0;
+    for (int j = 0; j < J; ++j) O[j] = E[j] = 0.0;
     if (OP == OP_PRE) {
 #pragma unroll
         for (int j = 0; j < J; ++j) O[j] = g.o_pre[(int64_t)p * kJmax + j];
@@ -57,8 +57,9 @@ __device__ void pair_2c_fp64(const Args2c &g, int p)
         const int Kb = sb.nprim, npp = sa.nprim * Kb;
         for (int q = 0; q < npp; ++q) {
             const int ia = q / Kb, ib = q - ia * Kb;
-            radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, la, g, O);
+            radial_acc_fp64<OP, J>(g.prims[sa.prim_off + ia], g.prims[sb.prim_off + ib], R2, kmax, la, g, O, E);
         }
+        radial_finish_fp64<OP, J>(R2, kmax, g.k, O, E);
     }
 
     // g_e = 2^{kmax-j} (2j-1)!! B_{j,kappa} O^{(kmax-j)}, shared by z = c, s

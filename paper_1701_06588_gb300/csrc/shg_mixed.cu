@@ -252,6 +252,50 @@ __device__ __forceinline__ df mix_boys_prefactor(const MixPair &m, const MixPrim
     return mul(mul(ldf(km.two_pi52), m.rc), mul(ldf(pa.inv_alpha), ldf(pb.inv_alpha)));
 }
 
+// Top order and recursion terms of the fused pass (contracted downward
+// recursion, as in the FP64 fused kernel): with the order factors hp[j] of
+// this path (they carry (-2 rho)^k), a Coulomb-type term Y_n = hp(n) X_n
+// obeys Y_n = (-R^2 Y_{n+1} + hp(n) P q^n exp(-T')) / (2n+1) for the 1/r
+// (P = pre, q = 1, T' = T) and the attenuated (P = pre omega / sqrt(omega^2 +
+// rho), q = s, T' = s T) sums alike; -R^2 is the same for every primitive pair,
+// so only the top order S[0] and the terms E[j], j >= 1, are summed here.
+template <int J>
+__device__ __forceinline__ void mix_coulomb_near_top(const MixPair &m, const df (&hp)[J], df pre, int kmax,
+                                                     const float4 *boys, const float2 *boys_e, const ConstsMix &km,
+                                                     df (&S)[J], df (&E)[J])
+{
+    df F, e;
+    boys_head_mix_near(m.T, kmax, boys, boys_e, km, F, e);
+    S[0] = add(S[0], mul(mul(hp[0], pre), F));
+    if (J > 1) {
+        const df pe = mul(pre, e);
+#pragma unroll
+        for (int j = 1; j < J; ++j) E[j] = add(E[j], mul(hp[j], pe));
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void mix_attenuated_top(const MixPair &m, const df (&hp)[J], df pre, df omega, df omega2,
+                                                   int kmax, const float4 *boys, const float2 *boys_e,
+                                                   const ConstsMix &km, df (&S)[J], df (&E)[J])
+{
+    const df rw = rsqrt_df(add(omega2, m.rho));
+    const df s = mul(omega2, mul(rw, rw));                                   // omega^2 / (omega^2 + rho)
+    df F, e;
+    boys_head_mix(mul(s, m.T), kmax, boys, boys_e, km, F, e);
+    df X = mul(mul(pre, mul(omega, rw)), powi_df(s, kmax - J + 1));          // order kmin
+    if (J > 1) {
+        df Xe = mul(X, e);
+#pragma unroll
+        for (int j = J - 1; j >= 1; --j) {
+            E[j] = add(E[j], mul(hp[j], Xe));
+            Xe = mul(Xe, s);
+            X = mul(X, s);
+        }
+    }
+    S[0] = add(S[0], mul(mul(hp[0], X), F));
+}
+
 // S_j += hp[j] X_k for one primitive pair, k = kmax-j, j = 0..J-1: the
 // operator parts X_k of Table S1 without their (-rho)^k, which hp carries
 // (with the weights and the 2^k of the assembly).
@@ -561,9 +605,10 @@ __device__ void pair_2c_mix_fused(const ArgsMixFused &g, int p)
     const bool f_er = g.out[OP_ERF] != nullptr;
     const bool f_x = g.out[OP_ERFC] != nullptr && !(f_er && g.share_att);
 
-    df Sov[J], Sco[J], Sx[J], Ser[J], Sga[J];
+    // S*[j]: order kmax - j; E*[j], j >= 1: the exp(-T') terms of the contracted recursion
+    df Sov[J], Sco[J], Sx[J], Ser[J], Sga[J], Eco[J], Ex[J], Eer[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) Sov[j] = Sco[j] = Sx[j] = Ser[j] = Sga[j] = df_f(0.0f);
+    for (int j = 0; j < J; ++j) Sov[j] = Sco[j] = Sx[j] = Ser[j] = Sga[j] = Eco[j] = Ex[j] = Eer[j] = df_f(0.0f);
     // far field of the 1/r sum, T >= kBoysTmax: sum of the FP64 weights fw_a fw_b
     // (on the FP64 pipe), times the per-pair order factors after the loop
     double far = 0.0;
@@ -578,13 +623,25 @@ __device__ void pair_2c_mix_fused(const ArgsMixFused &g, int p)
         if (f_co || f_er || f_x) {
             const df pre = mix_boys_prefactor(m, pa, pb, g.km);
             if (f_co) {
-                if (m.T.hi < (float)kBoysTmax) mix_coulomb_near<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, Sco);
+                if (m.T.hi < (float)kBoysTmax)
+                    mix_coulomb_near_top<J>(m, hp, pre, kmax, g.boys, g.boys_e, g.km, Sco, Eco);
                 else far = fma(pa.fw, pb.fw, far);
             }
             if (f_er)
-                mix_attenuated<J>(m, hp, pre, ldf(g.w_erf), ldf(g.w_erf2), false, kmax, g.boys, g.boys_e, g.km, Ser);
+                mix_attenuated_top<J>(m, hp, pre, ldf(g.w_erf), ldf(g.w_erf2), kmax, g.boys, g.boys_e, g.km, Ser, Eer);
             if (f_x)
-                mix_attenuated<J>(m, hp, pre, ldf(g.w_erfc), ldf(g.w_erfc2), false, kmax, g.boys, g.boys_e, g.km, Sx);
+                mix_attenuated_top<J>(m, hp, pre, ldf(g.w_erfc), ldf(g.w_erfc2), kmax, g.boys, g.boys_e, g.km, Sx, Ex);
+        }
+    }
+    // contracted downward recursion, orders kmax-1 .. kmin (far field added afterwards)
+    if (J > 1) {
+        const df mR2 = neg(R2);
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            const df inv = ldf(g.km.inv_int[2 * (kmax - j) + 1]);
+            Sco[j] = mul(add(mul(mR2, Sco[j - 1]), Eco[j]), inv);
+            Ser[j] = mul(add(mul(mR2, Ser[j - 1]), Eer[j]), inv);
+            Sx[j] = mul(add(mul(mR2, Sx[j - 1]), Ex[j]), inv);
         }
     }
     if (far != 0.0) {
