@@ -447,22 +447,19 @@ const DeviceTables *device_tables_impl(int **ranks, int **rank3 = nullptr)
             const float f[4] = {(float)r[4], (float)r[5], (float)r[6], 0.0f};
             std::memcpy(d + 4, f, sizeof f);
         }
-        // double-float table (step 1/16)
-        std::vector<double> mraw((size_t)kBoysGridMix * kBoysN * kBoysTerms), metab_d(kBoysGridMix);
-        make_boys_table(16, kBoysGridMix, kBoysTerms, mraw.data(), metab_d.data());
-        std::vector<float4> mtab((size_t)kBoysGridMix * kBoysN * 4);
-        std::vector<float2> metab(kBoysGridMix);
-        for (int i = 0; i < kBoysGridMix; ++i) {
+        // double-float table (the same grid): c0..c2 as hi/lo float pairs, c3..c6 as floats
+        std::vector<float4> mtab((size_t)kBoysGrid * kBoysN * 3);
+        std::vector<float2> metab(kBoysGrid);
+        for (int i = 0; i < kBoysGrid; ++i) {
             for (int n = 0; n < kBoysN; ++n) {
-                const double *cf = &mraw[((size_t)i * kBoysN + n) * kBoysTerms];
-                float4 *q = &mtab[((size_t)i * kBoysN + n) * 4];
-                const float2 c0 = split2(cf[0]), c1 = split2(cf[1]), c2 = split2(cf[2]), c3 = split2(cf[3]);
+                const double *cf = &raw[((size_t)i * kBoysN + n) * 7];
+                float4 *q = &mtab[((size_t)i * kBoysN + n) * 3];
+                const float2 c0 = split2(cf[0]), c1 = split2(cf[1]), c2 = split2(cf[2]);
                 q[0] = make_float4(c0.x, c0.y, c1.x, c1.y);
-                q[1] = make_float4(c2.x, c2.y, c3.x, c3.y);
-                q[2] = make_float4((float)cf[4], (float)cf[5], (float)cf[6], (float)cf[7]);
-                q[3] = make_float4(0, 0, 0, 0);
+                q[1] = make_float4(c2.x, c2.y, (float)cf[3], (float)cf[4]);
+                q[2] = make_float4((float)cf[5], (float)cf[6], 0.0f, 0.0f);
             }
-            metab[i] = split2(metab_d[i]);
+            metab[i] = split2(etab[i]);
         }
         double *d_tab = nullptr, *d_e = nullptr;
         float4 *d_mtab = nullptr;

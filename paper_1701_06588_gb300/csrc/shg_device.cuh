@@ -27,7 +27,7 @@ enum { OP_OVERLAP = 0, OP_COULOMB = 1, OP_ERFC = 2, OP_ERF = 3, OP_GAUSS = 4, OP
 // The two branches differ only in how F_kmax and exp(-T) are obtained, so  //
 // a warp whose lanes straddle T = 120 runs both short heads and one tail.  //
 //                                                                          //
-// Grid T_i = i/32, |d| <= 1/64: seven terms leave a remainder below         //
+// Grid T_i = i/32, |d| <~ 1/64: seven terms leave a remainder below        //
 // (1/64)^7/7! = 5e-17 of F (F_{n+t} <= F_n).  Terms 0..3 are summed in      //
 // FP64; terms 4..6, together at most (1/64)^4/4! = 2.5e-9 of F, in FP32     //
 // (relative error ~2e-7 there, so ~5e-16 of F), which moves three of the    //
@@ -55,15 +55,17 @@ __device__ __forceinline__ double flt_to_dbl(float x)
     return e ? __hiloint2double((int)hi, (int)(b << 29)) : 0.0;
 }
 
-// One Taylor head: grid index i and y = T_i - T (exact) for T < kBoysTmax.
-// Adding 1.5 * 2^52 rounds 32 T (< 2^31) to an integer held in the low word,
-// so T_i = i / 32 needs no float-to-int conversion.
+// One Taylor head: grid index i and y = T_i - T (exact) for 0 <= T < kBoysTmax.
+// The index is rounded from the float of 32 T (dbl_to_flt truncates, 32 T
+// < 3840 loses at most 5e-4), so |y| <= 1/64 + 2e-5; adding 1.5 * 2^23
+// rounds to an integer held in the low bits of the float, and T_i = i / 32 is
+// exact in FP32, so only y itself is an FP64 operation.
 __device__ __forceinline__ int boys_grid(double T, double &y)
 {
-    constexpr double kRound = 6755399441055744.0;
-    const double t32 = fma(T, 32.0, kRound);
-    y = fma(t32 - kRound, 0.03125, -T);
-    return __double2loint(t32);
+    constexpr float kRound = 12582912.0f;                     // 1.5 * 2^23
+    const float t = fmaf(dbl_to_flt(T), 32.0f, kRound);
+    y = flt_to_dbl((t - kRound) * 0.03125f) - T;
+    return __float_as_int(t) - __float_as_int(kRound);
 }
 
 // F_n(T) from the entry of (i, n): c0..c3 in FP64, c4..c6 in FP32 (see above)

@@ -23,21 +23,19 @@ constexpr int kTile = 32;         // pairs per warp tile
 constexpr int kMixedFp64MinL = 4;
 inline bool mixed_runs_fp64(int cls) { return cls / 7 >= kMixedFp64MinL && cls % 7 >= kMixedFp64MinL; }
 
-// Boys tables: Taylor coefficients F_{n+t}(T_i)/t! about grid points T_i,
-// n < kBoysN; Taylor expansion about the nearest grid point.
-//   FP64 table: T_i = i/32, i = 0..kBoysGrid-1 (|delta| <= 1/64), t = 0..6,
-//     per (i, n) kBoysStride doubles: c0..c3 as doubles, c4..c6 as floats
-//     (and one float of padding), 48 bytes.
-//   double-float table: T_i = i/16, i = 0..kBoysGridMix-1 (|delta| <= 1/32),
-//     t = 0..7 (c0..c3 as hi/lo float pairs, c4..c7 as floats).
+// Boys tables: Taylor coefficients c_t = F_{n+t}(T_i)/t!, t = 0..6, about the
+// grid points T_i = i/32, i = 0..kBoysGrid-1 (|delta| <= 1/64), n < kBoysN;
+// Taylor expansion about the nearest grid point.
+//   FP64 table: per (i, n) kBoysStride doubles: c0..c3 as doubles, c4..c6 as
+//     floats (and one float of padding), 48 bytes.
+//   double-float table: per (i, n) three float4: c0..c2 as hi/lo float pairs,
+//     c3..c6 as floats (and two floats of padding), 48 bytes.
 // Above kBoysTmax, F_n(T) = (2n-1)!! / (2T)^n sqrt(pi/(4T)) to better than
 // 1e-30 relative for n <= 16 (the neglected terms carry exp(-T)).
 constexpr int kBoysGrid = 3841;     // covers T < 120 at step 1/32
 constexpr int kBoysStride = 6;
-constexpr int kBoysGridMix = 1921;  // covers T < 120 at step 1/16
 constexpr double kBoysTmax = 120.0;
 constexpr int kBoysN = 16;          // orders n = 0..15 from the tables
-constexpr int kBoysTerms = 8;       // terms of the double-float table
 
 // Per-shell screening data (host-computed): smallest exponent, sum |N c| over
 // the primitives, and (l / (alpha_min e))^{l/2} (1 for l = 0).
@@ -127,8 +125,8 @@ struct DeviceTables {
     const int *gaunt_base;     // [7*7] first row of the (l, l~) block
     const int *gaunt_row;      // row pointers
     const GauntEnt *gaunt;     // entries
-    const float4 *boys_mix;    // [kBoysGridMix][kBoysN][4] (c0..c3 as hi/lo, c4..c7 as float, pad)
-    const float2 *boys_e_mix;  // [kBoysGridMix] exp(-T_i) as hi/lo, T_i = i/16
+    const float4 *boys_mix;    // [kBoysGrid][kBoysN][3] (layout above)
+    const float2 *boys_e_mix;  // [kBoysGrid] exp(-T_i) as hi/lo
 };
 
 // Extra constants of the three-index kernels (by value).

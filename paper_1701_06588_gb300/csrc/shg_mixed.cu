@@ -62,6 +62,38 @@ __device__ __noinline__ df exp_neg_df(df x, const ConstsMix &k)
     return df{e.hi * s, e.lo * s};
 }
 
+// Taylor head in double-float on the grid T_i = i/32 (|y| <= 1/64, y = T_i - T):
+// F_n(T) = sum_{t<=6} c_t y^t with c0..c2 in double-float and the terms 3..6,
+// together at most (1/64)^3/3! = 6.4e-7 of F, in FP32 (relative error ~1e-7
+// there, so ~6e-14 of F); exp(-T) = exp(-T_i) exp(y) the same way.  The
+// index is rounded by adding 1.5 * 2^23 (no float-to-int conversion);
+// T.hi - T_i is exact (Sterbenz), so y is exact in double-float.
+__device__ __forceinline__ void boys_taylor_mix(df T, int kmax, const float4 *__restrict__ tab,
+                                                const float2 *__restrict__ etab, df &f, df *e)
+{
+    constexpr float kRound = 12582912.0f;                          // 1.5 * 2^23
+    const float t32 = fmaf(T.hi, 32.0f, kRound);
+    const int i = __float_as_int(t32) - __float_as_int(kRound);
+    const float d0 = T.hi - (t32 - kRound) * 0.03125f;             // exact
+    const df y = two_sum(-d0, -T.lo);                              // T_i - T
+    const float4 *c = tab + ((size_t)i * kBoysN + kmax) * 3;
+    const float4 q0 = __ldg(c), q1 = __ldg(c + 1), q2 = __ldg(c + 2);
+    float t = fmaf(q2.y, y.hi, q2.x);                              // c6 y + c5
+    t = fmaf(t, y.hi, q1.w);                                       // + c4
+    t = fmaf(t, y.hi, q1.z);                                       // + c3
+    f = add(mul_f(y, t), df{q1.x, q1.y});
+    f = add(mul(y, f), df{q0.z, q0.w});
+    f = add(mul(y, f), df{q0.x, q0.y});
+    if (e) {
+        const float te = fmaf(fmaf(fmaf(1.0f / 720.0f, y.hi, 1.0f / 120.0f), y.hi, 1.0f / 24.0f), y.hi,
+                              1.0f / 6.0f);
+        df x = add(mul_f(y, te), df_f(0.5f));
+        x = add(mul(y, x), df_f(1.0f));
+        x = add(mul(y, x), df_f(1.0f));
+        *e = mul(x, ldf(__ldg(etab + i)));
+    }
+}
+
 // Boys head in double-float: F_kmax and exp(-T) (0 above the table range),
 // the same scheme as the FP64 path: Taylor head from the table below T = 120,
 // asymptotic head above.
@@ -69,25 +101,7 @@ __device__ __forceinline__ void boys_head_mix(df T, int kmax, const float4 *__re
                                               const float2 *__restrict__ etab, const ConstsMix &k, df &f, df &e)
 {
     if (T.hi < (float)kBoysTmax) {
-        const int i = __float2int_rn(T.hi * 16.0f);
-        const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
-        const df y = two_sum(-d0, -T.lo);                          // -(T - T_i)
-        const float4 *c = tab + ((size_t)i * kBoysN + kmax) * 4;
-        const float4 q0 = __ldg(c), q1 = __ldg(c + 1), q2 = __ldg(c + 2);
-        float t = fmaf(q2.w, y.hi, q2.z);
-        t = fmaf(t, y.hi, q2.y);
-        t = fmaf(t, y.hi, q2.x);
-        f = add(mul_f(y, t), df{q1.z, q1.w});
-        f = add(mul(y, f), df{q1.x, q1.y});
-        f = add(mul(y, f), df{q0.z, q0.w});
-        f = add(mul(y, f), df{q0.x, q0.y});
-        const float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi,
-                              k.inv_fact_f[4]);
-        e = add(mul_f(y, te), ldf(k.inv_fact[3]));
-        e = add(mul(y, e), ldf(k.inv_fact[2]));
-        e = add(mul(y, e), df_f(1.0f));
-        e = add(mul(y, e), df_f(1.0f));
-        e = mul(e, ldf(__ldg(etab + i)));
+        boys_taylor_mix(T, kmax, tab, etab, f, &e);
     } else {
         // (2kmax-1)!! (2T)^-kmax sqrt(pi/(4T)); exp(-T) is below FP32 range here
         const df rT = rsqrt_df(T);
@@ -100,25 +114,8 @@ __device__ __forceinline__ void boys_head_mix(df T, int kmax, const float4 *__re
 __device__ __forceinline__ void boys_head_mix_near(df T, int kmax, const float4 *__restrict__ tab,
                                                    const float2 *__restrict__ etab, const ConstsMix &k, df &f, df &e)
 {
-    const int i = __float2int_rn(T.hi * 16.0f);
-    const float d0 = T.hi - (float)i * 0.0625f;                 // exact (Sterbenz)
-    const df y = two_sum(-d0, -T.lo);                          // -(T - T_i)
-    const float4 *c = tab + ((size_t)i * kBoysN + kmax) * 4;
-    const float4 q0 = __ldg(c), q1 = __ldg(c + 1), q2 = __ldg(c + 2);
-    float t = fmaf(q2.w, y.hi, q2.z);
-    t = fmaf(t, y.hi, q2.y);
-    t = fmaf(t, y.hi, q2.x);
-    f = add(mul_f(y, t), df{q1.z, q1.w});
-    f = add(mul(y, f), df{q1.x, q1.y});
-    f = add(mul(y, f), df{q0.z, q0.w});
-    f = add(mul(y, f), df{q0.x, q0.y});
-    const float te = fmaf(fmaf(fmaf(k.inv_fact_f[7], y.hi, k.inv_fact_f[6]), y.hi, k.inv_fact_f[5]), y.hi,
-                          k.inv_fact_f[4]);
-    e = add(mul_f(y, te), ldf(k.inv_fact[3]));
-    e = add(mul(y, e), ldf(k.inv_fact[2]));
-    e = add(mul(y, e), df_f(1.0f));
-    e = add(mul(y, e), df_f(1.0f));
-    e = mul(e, ldf(__ldg(etab + i)));
+    (void)k;
+    boys_taylor_mix(T, kmax, tab, etab, f, &e);
 }
 
 // Boys F_k(T), k = kmax-J+1..kmax, F[j] = F_{kmax-j}: head, then one shared
