@@ -19,7 +19,6 @@ whole workload, weak scaling).  Prints one JSON line on rank 0.
 """
 import argparse
 import hashlib
-import glob
 import json
 import os
 import statistics
@@ -219,10 +218,17 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------- #
 # GPU arm                                                                     #
 # --------------------------------------------------------------------------- #
+# the sources that build the two-center kernels the profiles describe (their
+# device code, tables and launch logic); the (aab), family, gradient and
+# allocation-free translation units are not part of them
+KERNEL_SOURCES = ["shg_api.cpp", "shg_device.cuh", "shg_df.cuh", "shg_fused.cu", "shg_grad_angular.cuh",
+                  "shg_internal.h", "shg_kernels.cu", "shg_mix_angular.cuh", "shg_mixed.cu"]
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1701_06588_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1701_06588_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -220,27 +220,35 @@ def workload_elements(shells, pair_a, pair_b):
 def triple_flops(la, lt, lb, ka, kt, kb):
     """Algorithmic FP64 flops of one contracted (a b a~) triple in the order the
     (aab) formula is evaluated (Eqs. Pa_aba, sra2ms, devsra2ms, I_jab; Sec. II D),
-    numpy-vectorised.  The Gaunt sum counts 2 nL terms per (m_a, m_a~), an upper
-    estimate of the real Gaunt coefficients that are non-zero."""
+    numpy-vectorised.  Per (a, a~) primitive pair: alpha' = alpha + alpha~, its
+    inverse square root and the powers alpha'^{-j}; per primitive triple: the
+    setup, D_m^{(i)} by Horner times (beta^2/c)^i, (-rho)^n, the sums
+    V[m][k] (one multiply-add per term, binom(k,i)(-rho)^{k-i} formed once per
+    (k, i)) and P^{(k)} (binom(p,j)(L)_j alpha'^{-j} formed once per (L, j)).
+    The Gaunt sum counts 2 nL terms per (m_a, m_a~), an upper estimate of the
+    real Gaunt coefficients that are non-zero."""
     la, lt, lb = (np.asarray(v, dtype=np.int64) for v in (la, lt, lb))
-    kk = np.asarray(ka, dtype=np.int64) * np.asarray(kt, dtype=np.int64) * np.asarray(kb, dtype=np.int64)
+    kat = np.asarray(ka, dtype=np.int64) * np.asarray(kt, dtype=np.int64)
+    kk = kat * np.asarray(kb, dtype=np.int64)
     out = np.zeros(np.broadcast(la, lt, lb, kk).shape, dtype=np.float64)
-    it = np.nditer([la, lt, lb, kk], flags=["multi_index", "refs_ok"])
-    for a, t, b, k in it:
-        a, t, b, k = int(a), int(t), int(b), int(k)
+    it = np.nditer([la, lt, lb, kk, np.broadcast_to(kat, kk.shape)], flags=["multi_index", "refs_ok"])
+    for a, t, b, k, kp in it:
+        a, t, b, k, kp = int(a), int(t), int(b), int(k), int(kp)
         Lmin, Lmax = abs(a - t), a + t
         nL = (Lmax - Lmin) // 2 + 1
         p = nL - 1
         kmaxA = Lmax + b
         kminA = max(Lmin, b)
-        prim = 20 + p * (p + 1) * (p + 2) // 3 + kmaxA + 3 * p
-        for m in range(p + 1):
-            for kd in range(kminA, kmaxA + 1):
-                prim += 4 * (min(m, kd) + 1) + 1
+        pair = 12 + p
+        prim = 16 + 2 * p + p * (p + 1) * (p + 2) // 3 + (p + 1) * (p + 2) // 2 + kmaxA
+        for kd in range(kminA, kmaxA + 1):
+            prim += min(p, kd) + 1
+            for m in range(p + 1):
+                prim += 2 * (min(m, kd) + 1) + 1
         for iL in range(nL):
             L = Lmin + 2 * iL
             J = min(L, b) + 1
-            prim += J * (3 * (p - iL + 1) + 2) + 2
+            prim += (p - iL + 1) + J * (2 * (p - iL + 1) + 2) + 1
         lmax = max(Lmax, b)
         nb = 2 * b + 1
         Jmax = min(Lmax, b) + 1
@@ -250,7 +258,7 @@ def triple_flops(la, lt, lb, ka, kt, kb):
             J = min(L, b) + 1
             ang += J * J + (2 * L + 1) * (2 * J * J + nb * (2 * J * J + 2))
         ang += (2 * a + 1) * (2 * t + 1) * 2 * nL * nb * 2
-        out[it.multi_index] = k * prim + ang
+        out[it.multi_index] = k * prim + kp * pair + ang
     return out
 
 

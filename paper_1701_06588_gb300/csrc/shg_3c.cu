@@ -55,14 +55,27 @@ __device__ __forceinline__ TripleGeom aab_radial(const Args3c &g, int p, double 
 
     const int Ka = sa.nprim, Kt = st.nprim, Kb = sb.nprim;
     const int ntrip = Ka * Kt * Kb;
+    // per (a, a~) primitive pair (ib == 0): alpha' = alpha + alpha~ and its powers
+    double ap = 0.0, wat = 0.0, wL0 = 0.0, i2ap2 = 0.0;
+    double ia_p[kPmax + 1];
     for (int q = 0; q < ntrip; ++q) {
         const int ib = q % Kb;
-        const int it = (q / Kb) % Kt;
-        const int ia = q / (Kb * Kt);
-        const PrimRec pa = g.orb_prims[sa.prim_off + ia];
-        const PrimRec pt = g.orb_prims[st.prim_off + it];
+        if (ib == 0) {
+            const int it = (q / Kb) % Kt;
+            const int ia = q / (Kb * Kt);
+            const PrimRec pa = g.orb_prims[sa.prim_off + ia];
+            const PrimRec pt = g.orb_prims[st.prim_off + it];
+            ap = pa.alpha + pt.alpha;
+            const double rap = rsqrt(ap);
+            const double iap = rap * rap;                   // 1 / alpha'
+            wat = pa.wN * pt.wN * kPi32;
+            ia_p[0] = 1.0;
+            for (int m = 1; m <= pmax; ++m) ia_p[m] = ia_p[m - 1] * iap;
+            const double i2ap = 0.5 * iap;
+            wL0 = powi(i2ap, Lmin);                          // (2 alpha')^{-L_min}
+            i2ap2 = i2ap * i2ap;
+        }
         const PrimRec pb = g.aux_prims[sb.prim_off + ib];
-        const double ap = pa.alpha + pt.alpha;
         const double be = pb.alpha;
         const double c = ap + be;
         const double rc = rsqrt(c);
@@ -71,51 +84,52 @@ __device__ __forceinline__ TripleGeom aab_radial(const Args3c &g, int p, double 
         const double gg = be * be * ic;                 // beta^2 / c
         const double x = gg * R2;
         const double h = 0.5 * ic;                      // 1 / (2c)
-        const double rap = rsqrt(ap);
-        const double iap = rap * rap;                   // 1 / alpha'
         // pi^{3/2} c^{-3/2} exp(-rho R^2) and the weights N c of a, a~ and N c / (2beta)^lb of b
-        const double w0 = pa.wN * pt.wN * pb.w2c * kPi32 * ic * rc * exp(-rho * R2);
+        const double w0 = wat * pb.w2c * ic * rc * exp(-rho * R2);
 
-        // D_m^{(i)}(x) = sum_{j=i..m} d_{m,j} j!/(j-i)! x^{j-i}
-        double D[kPmax + 1][kPmax + 1];
+        double gp[kPmax + 1], hm[kPmax + 1];
+        gp[0] = hm[0] = 1.0;
+        for (int m = 1; m <= pmax; ++m) {
+            gp[m] = gp[m - 1] * gg;
+            hm[m] = hm[m - 1] * h;
+        }
+        // GD[m][i] = (beta^2/c)^i D_m^{(i)}(x),  D_m^{(i)}(x) = sum_{j=i..m} d_{m,j} j!/(j-i)! x^{j-i}
+        double GD[kPmax + 1][kPmax + 1];
         for (int m = 0; m <= pmax; ++m)
             for (int i = 0; i <= m; ++i) {
                 double s = g.k3.dd[m][i][m];
-                for (int j = m - 1; j >= i; --j) s = fma(s, x, g.k3.dd[m][i][j]);
-                D[m][i] = s;
+                for (int jj = m - 1; jj >= i; --jj) s = fma(s, x, g.k3.dd[m][i][jj]);
+                GD[m][i] = gp[i] * s;
             }
         double nr[kKmax3 + 1];                          // (-rho)^n
         nr[0] = 1.0;
         for (int n = 1; n <= kmaxA; ++n) nr[n] = nr[n - 1] * -rho;
-        double gp[kPmax + 1], hm[kPmax + 1], ia_p[kPmax + 1];
-        gp[0] = hm[0] = ia_p[0] = 1.0;
-        for (int m = 1; m <= pmax; ++m) {
-            gp[m] = gp[m - 1] * gg;
-            hm[m] = hm[m - 1] * h;
-            ia_p[m] = ia_p[m - 1] * iap;
-        }
-        // V[m][k] = (2c)^{-m} sum_{i<=min(m,k)} binom(k,i) (-rho)^{k-i} (beta^2/c)^i D_m^{(i)}(x)
+        // V[m][k] = (2c)^{-m} sum_{i<=min(m,k)} binom(k,i) (-rho)^{k-i} GD[m][i]
         double V[kPmax + 1][kKmax3 + 1];
-        for (int m = 0; m <= pmax; ++m)
-            for (int k = kminA; k <= kmaxA; ++k) {
+        for (int k = kminA; k <= kmaxA; ++k) {
+            double bn[kPmax + 1];
+            const int imax = pmax < k ? pmax : k;
+            for (int i = 0; i <= imax; ++i) bn[i] = g.k3.binom[k][i] * nr[k - i];
+            for (int m = 0; m <= pmax; ++m) {
                 double v = 0.0;
-                const int imax = m < k ? m : k;
-                for (int i = 0; i <= imax; ++i) v = fma(g.k3.binom[k][i] * nr[k - i], gp[i] * D[m][i], v);
+                const int im = m < k ? m : k;
+                for (int i = 0; i <= im; ++i) v = fma(bn[i], GD[m][i], v);
                 V[m][k] = hm[m] * v;
             }
+        }
         // P_L^{(k)} += w0 (2 alpha')^{-L} sum_j binom(p,j) (L)_j alpha'^{-j} V[p-j][k]
-        const double i2ap = 0.5 * iap;
-        double wL = w0 * powi(i2ap, Lmin);
-        const double i2ap2 = i2ap * i2ap;
+        double wL = w0 * wL0;
         for (int iL = 0; iL < nL; ++iL) {
             const int L = Lmin + 2 * iL;
             const int pL = pmax - iL;
             const int J = (L < lb ? L : lb) + 1;
             const int kmaxL = L + lb;
+            double bj[kPmax + 1];
+            for (int jj = 0; jj <= pL; ++jj) bj[jj] = g.k3.bj[L][pL][jj] * ia_p[jj];
             for (int j = 0; j < J; ++j) {
                 const int k = kmaxL - j;
                 double s = 0.0;
-                for (int jj = 0; jj <= pL; ++jj) s = fma(g.k3.bj[L][pL][jj] * ia_p[jj], V[pL - jj][k], s);
+                for (int jj = 0; jj <= pL; ++jj) s = fma(bj[jj], V[pL - jj][k], s);
                 P[iL][j] = fma(wL, s, P[iL][j]);
             }
             wL *= i2ap2;
@@ -356,14 +370,27 @@ __device__ void triple_aab_grad_fp64(const Args3c &g, int p)
         for (int j = 0; j <= kJmax; ++j) P[i][j] = 0.0;
     const int Ka = sa.nprim, Kt = st.nprim, Kb = sb.nprim;
     const int ntrip = Ka * Kt * Kb;
+    // per (a, a~) primitive pair (ib == 0), as in aab_radial
+    double ap = 0.0, wat = 0.0, wL0 = 0.0, i2ap2 = 0.0;
+    double ia_p[kPmax + 1];
     for (int q = 0; q < ntrip; ++q) {
         const int ib = q % Kb;
-        const int it = (q / Kb) % Kt;
-        const int ia = q / (Kb * Kt);
-        const PrimRec pa = g.orb_prims[sa.prim_off + ia];
-        const PrimRec pt = g.orb_prims[st.prim_off + it];
+        if (ib == 0) {
+            const int it = (q / Kb) % Kt;
+            const int ia = q / (Kb * Kt);
+            const PrimRec pa = g.orb_prims[sa.prim_off + ia];
+            const PrimRec pt = g.orb_prims[st.prim_off + it];
+            ap = pa.alpha + pt.alpha;
+            const double rap = rsqrt(ap);
+            const double iap = rap * rap;
+            wat = pa.wN * pt.wN * kPi32;
+            ia_p[0] = 1.0;
+            for (int m = 1; m <= pmax; ++m) ia_p[m] = ia_p[m - 1] * iap;
+            const double i2ap = 0.5 * iap;
+            wL0 = powi(i2ap, Lmin);
+            i2ap2 = i2ap * i2ap;
+        }
         const PrimRec pb = g.aux_prims[sb.prim_off + ib];
-        const double ap = pa.alpha + pt.alpha;
         const double be = pb.alpha;
         const double c = ap + be;
         const double rc = rsqrt(c);
@@ -372,46 +399,47 @@ __device__ void triple_aab_grad_fp64(const Args3c &g, int p)
         const double gg = be * be * ic;
         const double x = gg * R2;
         const double h = 0.5 * ic;
-        const double rap = rsqrt(ap);
-        const double iap = rap * rap;
-        const double w0 = pa.wN * pt.wN * pb.w2c * kPi32 * ic * rc * exp(-rho * R2);
-        double D[kPmax + 1][kPmax + 1];
+        const double w0 = wat * pb.w2c * ic * rc * exp(-rho * R2);
+        double gp[kPmax + 1], hm[kPmax + 1];
+        gp[0] = hm[0] = 1.0;
+        for (int m = 1; m <= pmax; ++m) {
+            gp[m] = gp[m - 1] * gg;
+            hm[m] = hm[m - 1] * h;
+        }
+        double GD[kPmax + 1][kPmax + 1];
         for (int m = 0; m <= pmax; ++m)
             for (int i = 0; i <= m; ++i) {
                 double s = g.k3.dd[m][i][m];
-                for (int j = m - 1; j >= i; --j) s = fma(s, x, g.k3.dd[m][i][j]);
-                D[m][i] = s;
+                for (int jj = m - 1; jj >= i; --jj) s = fma(s, x, g.k3.dd[m][i][jj]);
+                GD[m][i] = gp[i] * s;
             }
         double nr[kKmax3 + 2];
         nr[0] = 1.0;
         for (int n = 1; n <= kmaxA; ++n) nr[n] = nr[n - 1] * -rho;
-        double gp[kPmax + 1], hm[kPmax + 1], ia_p[kPmax + 1];
-        gp[0] = hm[0] = ia_p[0] = 1.0;
-        for (int m = 1; m <= pmax; ++m) {
-            gp[m] = gp[m - 1] * gg;
-            hm[m] = hm[m - 1] * h;
-            ia_p[m] = ia_p[m - 1] * iap;
-        }
         double V[kPmax + 1][kKmax3 + 2];
-        for (int m = 0; m <= pmax; ++m)
-            for (int k = kminA; k <= kmaxA; ++k) {
+        for (int k = kminA; k <= kmaxA; ++k) {
+            double bn[kPmax + 1];
+            const int imax = pmax < k ? pmax : k;
+            for (int i = 0; i <= imax; ++i) bn[i] = g.k3.binom[k][i] * nr[k - i];
+            for (int m = 0; m <= pmax; ++m) {
                 double vv = 0.0;
-                const int imax = m < k ? m : k;
-                for (int i = 0; i <= imax; ++i) vv = fma(g.k3.binom[k][i] * nr[k - i], gp[i] * D[m][i], vv);
+                const int im = m < k ? m : k;
+                for (int i = 0; i <= im; ++i) vv = fma(bn[i], GD[m][i], vv);
                 V[m][k] = hm[m] * vv;
             }
-        const double i2ap = 0.5 * iap;
-        double wL = w0 * powi(i2ap, Lmin);
-        const double i2ap2 = i2ap * i2ap;
+        }
+        double wL = w0 * wL0;
         for (int iL = 0; iL < nL; ++iL) {
             const int L = Lmin + 2 * iL;
             const int pL = pmax - iL;
             const int J = (L < lb ? L : lb) + 1;
             const int kmaxL = L + lb + 1;
+            double bj[kPmax + 1];
+            for (int jj = 0; jj <= pL; ++jj) bj[jj] = g.k3.bj[L][pL][jj] * ia_p[jj];
             for (int j = 0; j <= J; ++j) {
                 const int k = kmaxL - j;
                 double s = 0.0;
-                for (int jj = 0; jj <= pL; ++jj) s = fma(g.k3.bj[L][pL][jj] * ia_p[jj], V[pL - jj][k], s);
+                for (int jj = 0; jj <= pL; ++jj) s = fma(bj[jj], V[pL - jj][k], s);
                 P[iL][j] = fma(wL, s, P[iL][j]);
             }
             wL *= i2ap2;
