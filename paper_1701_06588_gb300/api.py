@@ -294,17 +294,20 @@ class Graph2c:
 
 class HostPipeline2c:
     """Two-center blocks from host pair lists into host output arrays, with
-    the read-back overlapped with the computation.
+    the copies and the planning overlapped with the computation.
 
     The pair list is split into n_chunks contiguous slices (default:
-    default_chunks(precision)), each planned on
-    the device (shg_plan_2c_create) and evaluated by one fused pass
-    (shg_plan_2c_exec_fused) on the compute stream; as soon as slice k is
-    done, its blocks (a contiguous range of every output, since the offsets
-    are the prefix sums of the block sizes) are copied to the host on a copy
-    stream while slice k+1 computes.  Inputs: pinned host tensors pair_a,
-    pair_b (int32), offsets (int64) and centers; outputs: pinned host float64
-    tensors, one per operator.  Device buffers are kept between calls.
+    default_chunks(precision)).  For slice k: its pair lists and offsets are
+    copied to the device on an upload stream, planned there
+    (shg_plan_2c_create, whose one synchronisation waits for that stream
+    only), evaluated by one fused pass (shg_plan_2c_exec_fused) on the
+    caller's stream, and its blocks (a contiguous range of every output,
+    since the offsets are the prefix sums of the block sizes) are copied to
+    the host on a copy stream.  The host plans slice k+1 while the GPU
+    computes slice k, and the read-back of slice k overlaps the computation
+    of slice k+1.  Inputs: pinned host tensors pair_a, pair_b (int32),
+    offsets (int64) and centers; outputs: pinned host float64 tensors, one
+    per operator.  Device buffers are kept between calls.
     """
 
     def __init__(self, basis, n_chunks=None, launch=None, schedule="persistent"):
@@ -313,15 +316,17 @@ class HostPipeline2c:
         self.launch = launch
         self.schedule = schedule
         self.copy_stream = torch.cuda.Stream()
+        self.upload_stream = torch.cuda.Stream()
         self._dev = {}
 
     @staticmethod
     def default_chunks(precision):
-        """FP64: two chunks (the read-back of the first hides behind the
-        second).  Mixed: one, since every chunk of a mixed pass waits for its
-        own FP64 launch of the classes with both l >= 4, whose slowest tile
-        sets a fixed time per chunk."""
-        return 1 if precision == "mixed" else 2
+        """FP64: four chunks (measured on the 2M-pair workload: 19.2, 19.3,
+        19.3, 18.8 and 20.2 ms for 1, 2, 3, 4 and 6 chunks).  Mixed: one,
+        since every chunk of a mixed pass waits for its own FP64 launch of the
+        classes with both l >= 4, whose slowest tile sets a fixed time per
+        chunk (8.3 ms for one chunk, 10.0 for two)."""
+        return 1 if precision == "mixed" else 4
 
     def _buf(self, name, n, dtype):
         t = self._dev.get(name)
@@ -335,31 +340,41 @@ class HostPipeline2c:
         total = int(outs[0].numel())
         omegas = [0.0] * len(ops) if omegas is None else list(omegas)
         stream = torch.cuda.current_stream()
+        up = self.upload_stream
         d_pa = self._buf("pa", n, torch.int32)
         d_pb = self._buf("pb", n, torch.int32)
         d_off = self._buf("off", n, torch.int64)
         d_out = [self._buf("out%d" % i, total, torch.float64) for i in range(len(ops))]
-        torch.cuda.nvtx.range_push("shg:h2d")
-        d_pa.copy_(pair_a, non_blocking=True)
-        d_pb.copy_(pair_b, non_blocking=True)
-        d_off.copy_(offsets, non_blocking=True)
         if centers is not None:
             self.basis.set_centers(centers)
-        torch.cuda.nvtx.range_pop()
+        # earlier work on the caller's stream (a previous run's use of the
+        # buffers) comes before the uploads
+        start = torch.cuda.Event()
+        start.record(stream)
+        up.wait_event(start)
         off_h = offsets.numpy()
         chunks = self.n_chunks or self.default_chunks(precision)
         bounds = [n * k // chunks for k in range(chunks + 1)]
         plans = []
-        for k in range(self.n_chunks):
+        for k in range(chunks):
             lo, hi = bounds[k], bounds[k + 1]
-            if hi > lo:
-                plan = Plan2c(self.basis, d_pa[lo:hi], d_pb[lo:hi], schedule=self.schedule)
-                if self.launch:
-                    set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"],
-                               self.launch.get("variant", 0))
-                plans.append((lo, hi, plan))
-        for lo, hi, plan in plans:
-            plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision)
+            if hi <= lo:
+                continue
+            torch.cuda.nvtx.range_push("shg:h2d")
+            with torch.cuda.stream(up):
+                d_pa[lo:hi].copy_(pair_a[lo:hi], non_blocking=True)
+                d_pb[lo:hi].copy_(pair_b[lo:hi], non_blocking=True)
+                d_off[lo:hi].copy_(offsets[lo:hi], non_blocking=True)
+            torch.cuda.nvtx.range_pop()
+            plan = Plan2c(self.basis, d_pa[lo:hi], d_pb[lo:hi], schedule=self.schedule, stream=up)
+            plans.append(plan)
+            if self.launch:
+                set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"],
+                           self.launch.get("variant", 0))
+            planned = torch.cuda.Event()
+            planned.record(up)
+            stream.wait_event(planned)
+            plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision, stream=stream)
             e0 = int(off_h[lo])
             e1 = int(off_h[hi]) if hi < n else total
             done = torch.cuda.Event()
@@ -373,7 +388,10 @@ class HostPipeline2c:
         fin = torch.cuda.Event()
         fin.record(self.copy_stream)
         stream.wait_event(fin)
-        for _, _, plan in plans:
+        # the plans' memory is released in the order of the upload stream, after
+        # every pass that used it
+        up.wait_event(fin)
+        for plan in plans:
             plan.close()
         return outs
 
