@@ -343,7 +343,7 @@ def run_ours(args, rank, world):
         if args.no_extras and f != form:
             continue
         if args.no_tune:
-            tuned[f] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0, "variant": 0}
+            tuned[f] = {"schedule": "persistent", "threads_per_cta": 128, "ctas_per_sm": 0, "variant": 1}
         else:
             tuned[f] = autotune.tune_2c(basis, pa, pb, names, omegas, d_off, outs, precision=f)
 

@@ -190,12 +190,18 @@ int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thres
                      const int64_t *d_out_offsets, double *d_out, void *stream);
 
 /*
- * shg_plan_2c_set_variant - compiled variant of the double-float fused kernel
- * used by later mixed-precision executions of the plan (an autotuner knob):
- * 0 = registers as the compiler allocates them (126 per thread, four
- * 128-thread CTAs per SM), 1 = at most 96 registers (five CTAs per SM, a few
- * values spilled).  Results are the same up to the order of operations.
- * SHG_EINVAL for another value.
+ * shg_plan_2c_set_variant - compiled variant of the persistent fused kernel
+ * used by later fused executions of the plan (an autotuner knob).
+ *   FP64:  0 = registers as the compiler allocates them (253 per thread),
+ *          1 = at most 170 (three 128-thread CTAs per SM), 2 = at most 128
+ *          (four); the capped variants spill some values to local memory.
+ *   mixed: 0 = as compiled (126 per thread), 1 or 2 = only the J <= 4
+ *          instantiations (the classes with both l >= 4 run in FP64), at most
+ *          96 registers.
+ * A new plan uses variant 1 (the fastest of the three on GB300 for both
+ * precisions on the 2M-pair workload).  The variants run the same operations
+ * in the same order, so the results are bitwise equal.  SHG_EINVAL for a
+ * value outside 0..2.
  */
 int shg_plan_2c_set_variant(shg_plan_t *plan, int variant);
 

@@ -370,7 +370,7 @@ class HostPipeline2c:
             plans.append(plan)
             if self.launch:
                 set_launch(plan, self.launch["threads_per_cta"], self.launch["ctas_per_sm"],
-                           self.launch.get("variant", 0))
+                           self.launch.get("variant", 1))
             planned = torch.cuda.Event()
             planned.record(up)
             stream.wait_event(planned)
@@ -396,10 +396,10 @@ class HostPipeline2c:
         return outs
 
 
-def set_launch(plan, threads_per_cta=128, ctas_per_sm=0, variant=0):
+def set_launch(plan, threads_per_cta=128, ctas_per_sm=0, variant=1):
     """Launch shape of later executions of a plan: threads per CTA, persistent
     CTAs per SM (0 = occupancy limit) and the compiled variant of the
-    double-float fused kernel (0 or 1, see shg_plan_2c_set_variant)."""
+    fused kernel (0, 1 or 2, see shg_plan_2c_set_variant)."""
     L.shg_plan_2c_set_launch(plan.handle, int(threads_per_cta), int(ctas_per_sm))
     L.shg_plan_2c_set_variant(plan.handle, int(variant))
 

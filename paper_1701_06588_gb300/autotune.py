@@ -21,7 +21,7 @@ from . import api
 
 CANDIDATES = ([("per_class", t, 0) for t in (32, 64, 128)] +
               [("persistent", t, c) for t in (32, 64, 128) for c in (0, 1, 2, 4, 8)])
-VARIANTS = {"mixed_fused": (0, 1)}
+VARIANTS = {"mixed_fused": (0, 1), "fp64_fused": (0, 1, 2)}
 
 
 def cache_path():
@@ -66,7 +66,7 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
             for op, om, o in zip(ops, omegas, outs):
                 plan.exec(op, out_offsets, o, omega=om, precision=precision)
 
-    key = "|".join(["v2", torch.cuda.get_device_name(), precision, ",".join(map(str, ops)),
+    key = "|".join(["v3", torch.cuda.get_device_name(), precision, ",".join(map(str, ops)),
                     workload_signature(basis, pair_a, pair_b)])
     db = _load()
     if not force and key in db:
@@ -102,5 +102,5 @@ def tune_2c(basis, pair_a, pair_b, ops, omegas, out_offsets, outs, precision="fp
 
 def tuned_plan(basis, pair_a, pair_b, config):
     plan = api.Plan2c(basis, pair_a, pair_b, schedule=config["schedule"])
-    api.set_launch(plan, config["threads_per_cta"], config["ctas_per_sm"], config.get("variant", 0))
+    api.set_launch(plan, config["threads_per_cta"], config["ctas_per_sm"], config.get("variant", 1))
     return plan

@@ -995,7 +995,7 @@ int shg_plan_2c_set_variant(shg_plan_t *p, int variant)
 {
     g_err.clear();
     if (!p) return fail(SHG_EINVAL, "plan is NULL");
-    if (variant != 0 && variant != 1) return fail(SHG_EINVAL, "kernel variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(SHG_EINVAL, "kernel variant must be 0, 1 or 2");
     p->d.variant = variant;
     return SHG_OK;
 }
@@ -1387,8 +1387,10 @@ int shg_plan_2c_exec_fused(shg_plan_t *p, int n_ops, const int *ops, const doubl
         if (a.tile_end > 0) {
             SHG_CUDA(cudaMemsetAsync(p->d.counter, 0, sizeof(int), s));
             a.counter = p->d.counter;
-            SHG_CUDA(launch_2c_fused(a, persistent_grid_2c_fused(p->d.threads, p->d.ctas_per_sm), true, s,
-                                     p->d.threads));
+            // the variant applies to the FP64 pass of FP64 executions only
+            const int v = mixed ? 0 : p->d.variant;
+            SHG_CUDA(launch_2c_fused(a, persistent_grid_2c_fused(p->d.threads, p->d.ctas_per_sm, v), true, s,
+                                     p->d.threads, v));
         }
     } else {
         a.counter = nullptr;

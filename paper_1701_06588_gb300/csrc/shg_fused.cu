@@ -250,7 +250,10 @@ __device__ __forceinline__ void run_tile_fused(const ArgsFused &g, const Tile &t
     }
 }
 
-__global__ void __launch_bounds__(128) k_2c_fp64_fused_persistent(const ArgsFused g)
+// MinB: CTAs of 128 threads that must fit on an SM (a register cap: 1 leaves the
+// compiler's allocation, 3 caps at 170 registers, 4 at 128)
+template <int MinB>
+__global__ void __launch_bounds__(128, MinB) k_2c_fp64_fused_persistent(const ArgsFused g)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -274,10 +277,15 @@ __global__ void __launch_bounds__(128) k_2c_fp64_fused_static(const ArgsFused g)
 
 }  // namespace
 
-cudaError_t launch_2c_fused(const ArgsFused &a, int n_tiles_or_grid, bool persistent, cudaStream_t s, int threads)
+cudaError_t launch_2c_fused(const ArgsFused &a, int n_tiles_or_grid, bool persistent, cudaStream_t s, int threads,
+                            int variant)
 {
     if (persistent) {
-        k_2c_fp64_fused_persistent<<<n_tiles_or_grid, threads, 0, s>>>(a);
+        switch (variant) {
+        case 1: k_2c_fp64_fused_persistent<3><<<n_tiles_or_grid, threads, 0, s>>>(a); break;
+        case 2: k_2c_fp64_fused_persistent<4><<<n_tiles_or_grid, threads, 0, s>>>(a); break;
+        default: k_2c_fp64_fused_persistent<1><<<n_tiles_or_grid, threads, 0, s>>>(a); break;
+        }
     } else {
         const int tiles = a.tile_end - a.tile_begin;
         if (tiles <= 0) return cudaSuccess;
@@ -287,14 +295,18 @@ cudaError_t launch_2c_fused(const ArgsFused &a, int n_tiles_or_grid, bool persis
     return cudaGetLastError();
 }
 
-int persistent_grid_2c_fused(int threads, int ctas_per_sm)
+int persistent_grid_2c_fused(int threads, int ctas_per_sm, int variant)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_fused_persistent, threads, 0) != cudaSuccess ||
-        per < 1)
-        per = 1;
+    cudaError_t e;
+    switch (variant) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_fused_persistent<3>, threads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_fused_persistent<4>, threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_2c_fp64_fused_persistent<1>, threads, 0); break;
+    }
+    if (e != cudaSuccess || per < 1) per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     return (sms > 0 ? sms : 1) * per;
 }

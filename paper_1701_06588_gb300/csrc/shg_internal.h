@@ -211,7 +211,7 @@ struct PlanDev {
                                    // mixed-precision passes run in FP64 (both l >= kMixedFp64MinL)
     int threads = 128;             // launch shape (autotuned): threads per CTA (32, 64 or 128)
     int ctas_per_sm = 0;           // persistent CTAs per SM, 0 = occupancy limit
-    int variant = 0;               // compiled kernel variant of the double-float fused pass
+    int variant = 1;               // compiled variant of the fused kernels (shg_plan_2c_set_variant)
                                    // (0: free register count, 1: <= 96 registers, 5 CTAs per SM)
     // streams of a mixed-precision pass that runs the FP64 high-l tiles beside the
     // double-float launch (created on first use): side (highest priority) takes the
@@ -386,9 +386,11 @@ int persistent_grid_3c(int precision);
 cudaError_t launch_2c(const Args2c &args, int op, int precision, int n_tiles_or_grid, bool persistent,
                       cudaStream_t s, int threads = 128);
 int persistent_grid_2c(int op, int precision, int threads = 128, int ctas_per_sm = 0);
+// variant (persistent launches): 0 = the compiler's register allocation, 1 = at
+// most 170 registers (three 128-thread CTAs per SM), 2 = at most 128 (four)
 cudaError_t launch_2c_fused(const ArgsFused &args, int n_tiles_or_grid, bool persistent, cudaStream_t s,
-                            int threads);
-int persistent_grid_2c_fused(int threads = 128, int ctas_per_sm = 0);
+                            int threads, int variant = 0);
+int persistent_grid_2c_fused(int threads = 128, int ctas_per_sm = 0, int variant = 0);
 cudaError_t launch_pack_centers(const double *raw, int n, Vec4 *ctr, MixCenter *mctr, int *bad, cudaStream_t s);
 cudaError_t launch_family_radial(const ArgsFam &a, int op, cudaStream_t s);
 cudaError_t launch_gather_i64(const int64_t *src, const int32_t *idx, int64_t n, int64_t *dst, cudaStream_t s);

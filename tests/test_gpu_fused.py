@@ -193,3 +193,34 @@ def test_fused_edge_cases_and_errors(shg):
     assert np.all(np.abs(outs[1].cpu().numpy() - r) <= 1e-13 * (np.abs(r) + np.abs(r).max()))
     plan.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_kernel_variants_are_bitwise_equal(shg, precision):
+    """The compiled variants of the persistent fused kernels differ only in
+    their register caps (and, for double-float, in leaving out the J >= 5
+    code that runs in FP64 anyway): the same operations in the same order,
+    so every block must be bitwise equal; a variant outside 0..2 is
+    rejected."""
+    import torch
+    from paper_1701_06588_gb300 import _lib as L
+    sh, pa, pb = W.make("c3_2m_l6_k20", n=4000)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    d_off = torch.from_numpy(off).cuda()
+    names, oms = ["coulomb", "erfc"], [0.0, 0.11]
+    plan = shg.Plan2c(b, pa, pb)
+    res = []
+    for variant in (0, 1, 2):
+        shg.set_launch(plan, 128, 0, variant)
+        outs = [torch.full((total,), float("nan"), dtype=torch.float64, device="cuda") for _ in names]
+        plan.exec_fused(names, d_off, outs, omegas=oms, precision=precision)
+        torch.cuda.synchronize()
+        res.append([o.cpu().numpy() for o in outs])
+    for v in (1, 2):
+        for a, r in zip(res[v], res[0]):
+            assert np.array_equal(a, r), (precision, v)
+    with pytest.raises(L.ShgError):
+        L.shg_plan_2c_set_variant(plan.handle, 3)
+    plan.close()
+    b.close()
