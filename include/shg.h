@@ -195,9 +195,8 @@ int shg_plan_2c_exec(shg_plan_t *plan, int op, double omega, double screen_thres
  *   FP64:  0 = registers as the compiler allocates them (253 per thread),
  *          1 = at most 170 (three 128-thread CTAs per SM), 2 = at most 128
  *          (four); the capped variants spill some values to local memory.
- *   mixed: 0 = as compiled (126 per thread), 1 or 2 = only the J <= 4
- *          instantiations (the classes with both l >= 4 run in FP64), at most
- *          96 registers.
+ *   mixed: 0 = registers as the compiler allocates them (about 124),
+ *          1 = at most 96 (five 128-thread CTAs per SM), 2 = at most 85 (six).
  * A new plan uses variant 1 (the fastest of the three on GB300 for both
  * precisions on the 2M-pair workload).  The variants run the same operations
  * in the same order, so the results are bitwise equal.  SHG_EINVAL for a

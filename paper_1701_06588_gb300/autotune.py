@@ -21,7 +21,7 @@ from . import api
 
 CANDIDATES = ([("per_class", t, 0) for t in (32, 64, 128)] +
               [("persistent", t, c) for t in (32, 64, 128) for c in (0, 1, 2, 4, 8)])
-VARIANTS = {"mixed_fused": (0, 1), "fp64_fused": (0, 1, 2)}
+VARIANTS = {"mixed_fused": (0, 1, 2), "fp64_fused": (0, 1, 2)}
 
 
 def cache_path():

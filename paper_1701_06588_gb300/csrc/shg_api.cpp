@@ -920,8 +920,8 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
     const int64_t max_tiles = n / kTile + std::min<int64_t>(n, kNBins) + 1;
     const size_t bytes_perm = sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1);
     const size_t bytes_tiles = sizeof(Tile) * (size_t)max_tiles;
-    const size_t bytes_ws = sizeof(int) * ((size_t)n + 4 * (size_t)kNBins + 1);
-    const size_t bytes = bytes_perm + bytes_tiles + 2 * sizeof(int) + bytes_ws + 256;
+    const size_t bytes_ws = sizeof(int) * plan_ws_ints(n, kNBins, kNClass);
+    const size_t bytes = bytes_perm + bytes_tiles + bytes_ws + 256;
     void *blk = nullptr;
     SHG_CUDA(cudaMallocAsync(&blk, bytes, s));
 
@@ -942,7 +942,6 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
     d.tiles = (Tile *)c;                 c += (bytes_tiles + 15) / 16 * 16;
     d.perm = (int32_t *)c;               c += (bytes_perm + 15) / 16 * 16;
     d.counter = (int *)c;                c += 16;
-    int *d_err = (int *)c;               c += 16;
     int *ws = (int *)c;
 
     auto cleanup = [&](int code) {
@@ -950,19 +949,16 @@ int shg_plan_2c_create(const shg_basis_t *basis, int64_t n, const int32_t *pa, c
         delete p;
         return code;
     };
-    if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) return cleanup(fail(SHG_ECUDA, "memset failed"));
-    cudaError_t e = launch_plan_build(d, ws, kNBins, ranks[schedule], d_err, s);
+    cudaError_t e = launch_plan_build(d, ws, kNBins, ranks[schedule], s);
     if (e != cudaSuccess) return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(e)));
-    // first tile of every class chunk and the tile count: tile_start[c * kKbins2c], c = 0..kNClass
-    int chunk_tile[kNClass + 1];
-    int h_err = 0;
-    int *d_tile_start = ws + n + 3 * kNBins;
-    if (cudaMemcpy2DAsync(chunk_tile, sizeof(int), d_tile_start, sizeof(int) * kKbins2c, sizeof(int), kNClass + 1,
-                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    // first tile of every class chunk, the tile count and the error flag, in one read-back
+    int chunk_tile[kNClass + 2];
+    if (cudaMemcpyAsync(chunk_tile, plan_summary(ws, kNBins), sizeof(chunk_tile), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return cleanup(fail(SHG_ECUDA, "plan build: %s", cudaGetErrorString(cudaGetLastError())));
-    if (h_err) return cleanup(fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", basis->d.n_shells - 1));
+    if (chunk_tile[kNClass + 1])
+        return cleanup(fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", basis->d.n_shells - 1));
     d.n_tiles = chunk_tile[kNClass];
     for (int cls = 0; cls <= kNClass; ++cls) d.class_tile_begin[cls] = chunk_tile[cls];
     if (schedule == SHG_SCHED_PERSISTENT) {
@@ -1496,7 +1492,7 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
     const int64_t max_tiles = n / kTile + std::min<int64_t>(n, kNBins3) + 1;
     const size_t bytes_perm = sizeof(int32_t) * (size_t)n;
     const size_t bytes_tiles = sizeof(Tile) * (size_t)max_tiles;
-    const size_t bytes_ws = sizeof(int) * ((size_t)n + 4 * (size_t)kNBins3 + 1);
+    const size_t bytes_ws = sizeof(int) * plan_ws_ints(n, kNBins3, kNClass3);
     const size_t bytes = bytes_perm + bytes_tiles + bytes_ws + 512;
     void *blk = nullptr;
     SHG_CUDA(cudaMallocAsync(&blk, bytes, s));
@@ -1513,15 +1509,14 @@ static int eval_3c_common(const shg_basis_t *orb, const shg_basis_t *aux, int64_
     d.tiles = (Tile *)c;                 c += (bytes_tiles + 15) / 16 * 16;
     d.perm = (int32_t *)c;               c += (bytes_perm + 15) / 16 * 16;
     d.counter = (int *)c;                c += 16;
-    int *d_err = (int *)c;               c += 16;
     int *ws = (int *)c;
-    int *d_tile_start = ws + n + 3 * kNBins3;
-    int h[2] = {0, 0};
-    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_plan_build(d, ws, kNBins3, rank3, d_err, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h[0], d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], d_tile_start + kNBins3, sizeof(int), cudaMemcpyDeviceToHost, s);
+    // the end of the build summary: sm[0] = tile count, sm[1] = error flags
+    int sm[2] = {0, 0};
+    cudaError_t e = launch_plan_build(d, ws, kNBins3, rank3, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sm, plan_summary(ws, kNBins3) + kNClass3, sizeof(sm), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int h[2] = {sm[1], sm[0]};              // error flags, tile count
     if (e != cudaSuccess) {
         cudaFreeAsync(blk, s);
         return fail(SHG_ECUDA, "(aab) planning: %s", cudaGetErrorString(e));

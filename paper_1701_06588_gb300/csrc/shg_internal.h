@@ -369,8 +369,17 @@ struct Args3c {
 };
 
 // Kernel launchers (shg_kernels.cu, shg_3c.cu).
-cudaError_t launch_plan_build(PlanDev &plan, int *d_scratch_counts, int n_bins, const int *d_bin_rank,
-                              int *d_err, cudaStream_t s);
+// Planning workspace (ints): err, ticket, 2 spare, hist, bin_start, cursor
+// (n_bins each), tile_start (n_bins + 1), summary (n_chunks + 2), key (n).
+// After the build, summary[c] is the first tile of class chunk c
+// (c = 0..n_chunks-1), summary[n_chunks] the number of tiles and
+// summary[n_chunks + 1] the error flag of the classification.
+constexpr size_t plan_ws_ints(int64_t n, int n_bins, int n_chunks)
+{
+    return 4 + 4 * (size_t)n_bins + 1 + (size_t)n_chunks + 2 + (size_t)n;
+}
+inline int *plan_summary(int *ws, int n_bins) { return ws + 4 + 4 * (size_t)n_bins + 1; }
+cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d_bin_rank, cudaStream_t s);
 cudaError_t launch_3c(const Args3c &args, int precision, int grid, cudaStream_t s);
 // grid is ignored when args.counter is null (static launch, one warp per tile)
 cudaError_t launch_2c_grad(const Args2c &args, int op, int precision, int grid, cudaStream_t s, int threads = 128);

@@ -467,7 +467,8 @@ __device__ __forceinline__ int block_incl_scan(int x, int *s_warp)
 
 __global__ void __launch_bounds__(1024) k_scan_chunks(int n_bins, int chunk, const int *__restrict__ hist,
                                                       int *__restrict__ bin_start, int *__restrict__ cursor,
-                                                      int *__restrict__ tile_start, int *ticket)
+                                                      int *__restrict__ tile_start, int *ticket,
+                                                      int *__restrict__ summary, const int *err)
 {
     __shared__ int s_warp[32];
     __shared__ int s_last;
@@ -493,9 +494,12 @@ __global__ void __launch_bounds__(1024) k_scan_chunks(int n_bins, int chunk, con
     if (k < (int)gridDim.x) {
         bin_start[k * chunk] = ic - cnt;
         tile_start[k * chunk] = it - til;
+        summary[k] = it - til;
     }
     if (k == (int)gridDim.x - 1) {
         tile_start[n_bins] = it;
+        summary[k + 1] = it;
+        summary[k + 2] = __ldcg(err);
         *ticket = 0;
     }
 }
@@ -614,18 +618,23 @@ __global__ void __launch_bounds__(256) k_dmma_probe(int iters, double *sink)
 // ------------------------------------------------------------------------- //
 // Launchers                                                                 //
 // ------------------------------------------------------------------------- //
-cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d_bin_rank, int *d_err,
-                              cudaStream_t s)
+cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d_bin_rank, cudaStream_t s)
 {
-    // d_ws layout: key[n] | hist[n_bins] | bin_start[n_bins] | cursor[n_bins] | tile_start[n_bins+1]
+    // d_ws layout (plan_ws_ints): err | ticket | 2 spare | hist[n_bins] | bin_start[n_bins] | cursor[n_bins] |
+    // tile_start[n_bins+1] | summary[n_chunks+2] | key[n]; one memset clears err, ticket and hist.
     // d_bin_rank: bin_rank[n_bins] followed by rank_to_bin[n_bins]
     const int64_t n = plan.n_pairs;
-    int *key = d_ws;
-    int *hist = key + n;
+    int *d_err = d_ws;
+    int *ticket = d_ws + 1;
+    int *hist = d_ws + 4;
     int *bin_start = hist + n_bins;
     int *cursor = bin_start + n_bins;
     int *tile_start = cursor + n_bins;
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * n_bins, s);
+    const int bpc = plan.kind == 2 ? kKbins2c : kKbins3c;
+    const int n_chunks = n_bins / bpc;
+    int *summary = tile_start + n_bins + 1;
+    int *key = summary + n_chunks + 2;
+    cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(int) * (4 + (size_t)n_bins), s);
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int blocks = (int)((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
@@ -638,12 +647,7 @@ cudaError_t launch_plan_build(PlanDev &plan, int *d_ws, int n_bins, const int *d
                                                  d_bin_rank, key, hist, d_err);
     }
     // both rank orders are class-major (each class a chunk of bins_per_class ranks): one tiling per class
-    const int bpc = plan.kind == 2 ? kKbins2c : kKbins3c;
-    const int n_chunks = n_bins / bpc;
-    int *ticket = tile_start + n_bins - 1;            // never a chunk start (bpc > 1): free for the ticket
-    e = cudaMemsetAsync(ticket, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    k_scan_chunks<<<n_chunks, bpc, 0, s>>>(n_bins, bpc, hist, bin_start, cursor, tile_start, ticket);
+    k_scan_chunks<<<n_chunks, bpc, 0, s>>>(n_bins, bpc, hist, bin_start, cursor, tile_start, ticket, summary, d_err);
     if (n > 0) k_scatter<<<blocks, threads, 0, s>>>(n, bpc, key, bin_start, cursor, plan.perm);
     const int64_t max_tiles = n / kTile + n_chunks + 1;
     const int tb = (int)((max_tiles + 255) / 256 < 1024 ? (max_tiles + 255) / 256 : 1024);

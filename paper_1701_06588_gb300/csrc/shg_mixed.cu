@@ -684,10 +684,10 @@ __device__ __forceinline__ void run_tile_mix_fused(const ArgsMixFused &g, const 
     }
 }
 
-// MinB = 0: registers as the compiler sees fit (126, four 128-thread CTAs
-// per SM); MinB = 5: at most 96 per thread, five CTAs per SM (more warps to
-// hide load and instruction-fetch latency, a few spilled values).  The
-// autotuner picks (shg_plan_2c_set_variant).
+// MinB = 0: registers as the compiler sees fit (about 124, four 128-thread
+// CTAs per SM); MinB = 5: at most 96 per thread, five CTAs per SM; MinB = 6:
+// at most 85, six CTAs (more warps to hide load and instruction-fetch
+// latency, more spilled values).  The autotuner picks (shg_plan_2c_set_variant).
 template <int MinB>
 __global__ void __launch_bounds__(128, MinB) k_2c_mixed_fused_persistent(const ArgsMixFused g)
 {
@@ -817,8 +817,11 @@ cudaError_t launch_2c_mixed_fused(const ArgsMixFused &a, int grid, bool persiste
                                   int variant)
 {
     if (persistent) {
-        if (variant) k_2c_mixed_fused_persistent<5><<<grid, threads, 0, s>>>(a);
-        else k_2c_mixed_fused_persistent<0><<<grid, threads, 0, s>>>(a);
+        switch (variant) {
+        case 1: k_2c_mixed_fused_persistent<5><<<grid, threads, 0, s>>>(a); break;
+        case 2: k_2c_mixed_fused_persistent<6><<<grid, threads, 0, s>>>(a); break;
+        default: k_2c_mixed_fused_persistent<0><<<grid, threads, 0, s>>>(a); break;
+        }
     } else {
         const int tiles = a.tile_end - a.tile_begin;
         if (tiles <= 0) return cudaSuccess;
@@ -834,7 +837,9 @@ int persistent_grid_2c_mixed_fused(int threads, int ctas_per_sm, int variant)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void *kern = variant ? (const void *)k_2c_mixed_fused_persistent<5> : (const void *)k_2c_mixed_fused_persistent<0>;
+    const void *kern = variant == 1   ? (const void *)k_2c_mixed_fused_persistent<5>
+                       : variant == 2 ? (const void *)k_2c_mixed_fused_persistent<6>
+                                      : (const void *)k_2c_mixed_fused_persistent<0>;
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
     if (e != cudaSuccess || per < 1)
         per = 1;

@@ -36,7 +36,7 @@ constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxPairs / kTile + kNBins2c + 1;
 constexpr size_t kTilesBytes = ((size_t)kNoAllocMaxTiles * sizeof(Tile) + 255) / 256 * 256;
 constexpr size_t kPermBytes = ((size_t)kNoAllocMaxPairs * sizeof(int32_t) + 255) / 256 * 256;
 constexpr size_t kFlagsBytes = 256;
-constexpr size_t kWsBytes = ((size_t)(kNoAllocMaxPairs + 4 * (int64_t)kNBins2c + 1) * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kWsBytes = (plan_ws_ints(kNoAllocMaxPairs, kNBins2c, kNClass) * sizeof(int) + 255) / 256 * 256;
 constexpr size_t kNoAllocBytes = kTilesBytes + kPermBytes + kFlagsBytes + kWsBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -105,20 +105,18 @@ extern "C" int shg_eval_2c_noalloc(const shg_basis_t *basis, int64_t n_pairs, co
     plan.pair_b = d_pair_b;
     plan.tiles = (Tile *)c;                c += kTilesBytes;
     plan.perm = (int32_t *)c;              c += kPermBytes;
-    plan.counter = (int *)c;
-    int *d_err = (int *)(c + 16);          c += kFlagsBytes;
+    plan.counter = (int *)c;               c += kFlagsBytes;
     int *ws = (int *)c;
-    int *d_tile_start = ws + n_pairs + 3 * kNBins2c;
 
-    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_plan_build(plan, ws, kNBins2c, ranks[SHG_SCHED_PERSISTENT], d_err, s);
-    int h_flags[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags[0], d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags[1], d_tile_start + kNBins2c, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = launch_plan_build(plan, ws, kNBins2c, ranks[SHG_SCHED_PERSISTENT], s);
+    // the end of the build summary: tile count and error flag
+    int h_sum[2] = {0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_sum, plan_summary(ws, kNBins2c) + kNClass, sizeof(h_sum), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(SHG_ECUDA, "shg_eval_2c_noalloc planning: %s", cudaGetErrorString(e));
-    if (h_flags[0]) return fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", b.n_shells - 1);
-    const int n_tiles = h_flags[1];
+    if (h_sum[1]) return fail(SHG_EINVAL, "pair list holds a shell index outside 0..%d", b.n_shells - 1);
+    const int n_tiles = h_sum[0];
     if (n_tiles <= 0) return SHG_OK;
 
     Args2c a;

@@ -198,10 +198,8 @@ def test_fused_edge_cases_and_errors(shg):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_fused_kernel_variants_are_bitwise_equal(shg, precision):
     """The compiled variants of the persistent fused kernels differ only in
-    their register caps (and, for double-float, in leaving out the J >= 5
-    code that runs in FP64 anyway): the same operations in the same order,
-    so every block must be bitwise equal; a variant outside 0..2 is
-    rejected."""
+    their register caps: the same operations in the same order, so every
+    block must be bitwise equal; a variant outside 0..2 is rejected."""
     import torch
     from paper_1701_06588_gb300 import _lib as L
     sh, pa, pb = W.make("c3_2m_l6_k20", n=4000)
