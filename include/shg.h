@@ -267,7 +267,15 @@ int shg_plan_2c_exec_fused(shg_plan_t *plan, int n_ops, const int *ops, const do
 int shg_graph_2c_create_fused(shg_plan_t *plan, int n_ops, const int *ops, const double *omegas, int precision,
                               const int64_t *d_out_offsets, double *const *d_outs, shg_graph_t **out);
 
-/* shg_plan_destroy - free a plan (synchronises its stream first). NULL ok. */
+/*
+ * shg_plan_destroy - free a plan.  NULL ok.  The plan's device memory is
+ * released in the order of the stream the plan was created on
+ * (cudaFreeAsync), without a host synchronisation: executions queued on that
+ * stream finish first, and executions on another stream must be ordered
+ * before it by the caller (an event that stream waits for).  The side streams
+ * and events of mixed-precision executions are destroyed with the plan; the
+ * executions have already joined them into the caller's stream.
+ */
 void shg_plan_destroy(shg_plan_t *plan);
 
 /*
