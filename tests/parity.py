@@ -41,7 +41,7 @@ TOL_GRAD = (1e-10, 1e-12, 1e-15)
 TOL_MIXED = (1e-10, 1e-14, 2e-13)
 TOL_GRAD_MIXED = (1e-10, 1e-12, 2e-13)
 
-# the bars with no conditioning term (the benchmark spec's plain tolerances)
+# the bars with no conditioning term (the plain element-wise tolerances)
 PLAIN_FP64 = (1e-12, 1e-14, 0.0)
 PLAIN_GRAD = (1e-10, 1e-12, 0.0)
 PLAIN_MIXED = (1e-10, 1e-14, 0.0)
