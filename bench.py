@@ -539,10 +539,11 @@ def run_ours(args, rank, world):
         "forms": forms,
         "e2e": {"value": job_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "what": ("per step, api.HostPipeline2c: pinned H2D of pair lists, offsets and centers, "
-                         "shg_basis_set_centers, then the pair list in %d contiguous chunks: shg_plan_2c_create "
-                         "and shg_plan_2c_exec_fused (both operators) per chunk, the D2H of chunk k's blocks to "
-                         "pinned memory on a copy stream overlapping chunk k+1" % e2e_chunks if fused else
+                "what": ("per step, api.HostPipeline2c: shg_basis_set_centers from pinned host centers, then the "
+                         "pair list in %d contiguous chunks; per chunk the pinned H2D of its pair lists and "
+                         "offsets and shg_plan_2c_create on an upload stream (overlapping the previous chunk's "
+                         "pass), shg_plan_2c_exec_fused (both operators), and the D2H of its blocks to pinned "
+                         "memory on a copy stream overlapping the next chunk" % e2e_chunks if fused else
                          "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
                          "shg_plan_2c_create, one shg_plan_2c_exec per operator, D2H of all blocks to pinned memory (operator "
                          "k's copy on a second stream overlaps operator k+1's kernel)"),
