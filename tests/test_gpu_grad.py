@@ -258,3 +258,36 @@ def test_grad_mixed_runs_high_l_classes_in_fp64(shg):
     with pytest.raises(Exception):
         shg.eval_2c_grad(b, pa, pb, "ra2n", w, offsets=off, omega=1.0, precision="mixed")
     b.close()
+
+
+def test_grad_mixed_single_kind_lists(shg):
+    """Mixed-precision gradients of a list with no class run in FP64 (l <= 3:
+    one double-float launch, no side streams) and of a list with only such
+    classes (both l >= 4: the FP64 kernel alone, bitwise equal to FP64)."""
+    import torch
+    from tests.parity import TOL_GRAD_MIXED
+    sh, pa, pb = W.make("c1_2k_l3_k4", n=300)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = np.random.default_rng(21).uniform(-1, 1, total)
+    ga, _ = shg.eval_2c_grad(b, pa, pb, "erfc", torch.from_numpy(w).cuda(), offsets=off, omega=0.11,
+                             precision="mixed")
+    torch.cuda.synchronize()
+    ref, scale = _oracle_vjp(sh, pa, pb, oracle.OP_ERFC, 0.11, w)
+    rtol, atol, gamma = TOL_GRAD_MIXED
+    ex = np.abs(ga.cpu().numpy() - ref) / (rtol * np.abs(ref) + atol + gamma * scale)
+    assert ex.max() <= 1.0, ex.max()
+    b.close()
+
+    sh, pa, pb = W.make("c5_grad_500k_l5_k12", n=20000)
+    l = np.asarray(sh["l"])
+    keep = np.where((l[pa] >= 4) & (l[pb] >= 4))[0][:300]
+    sh, pa, pb = W.subset_pairs(sh, pa, pb, keep)
+    b = shg.Basis(sh)
+    off, total = b.pair_offsets(pa, pb)
+    w = torch.from_numpy(np.random.default_rng(22).uniform(-1, 1, total)).cuda()
+    g64, _ = shg.eval_2c_grad(b, pa, pb, "coulomb", w, offsets=off, precision="fp64")
+    gmx, _ = shg.eval_2c_grad(b, pa, pb, "coulomb", w, offsets=off, precision="mixed")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g64.cpu().numpy(), gmx.cpu().numpy())
+    b.close()
