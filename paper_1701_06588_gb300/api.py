@@ -300,8 +300,9 @@ class HostPipeline2c:
     default_chunks(precision)).  For slice k: its pair lists and offsets are
     copied to the device on an upload stream, planned there
     (shg_plan_2c_create, whose one synchronisation waits for that stream
-    only), evaluated by one fused pass (shg_plan_2c_exec_fused) on the
-    caller's stream, and its blocks (a contiguous range of every output,
+    only), evaluated by one fused pass (shg_plan_2c_exec_fused) on one of
+    two compute streams (alternating, so that consecutive passes overlap at
+    their tails), and its blocks (a contiguous range of every output,
     since the offsets are the prefix sums of the block sizes) are copied to
     the host on a copy stream.  The host plans slice k+1 while the GPU
     computes slice k, and the read-back of slice k overlaps the computation
@@ -317,16 +318,19 @@ class HostPipeline2c:
         self.schedule = schedule
         self.copy_stream = torch.cuda.Stream()
         self.upload_stream = torch.cuda.Stream()
+        # chunks alternate between two compute streams, so that chunk k+1's pass
+        # fills the tail of chunk k's (each ends with its slowest tile)
+        self.compute_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         self._dev = {}
 
     @staticmethod
     def default_chunks(precision):
-        """FP64: four chunks (measured on the 2M-pair workload: 19.2, 19.3,
-        19.3, 18.8 and 20.2 ms for 1, 2, 3, 4 and 6 chunks).  Mixed: one,
-        since every chunk of a mixed pass waits for its own FP64 launch of the
-        classes with both l >= 4, whose slowest tile sets a fixed time per
-        chunk (8.3 ms for one chunk, 10.0 for two)."""
-        return 1 if precision == "mixed" else 4
+        """Measured on the 2M-pair workload (1/r and erfc): FP64 18.7, 18.1,
+        18.5 and 19.3 ms for 1, 2, 4 and 8 chunks, so two; mixed 8.3, 8.4, 9.9
+        and 12.7 ms, so one (every chunk of a mixed pass also waits for its own
+        FP64 launch of the classes with both l >= 4, whose slowest tile sets a
+        fixed time per chunk)."""
+        return 1 if precision == "mixed" else 2
 
     def _buf(self, name, n, dtype):
         t = self._dev.get(name)
@@ -348,10 +352,12 @@ class HostPipeline2c:
         if centers is not None:
             self.basis.set_centers(centers)
         # earlier work on the caller's stream (a previous run's use of the
-        # buffers) comes before the uploads
+        # buffers) comes before the uploads and the passes
         start = torch.cuda.Event()
         start.record(stream)
         up.wait_event(start)
+        for cs in self.compute_streams:
+            cs.wait_event(start)
         off_h = offsets.numpy()
         chunks = self.n_chunks or self.default_chunks(precision)
         bounds = [n * k // chunks for k in range(chunks + 1)]
@@ -373,18 +379,20 @@ class HostPipeline2c:
                            self.launch.get("variant", 1))
             planned = torch.cuda.Event()
             planned.record(up)
-            stream.wait_event(planned)
-            plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision, stream=stream)
+            cs = self.compute_streams[len(plans) % 2]
+            cs.wait_event(planned)
+            plan.exec_fused(ops, d_off[lo:hi], d_out, omegas=omegas, precision=precision, stream=cs)
             e0 = int(off_h[lo])
             e1 = int(off_h[hi]) if hi < n else total
             done = torch.cuda.Event()
-            done.record(stream)
+            done.record(cs)
             self.copy_stream.wait_event(done)
             torch.cuda.nvtx.range_push("shg:d2h")
             with torch.cuda.stream(self.copy_stream):
                 for o_h, o_d in zip(outs, d_out):
                     o_h[e0:e1].copy_(o_d[e0:e1], non_blocking=True)
             torch.cuda.nvtx.range_pop()
+        # the copy stream waited for every pass: fin orders all of them
         fin = torch.cuda.Event()
         fin.record(self.copy_stream)
         stream.wait_event(fin)
