@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--replicas", action="store_true",
                    help="N > 1: every rank evaluates the whole workload (weak scaling) instead of its "
                         "cost-balanced slice of the one pair list (strong scaling, the default)")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--e2e-chunks", type=int, default=0,
                    help="contiguous chunks of the end-to-end pipeline (read-back of chunk k overlaps chunk k+1); "
                         "0: the pipeline's default for the precision")
@@ -491,7 +491,9 @@ def run_ours(args, rank, world):
             if it > 0:
                 times.append(time.perf_counter() - t1)
         if times:
-            e2e_s = statistics.mean(times)
+            # median: a host-timed call with 128 MB in and 268 MB out through the
+            # host link is exposed to outliers (other traffic on the link)
+            e2e_s = statistics.median(times)
     if dist:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -543,7 +545,8 @@ def run_ours(args, rank, world):
                          "pair list in %d contiguous chunks; per chunk the pinned H2D of its pair lists and "
                          "offsets and shg_plan_2c_create on an upload stream (overlapping the previous chunk's "
                          "pass), shg_plan_2c_exec_fused (both operators), and the D2H of its blocks to pinned "
-                         "memory on a copy stream overlapping the next chunk" % e2e_chunks if fused else
+                         "memory on a copy stream overlapping the next chunk; median over the timed calls"
+                         % e2e_chunks if fused else
                          "per step: pinned H2D of pair lists, offsets and centers, shg_basis_set_centers, "
                          "shg_plan_2c_create, one shg_plan_2c_exec per operator, D2H of all blocks to pinned memory (operator "
                          "k's copy on a second stream overlaps operator k+1's kernel)"),

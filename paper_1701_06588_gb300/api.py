@@ -325,12 +325,12 @@ class HostPipeline2c:
 
     @staticmethod
     def default_chunks(precision):
-        """Measured on the 2M-pair workload (1/r and erfc): FP64 18.7, 18.1,
-        18.5 and 19.3 ms for 1, 2, 4 and 8 chunks, so two; mixed 8.3, 8.4, 9.9
-        and 12.7 ms, so one (every chunk of a mixed pass also waits for its own
-        FP64 launch of the classes with both l >= 4, whose slowest tile sets a
-        fixed time per chunk)."""
-        return 1 if precision == "mixed" else 2
+        """Measured on the 2M-pair workload (1/r and erfc), median ms per
+        call: FP64 18.7, 18.1-18.8, 18.5 and 19.3 for 1, 2, 4 and 8 chunks
+        (4 varies least); mixed 8.3, 8.4, 9.9 and 12.7, so one chunk (every
+        chunk of a mixed pass also waits for its own FP64 launch of the classes
+        with both l >= 4, whose slowest tile sets a fixed time per chunk)."""
+        return 1 if precision == "mixed" else 4
 
     def _buf(self, name, n, dtype):
         t = self._dev.get(name)
